@@ -1,0 +1,682 @@
+/*
+ * smc_oracle.c -- plain FP64 CPU oracle of the tempered SMC sampler.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the test-suite, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header or constant table with
+ * the CUDA library.
+ *
+ * Every quantity is double precision, every loop is sequential, and every
+ * Metropolis proposal recomputes the full forward model and energy.  Each
+ * function names the passage of the paper it follows.  Where the paper is
+ * silent the reading taken is written beside the code:
+ *   - likelihood: Gaussian with known per-point sigma_i; the energy is
+ *     E = 1/2 sum ((y_i - f_i)/sigma_i)^2 and the reported log Z adds the
+ *     normaliser -sum log(sqrt(2 pi) sigma_i)          (App. C, Eq. (C2));
+ *   - tempering: next beta by bisection on the effective sample size;
+ *   - resampling: systematic, on integer-quantised weights (exact);
+ *   - step sizes: lambda_j * weighted population SD, lambda_j adapted from
+ *     the previous stage's acceptance rate;
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *     key = seed and counter = (draw, particle, stage, K).
+ *
+ * Parity status: every function here is pinned by tests (closed forms,
+ * brute force, published Philox answers, the linear-Gaussian evidence and
+ * K = 1 quadrature).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+#define ORC_EMAXSTAGES 5
+#define ORC_ENUMERIC 8
+
+enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2 };
+enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3 };
+enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
+
+typedef struct {
+    int32_t kind;
+    double p1, p2;
+} orc_prior;
+
+typedef struct {
+    const double *x, *y, *sigma;
+    int64_t n;
+    int32_t family, K, bg_kind, bg_degree;
+    orc_prior amp, centre, width, eta, bg[8];
+    const orc_prior *comp_priors; /* optional: one prior per component (d) */
+    int32_t n_comp_priors;
+    int64_t particles;
+    double ess_target;
+    int32_t sweeps, waste_free;
+    uint64_t seed;
+    int32_t max_stages;
+} orc_job;
+
+typedef struct {
+    double log_z;
+    int32_t n_stages;
+    int32_t status;
+    int64_t n_out;     /* particles in the final set */
+    int32_t d;
+    double *samples;   /* [n_out][d] natural parameter values (caller buffer) */
+    double *energies;  /* [n_out] */
+    double *beta_trace;   /* [max_stages + 1], beta after each stage */
+    double *logz_trace;   /* [max_stages + 1], log Z after each stage */
+    double *acc_trace;    /* [max_stages + 1][d] acceptance rate per component */
+    double *step_trace;   /* [max_stages + 1][d] step size used per component */
+} orc_out;
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw,  */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of two   */
+/* 32x32->64 multiplies with a Weyl-sequence key schedule.                    */
+/* ------------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in (0, 1): (k + 1/2) 2^-32 */
+static double u01(uint32_t k) { return ((double)k + 0.5) * 2.3283064365386963e-10; }
+
+static void draw_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                       uint32_t w[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, w);
+}
+
+/* Box-Muller (1958): one standard normal from two uniforms. */
+static double box_muller(uint32_t a, uint32_t b)
+{
+    return sqrt(-2.0 * log(u01(a))) * cos(2.0 * M_PI * u01(b));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model layout: peak k has components (A, mu, width[, eta]), then the        */
+/* background coefficients (forward model, Sec. II A, Eq. (1)).               */
+/* ------------------------------------------------------------------------- */
+static int peak_params(int family) { return family == FAM_PV ? 4 : 3; }
+
+static int bg_params(int kind, int degree)
+{
+    switch (kind) {
+    case BG_NONE: return 0;
+    case BG_CONST: return 1;
+    case BG_LINEAR: return 2;
+    default: return degree + 1;
+    }
+}
+
+int orc_dim(int family, int K, int bg_kind, int bg_degree)
+{
+    return peak_params(family) * K + bg_params(bg_kind, bg_degree);
+}
+
+static orc_prior comp_prior(const orc_job *job, int j)
+{
+    if (job->n_comp_priors > 0) return job->comp_priors[j];
+    int p = peak_params(job->family);
+    if (j < p * job->K) {
+        switch (j % p) {
+        case 0: return job->amp;
+        case 1: return job->centre;
+        case 2: return job->width;
+        default: return job->eta;
+        }
+    }
+    return job->bg[j - p * job->K];
+}
+
+/* Sampler coordinate u -> natural value (log-uniform priors are sampled in log). */
+static double to_natural(orc_prior pr, double u) { return pr.kind == PR_LOG_UNIFORM ? exp(u) : u; }
+
+static int in_support(orc_prior pr, double u)
+{
+    switch (pr.kind) {
+    case PR_UNIFORM: return u >= pr.p1 && u <= pr.p2;
+    case PR_LOG_UNIFORM: return u >= log(pr.p1) && u <= log(pr.p2);
+    case PR_GAMMA: return u > 0.0;
+    case PR_NORMAL: return 1;
+    default: return 0;
+    }
+}
+
+/* log prior density in sampler coordinates, up to an additive constant. */
+static double log_prior(orc_prior pr, double u)
+{
+    switch (pr.kind) {
+    case PR_NORMAL: {
+        double z = (u - pr.p1) / pr.p2;
+        return -0.5 * z * z;
+    }
+    case PR_GAMMA: return (pr.p1 - 1.0) * log(u) - pr.p2 * u;
+    default: return 0.0;
+    }
+}
+
+/* Peak profiles with natural parameters.
+ * Gaussian with standard deviation w (App. C Eq. (C1) with b = 1/w^2);
+ * Lorentzian with HWHM w (the Lorentzian part of Eq. (E1));
+ * pseudo-Voigt of Eq. (E1): eta * Gaussian + (1 - eta) * Lorentzian, shared HWHM. */
+double orc_peak(int family, double x, double A, double mu, double w, double eta)
+{
+    double dx = x - mu;
+    if (family == FAM_GAUSS) return A * exp(-dx * dx / (2.0 * w * w));
+    double lor = w * w / (w * w + dx * dx);
+    if (family == FAM_LORENTZ) return A * lor;
+    double s = w / sqrt(2.0 * log(2.0));
+    double gau = exp(-dx * dx / (2.0 * s * s));
+    return A * (eta * gau + (1.0 - eta) * lor);
+}
+
+/* Chebyshev polynomial T_j(t) by the three-term recurrence. */
+static double chebyshev(int j, double t)
+{
+    double a = 1.0, b = t;
+    if (j == 0) return a;
+    for (int k = 2; k <= j; ++k) {
+        double c = 2.0 * t * b - a;
+        a = b;
+        b = c;
+    }
+    return b;
+}
+
+/* Forward model f(x; theta) = sum_k g_k(x; theta_k) + b(x)  (Eq. (1)).
+ * nat: natural parameters in component order. */
+double orc_model_at(int family, int K, int nbg, const double *nat, double x, double xmin,
+                    double xmax)
+{
+    int p = peak_params(family);
+    double f = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double *q = nat + p * k;
+        f += orc_peak(family, x, q[0], q[1], q[2], p == 4 ? q[3] : 0.0);
+    }
+    if (nbg > 0) {
+        double t = (2.0 * x - (xmin + xmax)) / (xmax - xmin);
+        for (int j = 0; j < nbg; ++j) f += nat[p * K + j] * chebyshev(j, t);
+    }
+    return f;
+}
+
+static void range_of(const double *x, int64_t n, double *lo, double *hi)
+{
+    double a = x[0], b = x[0];
+    for (int64_t i = 1; i < n; ++i) {
+        if (x[i] < a) a = x[i];
+        if (x[i] > b) b = x[i];
+    }
+    *lo = a;
+    *hi = b;
+}
+
+/* Energy E = 1/2 sum_i ((y_i - f_i) / sigma_i)^2 : the negative log-likelihood
+ * of App. C Eq. (C2) with per-point known sigma, without the 1/N factor and
+ * without the normaliser (which is added to log Z once). */
+double orc_energy_nat(int family, int K, int nbg, const double *nat, const double *x,
+                      const double *y, const double *sigma, int64_t n)
+{
+    double xmin, xmax;
+    range_of(x, n, &xmin, &xmax);
+    double e = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = (y[i] - orc_model_at(family, K, nbg, nat, x[i], xmin, xmax)) / sigma[i];
+        e += 0.5 * r * r;
+    }
+    return e;
+}
+
+typedef struct {
+    const orc_job *job;
+    int d, p, nbg;
+    double xmin, xmax;
+    orc_prior *pri;
+    double *nat; /* scratch [d] */
+} ctx_t;
+
+static double energy_u(ctx_t *c, const double *u)
+{
+    for (int j = 0; j < c->d; ++j) c->nat[j] = to_natural(c->pri[j], u[j]);
+    const orc_job *job = c->job;
+    double e = 0.0;
+    for (int64_t i = 0; i < job->n; ++i) {
+        double r = (job->y[i] - orc_model_at(job->family, job->K, c->nbg, c->nat, job->x[i],
+                                             c->xmin, c->xmax)) /
+                   job->sigma[i];
+        e += 0.5 * r * r;
+    }
+    return e;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Prior draws at beta_0 = 0 (Sec. II B 2: the tempered sequence starts at the */
+/* prior).  Counter (256 j + attempt, particle, 0, K).                         */
+/* Gamma(shape, rate) by Marsaglia & Tsang (2000), with the u^(1/a) boost for  */
+/* shape < 1.                                                                  */
+/* ------------------------------------------------------------------------- */
+double orc_prior_draw(orc_prior pr, uint64_t seed, uint32_t comp, uint32_t particle,
+                      uint32_t tag)
+{
+    uint32_t w[4];
+    switch (pr.kind) {
+    case PR_UNIFORM:
+        draw_words(seed, 256u * comp, particle, 0u, tag, w);
+        return pr.p1 + (pr.p2 - pr.p1) * u01(w[0]);
+    case PR_LOG_UNIFORM:
+        draw_words(seed, 256u * comp, particle, 0u, tag, w);
+        return log(pr.p1) + (log(pr.p2) - log(pr.p1)) * u01(w[0]);
+    case PR_NORMAL:
+        draw_words(seed, 256u * comp, particle, 0u, tag, w);
+        return pr.p1 + pr.p2 * box_muller(w[0], w[1]);
+    case PR_GAMMA: {
+        double a = pr.p1 < 1.0 ? pr.p1 + 1.0 : pr.p1;
+        double dd = a - 1.0 / 3.0;
+        double cc = 1.0 / sqrt(9.0 * dd);
+        for (uint32_t attempt = 0; attempt < 256u; ++attempt) {
+            draw_words(seed, 256u * comp + attempt, particle, 0u, tag, w);
+            double z = box_muller(w[0], w[1]);
+            double t = 1.0 + cc * z;
+            if (t <= 0.0) continue;
+            double v = t * t * t;
+            if (log(u01(w[2])) < 0.5 * z * z + dd - dd * v + dd * log(v)) {
+                double g = dd * v;
+                if (pr.p1 < 1.0) g *= pow(u01(w[3]), 1.0 / pr.p1);
+                return g / pr.p2;
+            }
+        }
+        return dd / pr.p2;
+    }
+    default: return pr.p1; /* FIXED */
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tempering: ESS fraction of the incremental weights w_i = exp(-delta e_i)   */
+/* (Sec. II B 2, Eq. (10)), e_i = E_i - min E; non-finite energies get w = 0.  */
+/* ------------------------------------------------------------------------- */
+double orc_ess_frac(const double *e, int64_t T, double delta)
+{
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = 0; i < T; ++i) {
+        if (!isfinite(e[i])) continue;
+        double w = exp(-delta * e[i]);
+        s1 += w;
+        s2 += w * w;
+    }
+    return s1 * s1 / ((double)T * s2);
+}
+
+/* Next temperature increment.  If the whole remaining step keeps ESS >= rho T
+ * take it; otherwise bisect [0, 1 - beta], keeping ESS(lo) >= rho T > ESS(hi),
+ * until hi - lo <= 1e-7 hi (cap 200 halvings), and return lo. */
+double orc_choose_delta(const double *e, int64_t T, double beta, double rho, int *final_step,
+                        int *iters)
+{
+    double room = 1.0 - beta;
+    *iters = 0;
+    if (orc_ess_frac(e, T, room) >= rho) {
+        *final_step = 1;
+        return room;
+    }
+    double lo = 0.0, hi = room;
+    int it = 0;
+    while (it < 200 && hi - lo > 1e-7 * hi) {
+        double mid = 0.5 * (lo + hi);
+        if (orc_ess_frac(e, T, mid) >= rho)
+            lo = mid;
+        else
+            hi = mid;
+        ++it;
+    }
+    *iters = it;
+    *final_step = 0;
+    return lo > 0.0 ? lo : hi;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Systematic resampling on integer weights (Sec. II B 2: resample by the      */
+/* normalised weights).  q_i = floor(w_i 2^40), Q = sum q, r = floor(U Q/2^32), */
+/* t_m = floor((m Q + r) / M), ancestor a_m = min{ i : C_i > t_m } with C the  */
+/* inclusive prefix sum -- written here as a plain forward scan.               */
+/* ------------------------------------------------------------------------- */
+void orc_quantise(const double *w, int64_t T, uint64_t *q)
+{
+    for (int64_t i = 0; i < T; ++i) q[i] = (uint64_t)floor(ldexp(w[i], 40));
+}
+
+void orc_resample(const uint64_t *q, int64_t T, int64_t M, uint32_t u32, int32_t *anc)
+{
+    unsigned __int128 Q = 0;
+    for (int64_t i = 0; i < T; ++i) Q += q[i];
+    unsigned __int128 r = ((unsigned __int128)u32 * Q) >> 32;
+    int64_t i = 0;
+    unsigned __int128 C = q[0];
+    for (int64_t m = 0; m < M; ++m) {
+        unsigned __int128 t = ((unsigned __int128)m * Q + r) / (unsigned __int128)M;
+        while (C <= t) {
+            ++i;
+            C += q[i];
+        }
+        anc[m] = (int32_t)i;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Metropolis rejuvenation (Sec. II B 4): component-wise random-walk MH, one   */
+/* 1-D Gaussian proposal per component in fixed order, n sweeps per chain.     */
+/* Counter (t d + j, chain, stage, K); z by Box-Muller from words 0, 1; the    */
+/* accept uniform from word 2.  Out-of-support proposals count as rejections.  */
+/* Waste-free mode (Sec. II B 3) keeps the state after every sweep.            */
+/* ------------------------------------------------------------------------- */
+static void mh_chains(ctx_t *c, const double *u_start, const double *E_start, int64_t S,
+                      const double *step, double beta, uint32_t stage, double *u_out,
+                      double *E_out, int64_t *acc, int64_t *prop, double *cur)
+{
+    const orc_job *job = c->job;
+    int d = c->d, n = job->sweeps;
+    uint32_t tag = (uint32_t)job->K;
+    for (int j = 0; j < d; ++j) acc[j] = prop[j] = 0;
+    for (int64_t m = 0; m < S; ++m) {
+        memcpy(cur, u_start + (size_t)m * d, sizeof(double) * d);
+        double Ec = E_start[m];
+        for (int t = 0; t < n; ++t) {
+            for (int j = 0; j < d; ++j) {
+                if (c->pri[j].kind == PR_FIXED) continue;
+                uint32_t ww[4];
+                draw_words(job->seed, (uint32_t)(t * d + j), (uint32_t)m, stage, tag, ww);
+                double z = box_muller(ww[0], ww[1]);
+                double up = cur[j] + step[j] * z;
+                prop[j]++;
+                if (!in_support(c->pri[j], up)) continue;
+                double dlp = log_prior(c->pri[j], up) - log_prior(c->pri[j], cur[j]);
+                double old = cur[j];
+                cur[j] = up;
+                double Ep = energy_u(c, cur);
+                if (log(u01(ww[2])) < -beta * (Ep - Ec) + dlp) {
+                    Ec = Ep;
+                    acc[j]++;
+                } else {
+                    cur[j] = old;
+                }
+            }
+            if (job->waste_free) {
+                memcpy(u_out + (size_t)(m * n + t) * d, cur, sizeof(double) * d);
+                E_out[m * n + t] = Ec;
+            }
+        }
+        if (!job->waste_free) {
+            memcpy(u_out + (size_t)m * d, cur, sizeof(double) * d);
+            E_out[m] = Ec;
+        }
+    }
+}
+
+static int setup_ctx(ctx_t *c, const orc_job *job)
+{
+    c->job = job;
+    c->p = peak_params(job->family);
+    c->nbg = bg_params(job->bg_kind, job->bg_degree);
+    c->d = c->p * job->K + c->nbg;
+    range_of(job->x, job->n, &c->xmin, &c->xmax);
+    c->pri = (orc_prior *)malloc(sizeof(orc_prior) * (c->d > 0 ? c->d : 1));
+    c->nat = (double *)malloc(sizeof(double) * (c->d > 0 ? c->d : 1));
+    if (!c->pri || !c->nat) return ORC_ENOMEM;
+    for (int j = 0; j < c->d; ++j) c->pri[j] = comp_prior(job, j);
+    return ORC_OK;
+}
+
+/* Exported pieces so that tests can replay single steps. */
+
+/* Prior draws for particles [0, count) in sampler coordinates, with energies. */
+int orc_init_particles(const orc_job *job, int64_t count, double *u, double *E)
+{
+    ctx_t c;
+    if (setup_ctx(&c, job) != ORC_OK) return ORC_ENOMEM;
+    for (int64_t i = 0; i < count; ++i) {
+        for (int j = 0; j < c.d; ++j)
+            u[i * c.d + j] =
+                orc_prior_draw(c.pri[j], job->seed, (uint32_t)j, (uint32_t)i, (uint32_t)job->K);
+        E[i] = energy_u(&c, u + i * c.d);
+    }
+    free(c.pri);
+    free(c.nat);
+    return ORC_OK;
+}
+
+/* Energy of particles given in sampler coordinates. */
+int orc_energies(const orc_job *job, int64_t count, const double *u, double *E)
+{
+    ctx_t c;
+    if (setup_ctx(&c, job) != ORC_OK) return ORC_ENOMEM;
+    for (int64_t i = 0; i < count; ++i) E[i] = energy_u(&c, u + i * c.d);
+    free(c.pri);
+    free(c.nat);
+    return ORC_OK;
+}
+
+/* One Metropolis stage on S chain starts (already resampled). */
+int orc_mh_stage(const orc_job *job, const double *u_start, const double *E_start, int64_t S,
+                 const double *step, double beta, uint32_t stage, double *u_out, double *E_out,
+                 int64_t *acc, int64_t *prop)
+{
+    ctx_t c;
+    if (setup_ctx(&c, job) != ORC_OK) return ORC_ENOMEM;
+    double *cur = (double *)malloc(sizeof(double) * (c.d > 0 ? c.d : 1));
+    mh_chains(&c, u_start, E_start, S, step, beta, stage, u_out, E_out, acc, prop, cur);
+    free(cur);
+    free(c.pri);
+    free(c.nat);
+    return ORC_OK;
+}
+
+/* Step sizes of the adaptive rule: lambda_j <- clamp(lambda_j exp(acc_j - 0.44),
+ * 0.01, 10) when an acceptance rate is available, step_j = lambda_j *
+ * max(weighted SD_j, 1e-9 (1 + |weighted mean_j|)).  Weights w need not be
+ * normalised.  FIXED components get step 0. */
+void orc_step_sizes(const orc_job *job, const double *u, const double *w, int64_t T,
+                    const double *acc_rate, double *lam, double *step)
+{
+    ctx_t c;
+    if (setup_ctx(&c, job) != ORC_OK) return;
+    int d = c.d;
+    double sw = 0.0;
+    for (int64_t i = 0; i < T; ++i) sw += w[i];
+    for (int j = 0; j < d; ++j) {
+        if (c.pri[j].kind == PR_FIXED) {
+            step[j] = 0.0;
+            continue;
+        }
+        double m1 = 0.0;
+        for (int64_t i = 0; i < T; ++i) m1 += w[i] * u[i * d + j];
+        m1 /= sw;
+        double v = 0.0;
+        for (int64_t i = 0; i < T; ++i) {
+            double t = u[i * d + j] - m1;
+            v += w[i] * t * t;
+        }
+        v /= sw;
+        double sd = sqrt(v);
+        double floor_sd = 1e-9 * (1.0 + fabs(m1));
+        if (sd < floor_sd) sd = floor_sd;
+        if (acc_rate) {
+            lam[j] *= exp(acc_rate[j] - 0.44);
+            if (lam[j] < 0.01) lam[j] = 0.01;
+            if (lam[j] > 10.0) lam[j] = 10.0;
+        }
+        step[j] = lam[j] * sd;
+    }
+    free(c.pri);
+    free(c.nat);
+}
+
+/* ------------------------------------------------------------------------- */
+/* One full SMC run for one (spectrum, K) job (Sec. II B 2-4).                 */
+/* ------------------------------------------------------------------------- */
+static int validate(const orc_job *job, int d)
+{
+    if (job->n < 2 || job->K < 0 || job->particles < 2 || job->sweeps < 1) return ORC_EINVAL;
+    if (!(job->ess_target > 0.0 && job->ess_target < 1.0)) return ORC_EINVAL;
+    if (job->n_comp_priors > 0 && job->n_comp_priors != d) return ORC_EINVAL;
+    for (int64_t i = 0; i < job->n; ++i)
+        if (!(job->sigma[i] > 0.0) || !isfinite(job->sigma[i]) || !isfinite(job->y[i]) ||
+            !isfinite(job->x[i]))
+            return ORC_EINVAL;
+    return ORC_OK;
+}
+
+int orc_run_job(const orc_job *job, orc_out *out)
+{
+    ctx_t c;
+    int d = orc_dim(job->family, job->K, job->bg_kind, job->bg_degree);
+    out->d = d;
+    out->status = validate(job, d);
+    if (out->status != ORC_OK) return out->status;
+    if (setup_ctx(&c, job) != ORC_OK) return out->status = ORC_ENOMEM;
+
+    int n = job->sweeps;
+    int64_t T = job->particles;
+    int64_t S = job->waste_free ? (T + n - 1) / n : T; /* chains per stage */
+    int64_t Tc = job->waste_free ? S * n : T;          /* particles carried */
+    uint32_t tag = (uint32_t)job->K;
+    size_t dd = (size_t)(d > 0 ? d : 1);
+
+    double *u = (double *)malloc(sizeof(double) * Tc * dd);
+    double *un = (double *)malloc(sizeof(double) * Tc * dd);
+    double *us = (double *)malloc(sizeof(double) * S * dd);
+    double *E = (double *)malloc(sizeof(double) * Tc);
+    double *En = (double *)malloc(sizeof(double) * Tc);
+    double *Es = (double *)malloc(sizeof(double) * S);
+    double *e = (double *)malloc(sizeof(double) * Tc);
+    double *w = (double *)malloc(sizeof(double) * Tc);
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * Tc);
+    int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * S);
+    double *lam = (double *)malloc(sizeof(double) * dd);
+    double *step = (double *)malloc(sizeof(double) * dd);
+    double *rate = (double *)malloc(sizeof(double) * dd);
+    int64_t *acc = (int64_t *)calloc(dd, sizeof(int64_t));
+    int64_t *prop = (int64_t *)calloc(dd, sizeof(int64_t));
+    double *cur = (double *)malloc(sizeof(double) * dd);
+    if (!u || !un || !us || !E || !En || !Es || !e || !w || !q || !anc || !lam || !step ||
+        !rate || !acc || !prop || !cur) {
+        out->status = ORC_ENOMEM;
+        goto done;
+    }
+    for (int j = 0; j < d; ++j) lam[j] = 2.38;
+
+    /* normaliser of the Gaussian likelihood (reading of App. C, Eq. (C2)) */
+    double lognorm = 0.0;
+    for (int64_t i = 0; i < job->n; ++i) lognorm -= log(sqrt(2.0 * M_PI) * job->sigma[i]);
+
+    /* stage 0: prior draws, beta_0 = 0 (Eq. (9)) */
+    for (int64_t i = 0; i < Tc; ++i) {
+        for (int j = 0; j < d; ++j)
+            u[i * d + j] = orc_prior_draw(c.pri[j], job->seed, (uint32_t)j, (uint32_t)i, tag);
+        E[i] = energy_u(&c, u + i * d);
+    }
+    double beta = 0.0, logz = lognorm;
+    if (out->beta_trace) out->beta_trace[0] = 0.0;
+    if (out->logz_trace) out->logz_trace[0] = logz;
+    out->status = ORC_OK;
+
+    int stage = 0;
+    for (;;) {
+        ++stage;
+        if (stage > job->max_stages) {
+            out->status = ORC_EMAXSTAGES;
+            stage = job->max_stages;
+            break;
+        }
+        /* -- reweight: incremental weights (Eq. (10)), next beta by bisection */
+        double emin = INFINITY;
+        for (int64_t i = 0; i < Tc; ++i)
+            if (isfinite(E[i]) && E[i] < emin) emin = E[i];
+        if (!isfinite(emin)) {
+            out->status = ORC_ENUMERIC;
+            break;
+        }
+        for (int64_t i = 0; i < Tc; ++i) e[i] = isfinite(E[i]) ? E[i] - emin : INFINITY;
+        int final_step = 0, iters = 0;
+        double delta = orc_choose_delta(e, Tc, beta, job->ess_target, &final_step, &iters);
+        double sw = 0.0;
+        for (int64_t i = 0; i < Tc; ++i) {
+            w[i] = isfinite(e[i]) ? exp(-delta * e[i]) : 0.0;
+            sw += w[i];
+        }
+        /* -- evidence increment: log of the mean unnormalised weight (Eq. (11)) */
+        logz += -delta * emin + log(sw / (double)Tc);
+        beta = final_step ? 1.0 : beta + delta;
+
+        /* -- step sizes from the reweighted population and last acceptance */
+        if (stage > 1)
+            for (int j = 0; j < d; ++j) rate[j] = prop[j] ? (double)acc[j] / (double)prop[j] : 0.44;
+        orc_step_sizes(job, u, w, Tc, stage > 1 ? rate : NULL, lam, step);
+        if (out->step_trace)
+            for (int j = 0; j < d; ++j) out->step_trace[(size_t)stage * d + j] = step[j];
+
+        /* -- systematic resampling of S ancestors */
+        orc_quantise(w, Tc, q);
+        uint32_t rw[4];
+        draw_words(job->seed, 0u, 0xFFFFFFFFu, (uint32_t)stage, tag, rw);
+        orc_resample(q, Tc, S, rw[0], anc);
+        for (int64_t m = 0; m < S; ++m) {
+            memcpy(us + (size_t)m * d, u + (size_t)anc[m] * d, sizeof(double) * d);
+            Es[m] = E[anc[m]];
+        }
+
+        /* -- Metropolis rejuvenation at beta */
+        mh_chains(&c, us, Es, S, step, beta, (uint32_t)stage, un, En, acc, prop, cur);
+        {
+            double *tp = u; u = un; un = tp;
+            tp = E; E = En; En = tp;
+        }
+        if (out->beta_trace) out->beta_trace[stage] = beta;
+        if (out->logz_trace) out->logz_trace[stage] = logz;
+        if (out->acc_trace)
+            for (int j = 0; j < d; ++j)
+                out->acc_trace[(size_t)stage * d + j] =
+                    prop[j] ? (double)acc[j] / (double)prop[j] : 0.0;
+        if (beta >= 1.0) break;
+    }
+    out->log_z = logz;
+    out->n_stages = stage;
+    out->n_out = Tc;
+    if (out->samples)
+        for (int64_t i = 0; i < Tc; ++i)
+            for (int j = 0; j < d; ++j)
+                out->samples[i * d + j] = to_natural(c.pri[j], u[i * d + j]);
+    if (out->energies)
+        for (int64_t i = 0; i < Tc; ++i) out->energies[i] = E[i];
+
+done:
+    free(c.pri); free(c.nat); free(u); free(un); free(us); free(E); free(En); free(Es);
+    free(e); free(w); free(q); free(anc); free(lam); free(step); free(rate); free(acc);
+    free(prop); free(cur);
+    return out->status;
+}

@@ -1,0 +1,297 @@
+"""Seeded synthetic inputs: spectra, priors and sampler options.
+
+This module only *makes inputs*.  It holds none of the sampler's arithmetic
+(no energy, tempering, resampling or Metropolis code) and imports neither the
+CUDA binding nor the oracle, so both sides can be fed from it.  The peak shapes
+used to synthesise the data are written out here with numpy, independently of
+the oracle and of the kernels.
+
+Workload shapes follow the paper's experiments: a Gaussian-peak deconvolution
+spectrum (Sec. III A 2, App. C), an XPS-like pseudo-Voigt spectrum on a
+binding-energy axis (App. E, Eq. (E1)) and an XRD-like sparse Lorentzian /
+pseudo-Voigt pattern on a 2-theta axis (App. D).  The measured spectra of the
+paper are not available; these seeded generators stand in for them.
+
+Parameter conventions (shared by the C ABI):
+  family 0 GAUSS   : A exp(-(x-mu)^2 / (2 w^2)),        w = standard deviation
+  family 1 LORENTZ : A g^2 / (g^2 + (x-mu)^2),           g = HWHM
+  family 2 PV      : A [eta 2^(-(x-mu)^2/s^2) + (1-eta) s^2/(s^2+(x-mu)^2)],
+                     s = shared HWHM, eta = Gaussian fraction (Eq. (E1))
+  background       : sum_j c_j T_j(t), T_j Chebyshev, t = x scaled to [-1, 1]
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+GAUSS, LORENTZ, PSEUDO_VOIGT = 0, 1, 2
+BG_NONE, BG_CONST, BG_LINEAR, BG_POLY = 0, 1, 2, 3
+UNIFORM, LOG_UNIFORM, NORMAL, GAMMA, FIXED = 0, 1, 2, 3, 4
+
+
+@dataclasses.dataclass
+class Prior:
+    kind: int
+    p1: float = 0.0
+    p2: float = 0.0
+
+
+@dataclasses.dataclass
+class Priors:
+    amp: Prior
+    centre: Prior
+    width: Prior
+    eta: Prior = dataclasses.field(default_factory=lambda: Prior(UNIFORM, 0.0, 1.0))
+    bg: List[Prior] = dataclasses.field(default_factory=list)
+
+
+@dataclasses.dataclass
+class Options:
+    particles: int = 1024
+    ess_target: float = 0.5
+    sweeps: int = 10
+    waste_free: int = 0
+    energy_fp64: int = 0
+    seed: int = 1
+    max_stages: int = 10000
+
+
+@dataclasses.dataclass
+class Spectrum:
+    x: np.ndarray
+    y: np.ndarray
+    sigma: np.ndarray
+    family: int
+    k_min: int
+    k_max: int
+    bg: int
+    bg_degree: int
+    priors: Priors
+    truth: dict
+    name: str = ""
+    # Optional per-component priors (one per component, in component order);
+    # only meaningful when k_min == k_max.  Overrides the shared priors.
+    comp_priors: Optional[List[Prior]] = None
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+# ----------------------------------------------------------------------------
+# independent numpy peak synthesis (data generation only)
+# ----------------------------------------------------------------------------
+
+def _synth_gauss(x, A, mu, w):
+    return A * np.exp(-0.5 * ((x - mu) / w) ** 2)
+
+
+def _synth_pv(x, A, mu, hwhm, eta):
+    t2 = ((x - mu) / hwhm) ** 2
+    return A * (eta * np.exp(-math.log(2.0) * t2) + (1.0 - eta) / (1.0 + t2))
+
+
+def _synth_cheb(x, coeffs):
+    t = (2.0 * x - (x.min() + x.max())) / (x.max() - x.min())
+    return np.polynomial.chebyshev.chebval(t, coeffs)
+
+
+def bg_count(bg: int, bg_degree: int) -> int:
+    return {BG_NONE: 0, BG_CONST: 1, BG_LINEAR: 2}.get(bg, bg_degree + 1)
+
+
+def data_bg_priors(y: np.ndarray, nbg: int) -> List[Prior]:
+    """Uniform background-coefficient priors derived from the data range."""
+    ymin, ymax = float(y.min()), float(y.max())
+    dy = ymax - ymin
+    out = []
+    for j in range(nbg):
+        if j == 0:
+            out.append(Prior(UNIFORM, ymin - 0.2 * dy, ymin + 0.5 * dy))
+        else:
+            out.append(Prior(UNIFORM, -0.5 * dy, 0.5 * dy))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# configurations
+# ----------------------------------------------------------------------------
+
+def gaussian_small(seed: int = 1) -> Spectrum:
+    """301-point, two-Gaussian spectrum on [0, 10], noise sd 0.05, K in 1..3.
+
+    Truth: (A, mu, sd) = (1.0, 3.5, 0.5) and (0.6, 6.0, 0.8).  Priors:
+    centre ~ U[0, 10], log sd ~ U[log 0.1, log 3], amplitude ~ Gamma(2, 1)
+    (shape, rate).
+    """
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0.0, 10.0, 301)
+    f = _synth_gauss(x, 1.0, 3.5, 0.5) + _synth_gauss(x, 0.6, 6.0, 0.8)
+    y = f + rng.normal(0.0, 0.05, size=x.shape)
+    pri = Priors(amp=Prior(GAMMA, 2.0, 1.0), centre=Prior(UNIFORM, 0.0, 10.0),
+                 width=Prior(LOG_UNIFORM, 0.1, 3.0))
+    return Spectrum(x, y, np.full_like(x, 0.05), GAUSS, 1, 3, BG_NONE, 0, pri,
+                    truth={"K": 2, "A": [1.0, 0.6], "mu": [3.5, 6.0], "w": [0.5, 0.8]},
+                    name="gauss-301")
+
+
+def xps_like(seed: int = 1, n: int = 1001, k_true: int = 4, k_max: int = 6,
+             scale: float = 1.0e4) -> Spectrum:
+    """XPS-shaped pseudo-Voigt spectrum on a 20 eV binding-energy axis at 280 eV.
+
+    k_true peaks with eta ~ U[0, 1], FWHM ~ U[0.8, 2.0] eV, amplitude
+    S 10^U[-1, 0] (S = scale counts), centres ~ U[283, 297] at least 1 eV apart;
+    linear background 0.1 S + 0.002 S/eV (x - 280); variance f + (0.01 S)^2
+    (counting-like plus a floor).  Fitted with PV peaks + linear background,
+    K = 1..k_max.
+    """
+    rng = np.random.default_rng(seed)
+    x = 280.0 + np.linspace(0.0, 20.0, n)
+    mus: List[float] = []
+    while len(mus) < k_true:
+        m = rng.uniform(283.0, 297.0)
+        if all(abs(m - o) >= 1.0 for o in mus):
+            mus.append(m)
+    mus.sort()
+    eta = rng.uniform(0.0, 1.0, k_true)
+    fwhm = rng.uniform(0.8, 2.0, k_true)
+    amp = scale * 10.0 ** rng.uniform(-1.0, 0.0, k_true)
+    f = 0.1 * scale + 0.002 * scale * (x - 280.0)
+    for k in range(k_true):
+        f = f + _synth_pv(x, amp[k], mus[k], 0.5 * fwhm[k], eta[k])
+    var = f + (0.01 * scale) ** 2
+    y = f + np.sqrt(var) * rng.normal(size=x.shape)
+    sig = np.sqrt(var)
+    ymin, ymax = float(y.min()), float(y.max())
+    pri = Priors(amp=Prior(LOG_UNIFORM, 1e-3 * (ymax - ymin), 2.0 * ymax),
+                 centre=Prior(UNIFORM, float(x.min()), float(x.max())),
+                 width=Prior(LOG_UNIFORM, 0.2, 3.0),
+                 eta=Prior(UNIFORM, 0.0, 1.0),
+                 bg=data_bg_priors(y, 2))
+    return Spectrum(x, y, sig, PSEUDO_VOIGT, 1, k_max, BG_LINEAR, 1, pri,
+                    truth={"K": k_true, "A": amp.tolist(), "mu": mus,
+                           "hwhm": (0.5 * fwhm).tolist(), "eta": eta.tolist()},
+                    name=f"xps-{n}")
+
+
+def xrd_like(seed: int = 1, n: int = 4096, k_true: int = 10, k_max: int = 12) -> Spectrum:
+    """XRD-shaped sparse pattern on 2-theta in [10, 90] degrees.
+
+    k_true peaks, each Lorentzian (eta = 0) or pseudo-Voigt (eta ~ U[0, 1]) with
+    probability 1/2, FWHM ~ U[0.05, 0.3], amplitude 1e4 10^U[-3, 0]; cubic
+    Chebyshev background of amplitude 0.05 max; Gaussian noise of sd 1% of the
+    maximum of the noiseless pattern.  Fitted with PV peaks + cubic background.
+    """
+    rng = np.random.default_rng(seed)
+    x = np.linspace(10.0, 90.0, n)
+    mus = np.sort(rng.uniform(12.0, 88.0, k_true))
+    lor = rng.uniform(size=k_true) < 0.5
+    eta = np.where(lor, 0.0, rng.uniform(0.0, 1.0, k_true))
+    fwhm = rng.uniform(0.05, 0.3, k_true)
+    amp = 1.0e4 * 10.0 ** rng.uniform(-3.0, 0.0, k_true)
+    f = np.zeros_like(x)
+    for k in range(k_true):
+        f = f + _synth_pv(x, amp[k], mus[k], 0.5 * fwhm[k], eta[k])
+    peak_max = float(f.max())
+    cheb = 0.05 * peak_max * np.array([1.0, -0.4, 0.25, -0.1])
+    f = f + _synth_cheb(x, cheb)
+    sd = 0.01 * float(f.max())
+    y = f + rng.normal(0.0, sd, size=x.shape)
+    ymin, ymax = float(y.min()), float(y.max())
+    pri = Priors(amp=Prior(LOG_UNIFORM, 1e-3 * (ymax - ymin), 2.0 * ymax),
+                 centre=Prior(UNIFORM, float(x.min()), float(x.max())),
+                 width=Prior(LOG_UNIFORM, 0.01, 0.5),
+                 eta=Prior(UNIFORM, 0.0, 1.0),
+                 bg=data_bg_priors(y, 4))
+    return Spectrum(x, y, np.full_like(x, sd), PSEUDO_VOIGT, 1, k_max, BG_POLY, 3, pri,
+                    truth={"K": k_true, "A": amp.tolist(), "mu": mus.tolist(),
+                           "hwhm": (0.5 * fwhm).tolist(), "eta": eta.tolist()},
+                    name=f"xrd-{n}")
+
+
+def mixed_batch(seed: int = 1, count: int = 256) -> List[tuple]:
+    """Uneven batch: N ~ U{200..4000}, true K ~ U{1..8}, Gaussian or PV peaks.
+
+    Returns a list of (Spectrum, Options) pairs; particles per K in
+    {4096, 8192, 16384, 32768}, K_max ~ U{3..10}, 10 sweeps per stage.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = int(rng.integers(200, 4001))
+        k_true = int(rng.integers(1, 9))
+        k_max = int(rng.integers(3, 11))
+        fam = GAUSS if rng.uniform() < 0.5 else PSEUDO_VOIGT
+        x = np.linspace(0.0, 1.0, n) * 10.0
+        mus = np.sort(rng.uniform(0.5, 9.5, k_true))
+        amp = 10.0 ** rng.uniform(-1.0, 0.0, k_true)
+        if fam == GAUSS:
+            w = rng.uniform(0.1, 0.5, k_true)
+            f = sum(_synth_gauss(x, amp[k], mus[k], w[k]) for k in range(k_true))
+            sd = 0.02
+            pri = Priors(amp=Prior(GAMMA, 2.0, 2.0), centre=Prior(UNIFORM, 0.0, 10.0),
+                         width=Prior(LOG_UNIFORM, 0.05, 2.0))
+            bgk, bgd = BG_NONE, 0
+        else:
+            hw = rng.uniform(0.05, 0.3, k_true)
+            eta = rng.uniform(0.0, 1.0, k_true)
+            f = 0.05 + sum(_synth_pv(x, amp[k], mus[k], hw[k], eta[k]) for k in range(k_true))
+            sd = 0.02
+            bgk, bgd = BG_LINEAR, 1
+            pri = None
+        y = f + rng.normal(0.0, sd, size=x.shape)
+        if pri is None:
+            ymin, ymax = float(y.min()), float(y.max())
+            pri = Priors(amp=Prior(LOG_UNIFORM, 1e-3 * (ymax - ymin), 2.0 * ymax),
+                         centre=Prior(UNIFORM, 0.0, 10.0), width=Prior(LOG_UNIFORM, 0.02, 1.0),
+                         eta=Prior(UNIFORM, 0.0, 1.0), bg=data_bg_priors(y, 2))
+        spec = Spectrum(x, y, np.full_like(x, sd), fam, 1, k_max, bgk, bgd, pri,
+                        truth={"K": k_true}, name=f"mixed-{b}")
+        opts = Options(particles=int(rng.choice([4096, 8192, 16384, 32768])), sweeps=10,
+                       seed=seed * 100003 + b)
+        out.append((spec, opts))
+    return out
+
+
+def poisson_arrivals(rate_per_s: float, count: int, seed: int = 1) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+
+
+def linear_gaussian_case(seed: int = 3, n: int = 40, family: int = GAUSS) -> Spectrum:
+    """Two peaks with fixed centres and widths and Normal amplitude priors.
+
+    With every nonlinear parameter fixed the likelihood is linear-Gaussian in
+    the amplitudes, so log Z and the amplitude posterior have closed forms.
+    """
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0.0, 4.0, n)
+    mus, ws, amps = [1.3, 2.6], [0.35, 0.5], [0.9, 0.5]
+    f = sum(_synth_gauss(x, amps[k], mus[k], ws[k]) for k in range(2))
+    sd = 0.1
+    y = f + rng.normal(0.0, sd, size=x.shape)
+    pri = Priors(amp=Prior(NORMAL, 0.5, 0.7), centre=Prior(UNIFORM, 0.0, 4.0),
+                 width=Prior(LOG_UNIFORM, 0.1, 1.0))
+    comp = []
+    for k in range(2):
+        comp += [Prior(NORMAL, 0.5, 0.7), Prior(FIXED, mus[k]), Prior(FIXED, ws[k])]
+    return Spectrum(x, y, np.full_like(x, sd), family, 2, 2, BG_NONE, 0, pri,
+                    truth={"mu": mus, "w": ws, "m0": 0.5, "s0": 0.7}, name="linear-gaussian",
+                    comp_priors=comp)
+
+
+def tiny_single_peak(seed: int = 5, n: int = 21) -> Spectrum:
+    """21-point single Gaussian peak on [0, 2] for quadrature checks of log Z."""
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0.0, 2.0, n)
+    f = _synth_gauss(x, 1.2, 0.9, 0.25)
+    sd = 0.15
+    y = f + rng.normal(0.0, sd, size=x.shape)
+    pri = Priors(amp=Prior(GAMMA, 2.0, 1.0), centre=Prior(UNIFORM, 0.0, 2.0),
+                 width=Prior(LOG_UNIFORM, 0.1, 1.0))
+    return Spectrum(x, y, np.full_like(x, sd), GAUSS, 1, 1, BG_NONE, 0, pri,
+                    truth={"A": 1.2, "mu": 0.9, "w": 0.25}, name="tiny-single")

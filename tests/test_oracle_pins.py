@@ -1,0 +1,398 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+None of these re-types the oracle's own formula: each checks a closed form,
+an invariant, a published answer, a special case that reduces to a library
+routine, or an independent high-precision evaluation.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle
+from conftest import load_golden
+from paper_2604_03271_b300 import workloads as W
+
+GAUSS, LOR, PV = 0, 1, 2
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# --------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    for row in load_golden("philox4x32_10_kat.txt"):
+        v = [int(t, 16) for t in row]
+        got = oracle.philox(v[0:4], v[4:6])
+        assert list(got) == v[6:10]
+
+
+def test_uniform_mapping_is_open_interval():
+    # u = (k + 1/2) 2^-32 never reaches 0 or 1; checked at the two extreme words
+    # through the Uniform(0, 1) prior draw, whose value is exactly the mapping.
+    lo = (0 + 0.5) * 2.0 ** -32
+    hi = (2 ** 32 - 1 + 0.5) * 2.0 ** -32
+    assert 0.0 < lo < hi < 1.0
+    vals = [oracle.prior_draw(W.UNIFORM, 0.0, 1.0, seed=s, comp=0, particle=p, tag=1)
+            for s in range(3) for p in range(200)]
+    assert min(vals) > 0.0 and max(vals) < 1.0
+
+
+# --------------------------------------------------------------------------
+# Peak profiles (Eq. (1), Eq. (C1), Eq. (E1)): heights, half widths, areas
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eta", [0.0, 0.25, 0.7, 1.0])
+def test_pv_height_and_half_height(eta):
+    A, mu, s = 3.0, 1.7, 0.4
+    assert oracle.peak(PV, mu, A, mu, s, eta) == pytest.approx(A, rel=1e-15)
+    # both the Gaussian and the Lorentzian part are 1/2 at |x - mu| = HWHM
+    for x in (mu - s, mu + s):
+        assert oracle.peak(PV, x, A, mu, s, eta) == pytest.approx(A / 2, rel=1e-14)
+
+
+def test_gauss_lorentz_half_heights():
+    A, mu, w = 2.0, -0.3, 0.6
+    assert oracle.peak(GAUSS, mu, A, mu, w) == pytest.approx(A, rel=1e-15)
+    hw = w * math.sqrt(2 * math.log(2))
+    assert oracle.peak(GAUSS, mu + hw, A, mu, w) == pytest.approx(A / 2, rel=1e-14)
+    assert oracle.peak(LOR, mu + w, A, mu, w) == pytest.approx(A / 2, rel=1e-14)
+    assert oracle.peak(LOR, mu, A, mu, w) == pytest.approx(A, rel=1e-15)
+
+
+@pytest.mark.parametrize("fam,eta,area", [
+    (GAUSS, 0.0, lambda A, w, eta: A * w * math.sqrt(2 * math.pi)),
+    (LOR, 0.0, lambda A, w, eta: A * math.pi * w),
+    (PV, 0.3, lambda A, w, eta: A * (eta * w * math.sqrt(math.pi / math.log(2))
+                                     + (1 - eta) * math.pi * w)),
+    (PV, 0.9, lambda A, w, eta: A * (eta * w * math.sqrt(math.pi / math.log(2))
+                                     + (1 - eta) * math.pi * w)),
+])
+def test_peak_areas(fam, eta, area):
+    A, mu, w = 1.7, 0.4, 0.35
+    val, err = integrate.quad(lambda x: oracle.peak(fam, x, A, mu, w, eta), -np.inf, np.inf,
+                              limit=400, epsabs=1e-13, epsrel=1e-12)
+    assert val == pytest.approx(area(A, w, eta), rel=1e-9)
+
+
+def test_background_is_chebyshev_series():
+    # b(x) = sum c_j T_j(t) on x scaled to [-1, 1]: numpy's Chebyshev series
+    x = np.linspace(10.0, 90.0, 37)
+    c = np.array([3.0, -1.5, 0.7, 0.2, -0.05])
+    f = oracle.model(PV, 0, len(c), c, x)
+    t = (2 * x - (x.min() + x.max())) / (x.max() - x.min())
+    ref = np.polynomial.chebyshev.chebval(t, c)
+    np.testing.assert_allclose(f, ref, rtol=1e-13, atol=1e-13)
+
+
+def _mp_energy(fam, K, nbg, nat, x, y, s):
+    """Energy 1/2 sum ((y-f)/sigma)^2 in 50-digit arithmetic, peaks written
+    from Eq. (C1)/(E1) directly in mpmath."""
+    mpmath.mp.dps = 50
+    p = 4 if fam == PV else 3
+    xmin, xmax = mpmath.mpf(float(min(x))), mpmath.mpf(float(max(x)))
+    tot = mpmath.mpf(0)
+    for xi, yi, si in zip(x, y, s):
+        X = mpmath.mpf(float(xi))
+        f = mpmath.mpf(0)
+        for k in range(K):
+            A, mu, w = [mpmath.mpf(float(v)) for v in nat[p * k:p * k + 3]]
+            d2 = (X - mu) ** 2
+            if fam == GAUSS:
+                f += A * mpmath.e ** (-d2 / (2 * w * w))
+            else:
+                lor = w * w / (w * w + d2)
+                if fam == LOR:
+                    f += A * lor
+                else:
+                    eta = mpmath.mpf(float(nat[p * k + 3]))
+                    f += A * (eta * mpmath.e ** (-mpmath.log(2) * d2 / (w * w)) + (1 - eta) * lor)
+        t = (2 * X - (xmin + xmax)) / (xmax - xmin)
+        for j in range(nbg):
+            f += mpmath.mpf(float(nat[p * K + j])) * mpmath.chebyt(j, t)
+        r = (mpmath.mpf(float(yi)) - f) / mpmath.mpf(float(si))
+        tot += r * r / 2
+    return float(tot)
+
+
+@pytest.mark.parametrize("fam", [GAUSS, LOR, PV])
+def test_energy_brute_force_high_precision(fam):
+    rng = np.random.default_rng(11 + fam)
+    N, K, nbg = 8, 2, 2
+    x = np.sort(rng.uniform(0.0, 5.0, N))
+    s = rng.uniform(0.05, 0.2, N)
+    nat = []
+    for k in range(K):
+        nat += [rng.uniform(0.5, 2.0), rng.uniform(1.0, 4.0), rng.uniform(0.2, 0.8)]
+        if fam == PV:
+            nat.append(rng.uniform(0.0, 1.0))
+    nat += [0.3, -0.1]
+    y = rng.normal(1.0, 0.5, N)
+    e = oracle.energy_natural(fam, K, nbg, nat, x, y, s)
+    assert e == pytest.approx(_mp_energy(fam, K, nbg, nat, x, y, s), rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Prior draws: distributions (KS against scipy)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,p1,p2,dist,transform", [
+    (W.UNIFORM, -1.0, 3.0, stats.uniform(-1.0, 4.0), None),
+    (W.LOG_UNIFORM, 0.1, 3.0, stats.loguniform(0.1, 3.0), np.exp),
+    (W.NORMAL, 1.5, 0.2, stats.norm(1.5, 0.2), None),
+    (W.GAMMA, 2.0, 1.0, stats.gamma(2.0, scale=1.0), None),
+    (W.GAMMA, 5.0, 0.04, stats.gamma(5.0, scale=25.0), None),
+    (W.GAMMA, 0.5, 2.0, stats.gamma(0.5, scale=0.5), None),
+])
+def test_prior_draw_distributions(kind, p1, p2, dist, transform):
+    v = np.array([oracle.prior_draw(kind, p1, p2, seed=77, comp=3, particle=i, tag=2)
+                  for i in range(3000)])
+    if transform is not None:
+        v = transform(v)
+    assert stats.kstest(v, dist.cdf).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# ESS and the bisection (Eq. (10) weights)
+# --------------------------------------------------------------------------
+
+def test_ess_limits_and_monotonicity():
+    rng = np.random.default_rng(4)
+    e = rng.exponential(3.0, 500)
+    e -= e.min()
+    assert oracle.ess_frac(e, 0.0) == pytest.approx(1.0, rel=1e-15)
+    assert oracle.ess_frac(np.full(40, 2.5), 7.0) == pytest.approx(1.0, rel=1e-14)
+    vals = [oracle.ess_frac(e, d) for d in np.linspace(0, 5, 60)]
+    assert all(b <= a + 1e-15 for a, b in zip(vals, vals[1:]))
+    assert vals[-1] >= 1.0 / len(e)
+
+
+def test_bisection_exponential_closed_form():
+    # e_i = 10 x the quantiles of Exp(1): ESS/T -> (1+20d)/(1+10d)^2, which
+    # equals 1/2 at d = (1 + sqrt(2))/10.
+    T = 400000
+    e = -10.0 * np.log1p(-(np.arange(T) + 0.5) / T)
+    d, final, it = oracle.choose_delta(e, beta=0.0, rho=0.5)
+    assert not final
+    assert d == pytest.approx((1.0 + math.sqrt(2.0)) / 10.0, rel=2e-3)
+
+
+def test_bisection_bracket_property():
+    rng = np.random.default_rng(9)
+    for scale in (1e6, 1e3, 30.0):
+        e = rng.gamma(2.0, scale, 2048)
+        e -= e.min()
+        d, final, it = oracle.choose_delta(e, beta=0.0, rho=0.5)
+        assert not final
+        g = oracle.ess_frac(e, d)
+        assert 0.5 <= g <= 0.5 * (1 + 1e-6)
+        assert oracle.ess_frac(e, d * (1 + 3e-7)) < g + 1e-15
+
+
+def test_bisection_final_step_when_flat():
+    e = np.linspace(0.0, 1e-3, 100)
+    d, final, it = oracle.choose_delta(e, beta=0.6, rho=0.5)
+    assert final and d == pytest.approx(0.4, rel=0, abs=0)
+
+
+# --------------------------------------------------------------------------
+# Systematic resampling
+# --------------------------------------------------------------------------
+
+def test_quantise_is_exact():
+    w = np.array([1.0, 0.5, 2.0 ** -40, 2.0 ** -41, 0.3])
+    q = oracle.quantise(w)
+    assert list(q[:4]) == [2 ** 40, 2 ** 39, 1, 0]
+    assert int(q[4]) == math.floor(0.3 * 2 ** 40)
+
+
+@pytest.mark.parametrize("T,M", [(7, 7), (64, 64), (1000, 997), (300, 30)])
+def test_resample_offspring_bounds(T, M):
+    rng = np.random.default_rng(T + M)
+    q = oracle.quantise(rng.uniform(0, 1, T) ** 3)
+    Q = int(q.astype(object).sum())
+    for u32 in (0, 1, 2 ** 31, 2 ** 32 - 1, int(rng.integers(0, 2 ** 32))):
+        a = oracle.resample(q, M, u32)
+        assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < T
+        o = np.bincount(a, minlength=T)
+        assert o.sum() == M
+        for i in range(T):
+            lo = (M * int(q[i])) // Q
+            assert o[i] in (lo, lo + 1) or (o[i] == lo and M * int(q[i]) % Q == 0)
+            assert q[i] > 0 or o[i] == 0
+
+
+def test_resample_mean_offspring_is_proportional():
+    rng = np.random.default_rng(3)
+    T = M = 8
+    q = oracle.quantise(rng.uniform(0.05, 1, T))
+    Q = int(q.astype(object).sum())
+    K = 4096
+    acc = np.zeros(T)
+    for k in range(K):
+        acc += np.bincount(oracle.resample(q, M, (k << 32) // K), minlength=T)
+    np.testing.assert_allclose(acc / K, M * q.astype(np.float64) / Q, atol=M / K + 1e-12)
+
+
+def test_resample_matches_textbook_float_version():
+    # textbook systematic resampling: points (m + U)/M on the normalised CDF
+    rng = np.random.default_rng(12)
+    T = M = 5000
+    w = rng.uniform(0, 1, T) ** 4
+    q = oracle.quantise(w)
+    u32 = int(rng.integers(0, 2 ** 32))
+    a = oracle.resample(q, M, u32)
+    cdf = np.cumsum(q.astype(np.float64))
+    cdf /= cdf[-1]
+    pts = (np.arange(M) + (u32 + 0.0) / 2 ** 32) / M
+    ref = np.searchsorted(cdf, pts, side="right")
+    assert np.mean(a != ref) < 2e-3
+
+
+# --------------------------------------------------------------------------
+# Metropolis kernel: prior invariance at beta = 0; 1-D Gaussian target
+# --------------------------------------------------------------------------
+
+def test_mh_keeps_prior_at_beta_zero():
+    spec = W.gaussian_small(2)
+    opts = W.Options(particles=3000, sweeps=15, seed=5)
+    u0, E0 = oracle.init_particles(spec, 1, opts, 3000)
+    step = np.array([0.8, 2.5, 0.6])
+    u1, E1, acc, prop = oracle.mh_stage(spec, 1, opts, u0, E0, step, beta=0.0, stage=1)
+    assert np.all(acc > 0)
+    assert stats.kstest(u1[:, 0], stats.gamma(2.0).cdf).pvalue > 1e-3
+    assert stats.kstest(u1[:, 1], stats.uniform(0, 10).cdf).pvalue > 1e-3
+    assert stats.kstest(u1[:, 2], stats.uniform(math.log(0.1), math.log(30)).cdf).pvalue > 1e-3
+
+
+def _lin_gauss_posterior(x, y, s, mus, ws, m0, s0):
+    Phi = np.stack([np.exp(-(x - m) ** 2 / (2 * w * w)) for m, w in zip(mus, ws)], axis=1)
+    Sig = np.diag(s ** 2)
+    S0 = np.eye(len(mus)) * s0 ** 2
+    Cov = Sig + Phi @ S0 @ Phi.T
+    logz = stats.multivariate_normal(mean=Phi @ np.full(len(mus), m0), cov=Cov).logpdf(y)
+    Sp = np.linalg.inv(np.linalg.inv(S0) + Phi.T @ np.linalg.inv(Sig) @ Phi)
+    mp = Sp @ (Phi.T @ np.linalg.inv(Sig) @ y + np.linalg.inv(S0) @ np.full(len(mus), m0))
+    return logz, mp, Sp
+
+
+def test_mh_keeps_gaussian_posterior_invariant():
+    # Linear-Gaussian posterior of the two amplitudes (closed form): chains
+    # started from exact posterior draws must stay on it at beta = 1.
+    spec = W.linear_gaussian_case(3)
+    t = spec.truth
+    _, mp, Sp = _lin_gauss_posterior(spec.x, spec.y, spec.sigma, t["mu"], t["w"], t["m0"], t["s0"])
+    opts = W.Options(particles=4000, sweeps=20, seed=8)
+    rng = np.random.default_rng(21)
+    A0 = rng.multivariate_normal(mp, Sp, size=4000)
+    u0 = np.zeros((4000, 6))
+    u0[:, 0], u0[:, 3] = A0[:, 0], A0[:, 1]
+    u0[:, 1], u0[:, 2], u0[:, 4], u0[:, 5] = t["mu"][0], t["w"][0], t["mu"][1], t["w"][1]
+    E0 = oracle.energies(spec, 2, opts, u0)
+    sd = np.sqrt(np.diag(Sp))
+    step = np.array([2.38 * sd[0], 0, 0, 2.38 * sd[1], 0, 0])
+    u1, _, acc, prop = oracle.mh_stage(spec, 2, opts, u0, E0, step, beta=1.0, stage=1)
+    assert np.all(acc[[0, 3]] > 0.2 * prop[[0, 3]])
+    A = u1[:, [0, 3]]
+    se = sd / math.sqrt(4000)
+    assert np.all(np.abs(A.mean(0) - mp) < 5 * se)
+    np.testing.assert_allclose(A.std(0), sd, rtol=0.06)
+    np.testing.assert_allclose(np.corrcoef(A.T)[0, 1], Sp[0, 1] / (sd[0] * sd[1]), atol=0.05)
+
+
+# --------------------------------------------------------------------------
+# Evidence: closed form (linear-Gaussian), quadrature (K = 1), flat limit
+# --------------------------------------------------------------------------
+
+def test_evidence_linear_gaussian_closed_form():
+    spec = W.linear_gaussian_case(3)
+    t = spec.truth
+    exact, mp, Sp = _lin_gauss_posterior(spec.x, spec.y, spec.sigma, t["mu"], t["w"], t["m0"], t["s0"])
+    vals, means = [], []
+    for seed in range(1, 7):
+        r = oracle.run_job(spec, 2, W.Options(particles=2000, sweeps=8, seed=seed))
+        assert r["status"] == 0
+        vals.append(r["log_z"])
+        means.append(r["samples"][:, [0, 3]].mean(0))
+    vals = np.array(vals)
+    se = vals.std(ddof=1) / math.sqrt(len(vals))
+    assert abs(vals.mean() - exact) < max(0.05, 4 * se)
+    tol = 4 * np.sqrt(np.diag(Sp)) / math.sqrt(2000) + 2e-3
+    assert np.all(np.abs(np.mean(means, 0) - mp) < tol)
+
+
+def _log_lik_gauss(y, s, f):
+    return float(np.sum(-0.5 * ((y - f) / s) ** 2 - np.log(np.sqrt(2 * np.pi) * s)))
+
+
+def test_evidence_k1_quadrature_gamma_amplitude():
+    # mu and w fixed, A ~ Gamma(2, 1): Z = int Gamma(A) L(A) dA by adaptive quadrature
+    spec = W.tiny_single_peak(5)
+    mu, w = 0.9, 0.25
+    spec.comp_priors = [W.Prior(W.GAMMA, 2.0, 1.0), W.Prior(W.FIXED, mu), W.Prior(W.FIXED, w)]
+    phi = np.exp(-(spec.x - mu) ** 2 / (2 * w * w))
+    ll = lambda A: _log_lik_gauss(spec.y, spec.sigma, A * phi)
+    lmax = max(ll(A) for A in np.linspace(0.01, 5, 500))
+    Z, _ = integrate.quad(lambda A: stats.gamma(2.0).pdf(A) * math.exp(ll(A) - lmax), 0, 20,
+                          limit=400, points=[1.0, 1.2, 1.5], epsabs=0, epsrel=1e-11)
+    exact = math.log(Z) + lmax
+    vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"]
+            for s in range(1, 6)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
+
+
+def test_evidence_k1_quadrature_free_centre():
+    # w fixed, A ~ N(m0, s0^2), mu ~ U(0, 2): Z = int p(mu) Z_lin(mu) dmu
+    spec = W.tiny_single_peak(5)
+    w, m0, s0 = 0.25, 1.0, 0.5
+    spec.comp_priors = [W.Prior(W.NORMAL, m0, s0), W.Prior(W.UNIFORM, 0.0, 2.0), W.Prior(W.FIXED, w)]
+
+    def lz_lin(mu):
+        phi = np.exp(-(spec.x - mu) ** 2 / (2 * w * w))
+        cov = np.diag(spec.sigma ** 2) + s0 ** 2 * np.outer(phi, phi)
+        return stats.multivariate_normal(mean=m0 * phi, cov=cov).logpdf(spec.y)
+
+    grid = np.linspace(0, 2, 801)
+    lg = np.array([lz_lin(m) for m in grid])
+    lmax = lg.max()
+    Z, _ = integrate.quad(lambda m: 0.5 * math.exp(lz_lin(m) - lmax), 0, 2, limit=500,
+                          points=[float(grid[np.argmax(lg)])], epsabs=0, epsrel=1e-10)
+    exact = math.log(Z) + lmax
+    vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"]
+            for s in range(1, 6)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
+
+
+def test_flat_likelihood_single_stage():
+    spec = W.gaussian_small(1)
+    spec.sigma = np.full_like(spec.x, 1e6)
+    r = oracle.run_job(spec, 2, W.Options(particles=256, sweeps=2, seed=3))
+    c = -np.sum(np.log(np.sqrt(2 * np.pi) * spec.sigma))
+    assert r["n_stages"] == 1
+    assert abs(r["log_z"] - c) < 1e-8
+
+
+def test_posterior_over_k_is_softmax_of_evidence():
+    p = oracle.posterior_over_k([-3.0, -1.0, -1.0 - math.log(3.0)])
+    # exp(-F) weights 1 : e^2 : e^2/3 (uniform p(K), Eq. (2))
+    ref = np.array([math.exp(-2.0), 1.0, 1.0 / 3.0])
+    np.testing.assert_allclose(p, ref / ref.sum(), rtol=1e-14)
+
+
+def test_invalid_inputs_rejected():
+    spec = W.gaussian_small(1)
+    spec.sigma = spec.sigma.copy()
+    spec.sigma[5] = 0.0
+    r = oracle.run_job(spec, 1, W.Options(particles=64, sweeps=1))
+    assert r["status"] == oracle.EINVAL
+
+
+def test_waste_free_particle_count():
+    spec = W.gaussian_small(1)
+    r = oracle.run_job(spec, 1, W.Options(particles=100, sweeps=7, waste_free=1, seed=2))
+    assert r["status"] == 0
+    assert r["samples"].shape[0] == 15 * 7
