@@ -1,0 +1,170 @@
+/*
+ * smc.h -- C ABI of the B300 (sm_103a) tempered sequential Monte Carlo sampler
+ * for Bayesian peak-count selection and peak-parameter estimation.
+ *
+ * Method (the paper's Sec. II): for every candidate peak count K the sampler
+ * moves T particles from the prior (beta = 0) to the posterior (beta = 1)
+ * through the tempered sequence pi_l ~ p(D|theta)^beta_l p(theta) (Eq. (9)).
+ * Each stage reweights by the incremental weights of Eq. (10), accumulates
+ * log Z by Eq. (11), resamples and rejuvenates with component-wise random-walk
+ * Metropolis (Sec. II B 4).  The free energy is F(K) = -log Z (Eq. (3)) and
+ * the posterior over K follows Eq. (2).
+ *
+ * Forward model (Eq. (1)): f(x) = sum_k g_k(x) + b(x) with
+ *   SMC_GAUSS          g = A exp(-(x-mu)^2 / (2 w^2))          w: standard deviation
+ *   SMC_LORENTZ        g = A w^2 / (w^2 + (x-mu)^2)            w: HWHM
+ *   SMC_PSEUDO_VOIGT   g = A [eta exp(-ln2 (x-mu)^2/w^2)
+ *                             + (1-eta) w^2/(w^2 + (x-mu)^2)]   w: shared HWHM,
+ *                                                               eta: Gaussian fraction (Eq. (E1))
+ * and background b(x) = sum_j c_j T_j(t), T_j Chebyshev polynomials of the first
+ * kind, t = (2x - (x_min + x_max)) / (x_max - x_min).
+ * Components per job, in this order (the Metropolis sweep order): for each peak
+ * (A, mu, w[, eta]), then c_0 .. c_{nbg-1}.  d = p K + nbg, p = 3 or 4.
+ *
+ * Likelihood: Gaussian with known per-point sigma_i.  Energy
+ * E(theta) = 1/2 sum_i ((y_i - f_i)/sigma_i)^2; the returned log Z includes the
+ * normaliser -sum_i log(sqrt(2 pi) sigma_i), so log Z is the log marginal
+ * likelihood of Eq. (5) and F = -log Z.
+ *
+ * Errors: every call returns an int status (SMC_OK = 0 or an SMC_E* code).
+ * On error nothing is allocated on the caller's behalf and output arguments
+ * are left untouched.  smc_strerror() gives a static message.
+ *
+ * Threading: one smc_ctx may be used from several threads; calls are
+ * serialised internally.  smc_submit / smc_poll / smc_wait are the serving
+ * interface: submitted requests run concurrently on the device with
+ * continuous batching (admitted as slots and the memory budget free up).
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SMC_MAX_BG 8     /* background coefficients (polynomial degree <= 7) */
+#define SMC_MAX_DIM 64   /* components per job: p K + nbg <= 64               */
+#define SMC_MAX_K 16     /* peaks per job                                     */
+
+typedef struct smc_ctx smc_ctx;
+typedef uint64_t smc_job;
+
+enum smc_status {
+    SMC_OK = 0,
+    SMC_EINVAL = 1,       /* invalid argument (sizes, priors, sigma <= 0, ...)     */
+    SMC_ENOMEM = 2,       /* device or host allocation failed / over budget        */
+    SMC_ECUDA = 3,        /* a CUDA runtime call failed                            */
+    SMC_ETIMEOUT = 4,     /* smc_wait ran out of time                              */
+    SMC_EMAXSTAGES = 5,   /* beta did not reach 1 within max_stages                */
+    SMC_ENOTREADY = 6,    /* result requested before the job finished              */
+    SMC_ECANCELLED = 7,   /* request cancelled (context destroyed while queued)    */
+    SMC_ENUMERIC = 8      /* every particle's energy is non-finite                 */
+};
+
+enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2 };
+enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3 };
+
+/* Prior kinds.  Sampling coordinates: log v for LOG_UNIFORM, v otherwise.
+ *   SMC_UNIFORM      p1 = lower, p2 = upper
+ *   SMC_LOG_UNIFORM  log v ~ U(log p1, log p2), 0 < p1 < p2
+ *   SMC_NORMAL       p1 = mean, p2 = standard deviation
+ *   SMC_GAMMA        p1 = shape, p2 = rate            (App. C and D priors)
+ *   SMC_FIXED        v = p1, never proposed
+ * Centres accept UNIFORM, NORMAL or FIXED; widths must have positive support. */
+enum smc_prior_kind { SMC_UNIFORM = 0, SMC_LOG_UNIFORM = 1, SMC_NORMAL = 2, SMC_GAMMA = 3, SMC_FIXED = 4 };
+
+typedef struct {
+    int32_t kind;
+    double p1, p2;
+} smc_prior;
+
+/* Shared priors for every peak (peaks are exchangeable in Eq. (1)) and one per
+ * background coefficient.  If n_comp > 0, comp[0..n_comp) gives one prior per
+ * component instead (requires k_min == k_max and n_comp == d). */
+typedef struct {
+    smc_prior amp, centre, width, eta, bg[SMC_MAX_BG];
+    const smc_prior *comp;
+    int32_t n_comp;
+} smc_priors;
+
+typedef struct {
+    int32_t device;           /* CUDA device ordinal                                 */
+    size_t mem_budget_bytes;  /* device bytes the context may hold (0 = 80% of free) */
+    void *cuda_stream;        /* cudaStream_t to run on (NULL = a private stream)    */
+} smc_create_opts;
+
+typedef struct {
+    int64_t particles;    /* T, particles per candidate K (2 .. 2^24)              */
+    double ess_target;    /* rho: next beta keeps ESS >= rho T (0 < rho < 1)       */
+    int32_t sweeps;       /* n, Metropolis sweeps per stage                        */
+    int32_t waste_free;   /* 1: resample ceil(T/n) chains, keep every sweep (Sec. II B 3) */
+    int32_t energy_fp64;  /* 1: plain FP64 path, one job per launch sequence       */
+    uint64_t seed;        /* Philox key                                            */
+    int32_t max_stages;   /* cap on tempering stages (SMC_EMAXSTAGES beyond)       */
+    int32_t keep_samples; /* 1: copy the final particle set to the host            */
+} smc_options;
+
+/* One spectrum and its candidate range, for smc_run_batch / smc_submit. */
+typedef struct {
+    const double *x, *y, *sigma;  /* n points each (host, or device if flagged)  */
+    int64_t n;
+    int32_t k_min, k_max;
+    int32_t family, bg, bg_degree;
+    const smc_priors *priors;
+    const smc_options *opts;
+} smc_request;
+
+/* Result of one spectrum: arrays indexed by K - k_min.  Views are owned by the
+ * context and stay valid until smc_release(job). */
+typedef struct {
+    int32_t k_min, k_max;
+    int32_t dim_max;              /* row stride of post_mean / post_sd / samples       */
+    int32_t status;               /* SMC_OK or the first failing job's status         */
+    const double *log_z;          /* [nK] log marginal likelihood, F = -log_z          */
+    const double *p_k;            /* [nK] posterior over K, uniform p(K) (Eq. (2))      */
+    const int32_t *n_stages;      /* [nK] tempering stages used                        */
+    const int32_t *job_status;    /* [nK]                                              */
+    const double *post_mean;      /* [nK][dim_max] natural values, peaks sorted by mu  */
+    const double *post_sd;        /* [nK][dim_max]                                     */
+    const float *samples;         /* [nK][n_samples][dim_max] natural values, or NULL  */
+    int64_t n_samples;            /* particles per K in the final set                  */
+    double latency_ms;            /* submit (or run start) to completion, host clock   */
+} smc_result_view;
+
+/* Create / destroy a context bound to one device. */
+int smc_create(smc_ctx **out, const smc_create_opts *opts);
+int smc_destroy(smc_ctx *ctx);
+
+/* Blocking run of one spectrum over K = k_min..k_max.  x, y, sigma are host
+ * arrays of n doubles, copied at call time.  *out receives a job handle whose
+ * result is read with smc_result and freed with smc_release. */
+int smc_run(smc_ctx *ctx, const double *x, const double *y, const double *sigma, int64_t n,
+            int32_t k_min, int32_t k_max, int32_t family, int32_t bg, int32_t bg_degree,
+            const smc_priors *priors, const smc_options *opts, smc_job *out);
+
+/* Blocking run of several spectra in one batched launch sequence (every
+ * (spectrum, K) job advances in the same kernels).  If inputs_on_device is 1,
+ * the x/y/sigma pointers are device pointers on the context's device.
+ * out[i] receives the handle of reqs[i]. */
+int smc_run_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, int32_t inputs_on_device,
+                  smc_job *out);
+
+/* Serving: enqueue a request (host arrays, copied at call time) and return at
+ * once.  Requests are admitted by the memory budget and run with continuous
+ * batching; their particle state stays on the device until retirement. */
+int smc_submit(smc_ctx *ctx, const smc_request *req, smc_job *out);
+int smc_poll(smc_ctx *ctx, smc_job job, int32_t *done);
+int smc_wait(smc_ctx *ctx, smc_job job, double timeout_s);
+
+int smc_result(smc_ctx *ctx, smc_job job, smc_result_view *out);
+int smc_release(smc_ctx *ctx, smc_job job);
+
+const char *smc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

@@ -1,0 +1,64 @@
+/*
+ * smc_kernels.h -- step-level entry points of the sampler, for parity testing
+ * and profiling of each kernel on its own.  They run exactly the kernels that
+ * smc_run launches, on a temporary one-job set, and copy results back.
+ *
+ * All array arguments are HOST arrays (copied in and out by the call).
+ * Particles are passed as natural parameter values, row-major [count][d],
+ * components in the order documented in smc.h.  `precision` selects the
+ * kernel family: 0 = the FP32-energy batched kernels, 1 = the plain FP64 ones.
+ * Every call returns an SMC_* status and leaves outputs untouched on error.
+ */
+#ifndef SMC_KERNELS_H
+#define SMC_KERNELS_H
+
+#include "smc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32-10 (Salmon et al., SC'11) evaluated on the device:
+ * out[4i..4i+3] = Philox(ctr[4i..4i+3], key = (seed lo, seed hi)), i < n. */
+int smc_k_philox(smc_ctx *ctx, uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n);
+
+/* Energy E = 1/2 sum ((y - f)/sigma)^2 of `count` particles for the model of
+ * spec with K peaks (forward model Eq. (1); Gaussian likelihood, App. C Eq. (C2)).
+ * spec->priors fixes each component's sampling coordinate. */
+int smc_k_energy(smc_ctx *ctx, const smc_request *spec, int32_t K, const double *nat,
+                 int64_t count, int32_t precision, double *E_out);
+
+/* Prior draws at beta = 0 (Eq. (9)) for particles 0..count-1 with spec->opts->seed:
+ * natural values [count][d] and their energies. */
+int smc_k_prior(smc_ctx *ctx, const smc_request *spec, int32_t K, int64_t count,
+                int32_t precision, double *nat_out, double *E_out);
+
+/* Tempering step for energies E[T] at inverse temperature beta: the increment
+ * delta from the ESS bisection (ESS >= rho T), the log-evidence increment
+ * log mean exp(-delta E) (Eq. (11)), whether the step reached beta = 1, and the
+ * integer-quantised weights q[T] = floor(exp(-delta (E - min E)) 2^40) used by
+ * the resampler (q_out may be NULL).  precision 0 rounds E to FP32 first. */
+int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double rho,
+                   int32_t precision, double *delta, double *logz_inc, int32_t *final_step,
+                   uint64_t *q_out);
+
+/* Systematic resampling of M ancestors from integer weights q[T] with the
+ * uniform word u32: a_m = min{i : C_i > floor((m Q + floor(u32 Q / 2^32)) / M)},
+ * C the inclusive prefix sum of q, Q = C_{T-1}. */
+int smc_k_resample(smc_ctx *ctx, const uint64_t *q, int64_t T, int64_t M, uint32_t u32,
+                   int32_t *anc);
+
+/* One Metropolis stage (Sec. II B 4) on S chain starts at inverse temperature
+ * beta and stage counter `stage`, with step sizes step[d] in sampling
+ * coordinates and spec->opts->sweeps sweeps.  Outputs the chains' final (or,
+ * if waste_free, every sweep's) states and energies, and per-component accept
+ * and proposal counts acc[d], prop[d]. */
+int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const double *nat_start,
+                   const double *E_start, int64_t S, const double *step, double beta,
+                   uint32_t stage, int32_t precision, double *nat_out, double *E_out,
+                   int64_t *acc, int64_t *prop);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_KERNELS_H */

@@ -1,0 +1,479 @@
+// k_mh.cu -- fused FP32 Metropolis rejuvenation (Sec. II B 4).
+//
+// One chain is owned by a group of G warps; its N grid points are spread over
+// the group's lanes (J points per lane, point i = 32 g + lane + 32 G jj), and
+// the chain's residual r_i = y_i - f_i stays in registers for the whole stage.
+// A component-wise random-walk proposal (Sec. II B 4) therefore costs one pass
+// over the lane's points and one group reduction:
+//   dE = 1/2 sum_i w_i D_i (D_i - 2 r_i),   D_i = g'_i - g_i (change of the peak)
+// which is E(theta') - E(theta) of the Gaussian energy (App. C Eq. (C2)).
+// Within a peak's block of components the unit-amplitude shapes of the peak
+// (the Gaussian and Lorentzian parts) are cached per point, so amplitude and
+// mixing-ratio proposals need no transcendental at all and centre / width
+// proposals need one EX2 (+ one RCP for Lorentzian parts) per point.
+//
+// Random numbers: Philox4x32-10, counter (t d + j, chain, stage, K).  At the
+// start of a sweep lane j draws component j's proposal (words 0,1 -> Box-Muller
+// normal, word 2 -> accept uniform) and folds the prior ratio into a threshold;
+// proposal j is accepted iff thr_j < -beta dE.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace smc {
+
+constexpr int MH_MAX_GROUPS = 8;
+
+template <int FAM>
+__device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, float &S1)
+{
+    const float t = (x - mu) * sc;
+    const float t2 = t * t;
+    if (FAM == FAM_GAUSS) {
+        S0 = ex2_approx(-t2);
+    } else if (FAM == FAM_LORENTZ) {
+        S0 = rcp_approx(1.0f + t2);
+    } else {
+        const float L = rcp_approx(1.0f + t2);
+        S0 = ex2_approx(-t2) - L;  // Gaussian minus Lorentzian part
+        S1 = L;
+    }
+}
+
+// unit-amplitude profile from the cached shapes
+template <int FAM>
+__device__ __forceinline__ float unit(float S0, float S1, float eta)
+{
+    return FAM == FAM_PV ? fmaf(eta, S0, S1) : S0;
+}
+
+struct GroupCtx {
+    int lane, gw, grp, G;
+    float *red;  // [2][G] for this group
+    int par;
+};
+
+__device__ __forceinline__ void group_sync(const GroupCtx &g)
+{
+    if (g.G == 1)
+        __syncwarp();
+    else
+        named_barrier(1 + g.grp, 32 * g.G);
+}
+
+__device__ __forceinline__ float group_sum(GroupCtx &g, float v)
+{
+    v = warp_sum(v);
+    if (g.G == 1) return v;
+    float *slot = g.red + g.par * MH_MAX_GROUPS;
+    if (g.lane == 0) slot[g.gw] = v;
+    named_barrier(1 + g.grp, 32 * g.G);
+    float s = 0.0f;
+    for (int w = 0; w < g.G; ++w) s += slot[w];
+    g.par ^= 1;
+    return s;
+}
+
+// Kahan-compensated energy 1/2 sum w r^2 over the group
+template <int J>
+__device__ __forceinline__ float group_energy(GroupCtx &g, const float *w, const float *r)
+{
+    float s = 0.0f, c = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        const float term = 0.5f * w[jj] * r[jj] * r[jj];
+        const float yk = term - c;
+        const float tk = s + yk;
+        c = (tk - s) - yk;
+        s = tk;
+    }
+    c = -c;
+    warp_sum2(s, c);
+    if (g.G == 1) return s + c;
+    float *slot = g.red + g.par * MH_MAX_GROUPS;
+    if (g.lane == 0) slot[g.gw] = s + c;
+    named_barrier(1 + g.grp, 32 * g.G);
+    // compensated sum of the warps' totals in a fixed order
+    float S = 0.0f, Cc = 0.0f;
+    for (int w2 = 0; w2 < g.G; ++w2) {
+        const float yk = slot[w2] - Cc;
+        const float tk = S + yk;
+        Cc = (tk - S) - yk;
+        S = tk;
+    }
+    g.par ^= 1;
+    return S - Cc;
+}
+
+__device__ __forceinline__ float sel(int h, float a0, float a1) { return h ? a1 : a0; }
+
+template <int FAM, int J>
+__global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots,
+                                               int nslots, int G)
+{
+    __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
+    __shared__ int work_sh[MH_MAX_GROUPS][2];
+    GroupCtx g;
+    g.lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    g.G = G;
+    g.grp = warp / G;
+    g.gw = warp - g.grp * G;
+    g.par = 0;
+    const int ngroups = (blockDim.x >> 5) / G;
+    if (g.grp >= ngroups) return;
+    g.red = &red_sh[g.grp][0][0];
+    const int lane = g.lane;
+    constexpr int P = (FAM == FAM_PV) ? 4 : 3;
+
+    int li = 0;
+    for (;;) {
+        // ---- claim the next chain (dynamic scheduling over the bucket's jobs)
+        int slot = -1, m = 0;
+        if (g.gw == 0 && lane == 0) {
+            while (li < nslots) {
+                const int sl = slots[li];
+                JobDev &jq = jobs[sl];
+                if (jq.state == JOB_ACTIVE && jq.status == 0) {
+                    const int c = atomicAdd(&jq.next_chain, 1);
+                    if (c < jq.S) {
+                        slot = sl;
+                        m = c;
+                        break;
+                    }
+                }
+                ++li;
+            }
+            if (G > 1) {
+                work_sh[g.grp][0] = slot;
+                work_sh[g.grp][1] = m;
+            }
+        }
+        if (G == 1) {
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            m = __shfl_sync(FULL_MASK, m, 0);
+        } else {
+            named_barrier(1 + g.grp, 32 * G);
+            slot = work_sh[g.grp][0];
+            m = work_sh[g.grp][1];
+            named_barrier(1 + g.grp, 32 * G);
+        }
+        if (slot < 0) break;
+
+        const JobDev &jb = jobs[slot];
+        const int K = jb.K, d = jb.d, nbg = jb.nbg, S = jb.S, T = jb.T, n = jb.sweeps;
+        const int wf = jb.waste_free;
+        const float beta = (float)jb.beta;
+        const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
+        const unsigned long long seed = jb.seed;
+
+        // ---- grid points of this lane
+        float x[J], w[J], r[J], S0[J], S1[J], N0[J], N1[J];
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            const int i = g.gw * 32 + lane + jj * 32 * G;
+            x[jj] = __ldg(jb.xc + i);
+            w[jj] = __ldg(jb.wt + i);
+            r[jj] = __ldg(jb.y + i);
+        }
+        // ---- components held by this lane (j = lane, lane + 32)
+        float th[2], nat[2], stp[2];
+        int kind[2];
+        float plo[2], phi[2], pa[2], pb[2];
+        unsigned acc[2] = {0u, 0u}, prp[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < d) {
+                const PriorDev &pr = jb.pri[j];
+                kind[h] = pr.kind;
+                plo[h] = pr.lof;
+                phi[h] = pr.hif;
+                pa[h] = pr.a;
+                pb[h] = pr.b;
+                th[h] = jb.ths[(size_t)j * S + m];
+                nat[h] = natural_f(pr, th[h]);
+                stp[h] = jb.stepf[j];
+            } else {
+                kind[h] = PR_FIXED;
+                th[h] = nat[h] = stp[h] = plo[h] = phi[h] = pa[h] = pb[h] = 0.0f;
+            }
+        }
+        // ---- residual r = y - f(theta)
+        for (int k = 0; k < K; ++k) {
+            const int j0 = k * P;
+            const float A = __shfl_sync(FULL_MASK, sel(j0 >> 5, nat[0], nat[1]), j0 & 31);
+            const float mu = __shfl_sync(FULL_MASK, sel((j0 + 1) >> 5, nat[0], nat[1]), (j0 + 1) & 31);
+            const float wd = __shfl_sync(FULL_MASK, sel((j0 + 2) >> 5, nat[0], nat[1]), (j0 + 2) & 31);
+            float eta = 0.0f;
+            if (FAM == FAM_PV) eta = __shfl_sync(FULL_MASK, sel((j0 + 3) >> 5, nat[0], nat[1]), (j0 + 3) & 31);
+            const float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+                float a0, a1 = 0.0f;
+                shape<FAM>(x[jj], mu, sc, a0, a1);
+                r[jj] -= A * unit<FAM>(a0, a1, eta);
+            }
+        }
+        for (int q = 0; q < nbg; ++q) {
+            const int jq = K * P + q;
+            const float cq = __shfl_sync(FULL_MASK, sel(jq >> 5, nat[0], nat[1]), jq & 31);
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+                const int i = g.gw * 32 + lane + jj * 32 * G;
+                const float t = __ldg(jb.ts + i);
+                float a = 1.0f, b = t, tq = 1.0f;
+                if (q == 1) tq = t;
+                for (int e = 2; e <= q; ++e) {
+                    tq = fmaf(2.0f * t, b, -a);
+                    a = b;
+                    b = tq;
+                }
+                r[jj] -= cq * tq;
+            }
+        }
+
+        for (int sw = 0; sw < n; ++sw) {
+            // ---- this lane's proposals for the sweep
+            float thr[2], un[2], vn[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                thr[h] = INFINITY;
+                un[h] = vn[h] = 0.0f;
+                if (kind[h] != PR_FIXED) {
+                    const uint4 wv = draw(seed, (uint32_t)(sw * d + j), (uint32_t)m, stage, tag);
+                    const float z = box_muller_f(wv.x, wv.y);
+                    const float lu = logf(u01f(wv.z));
+                    const float u = fmaf(stp[h], z, th[h]);
+                    prp[h] += 1u;
+                    un[h] = u;
+                    bool ok;
+                    if (kind[h] == PR_UNIFORM || kind[h] == PR_LOG_UNIFORM)
+                        ok = u >= plo[h] && u <= phi[h];
+                    else if (kind[h] == PR_GAMMA)
+                        ok = u > 0.0f;
+                    else
+                        ok = true;
+                    if (ok) {
+                        float dlp = 0.0f;
+                        if (kind[h] == PR_NORMAL) {
+                            const float z1 = (u - pa[h]) / pb[h], z0 = (th[h] - pa[h]) / pb[h];
+                            dlp = -0.5f * (z1 * z1 - z0 * z0);
+                        } else if (kind[h] == PR_GAMMA) {
+                            dlp = (pa[h] - 1.0f) * (logf(u) - logf(th[h])) - pb[h] * (u - th[h]);
+                        }
+                        thr[h] = lu - dlp;
+                        vn[h] = kind[h] == PR_LOG_UNIFORM ? expf(u) : u;
+                    }
+                }
+            }
+
+            // ---- peak blocks
+            for (int k = 0; k < K; ++k) {
+                const int j0 = k * P;
+                float A = __shfl_sync(FULL_MASK, sel(j0 >> 5, nat[0], nat[1]), j0 & 31);
+                float mu = __shfl_sync(FULL_MASK, sel((j0 + 1) >> 5, nat[0], nat[1]), (j0 + 1) & 31);
+                float wd = __shfl_sync(FULL_MASK, sel((j0 + 2) >> 5, nat[0], nat[1]), (j0 + 2) & 31);
+                float eta = 0.0f;
+                if (FAM == FAM_PV)
+                    eta = __shfl_sync(FULL_MASK, sel((j0 + 3) >> 5, nat[0], nat[1]), (j0 + 3) & 31);
+                float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj) {
+                    S1[jj] = 0.0f;
+                    shape<FAM>(x[jj], mu, sc, S0[jj], S1[jj]);
+                }
+                for (int c = 0; c < P; ++c) {
+                    const int j = j0 + c, src = j & 31, h = j >> 5;
+                    const float tj = __shfl_sync(FULL_MASK, sel(h, thr[0], thr[1]), src);
+                    if (tj == INFINITY) continue;  // fixed or outside the prior's support
+                    const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
+                    float part = 0.0f;
+                    if (c == 0) {  // amplitude: D = (A' - A) u
+                        const float dA = v - A;
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) {
+                            const float D = dA * unit<FAM>(S0[jj], S1[jj], eta);
+                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                        }
+                    } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
+                        const float dd = A * (v - eta);
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) {
+                            const float D = dd * S0[jj];
+                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                        }
+                    } else {  // centre or width: new shape
+                        const float mu2 = (c == 1) ? v : mu;
+                        const float sc2 = (c == 2) ? ((FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v) : sc;
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) {
+                            N1[jj] = 0.0f;
+                            shape<FAM>(x[jj], mu2, sc2, N0[jj], N1[jj]);
+                            const float D = A * (unit<FAM>(N0[jj], N1[jj], eta) - unit<FAM>(S0[jj], S1[jj], eta));
+                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                        }
+                    }
+                    const float dE = 0.5f * group_sum(g, part);
+                    if (tj < -beta * dE) {
+                        if (c == 0) {
+#pragma unroll
+                            for (int jj = 0; jj < J; ++jj) r[jj] -= (v - A) * unit<FAM>(S0[jj], S1[jj], eta);
+                            A = v;
+                        } else if (c == 3) {
+                            const float dd = A * (v - eta);
+#pragma unroll
+                            for (int jj = 0; jj < J; ++jj) r[jj] -= dd * S0[jj];
+                            eta = v;
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < J; ++jj) {
+                                r[jj] -= A * (unit<FAM>(N0[jj], N1[jj], eta) - unit<FAM>(S0[jj], S1[jj], eta));
+                                S0[jj] = N0[jj];
+                                S1[jj] = N1[jj];
+                            }
+                            if (c == 1)
+                                mu = v;
+                            else {
+                                wd = v;
+                                sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v;
+                            }
+                        }
+                        if (lane == src) {
+                            th[h] = sel(h, un[0], un[1]);
+                            nat[h] = v;
+                            acc[h] += 1u;
+                        }
+                    }
+                }
+            }
+            // ---- background coefficients: D = (c' - c) T_q(t)
+            for (int q = 0; q < nbg; ++q) {
+                const int j = K * P + q, src = j & 31, h = j >> 5;
+                const float tj = __shfl_sync(FULL_MASK, sel(h, thr[0], thr[1]), src);
+                if (tj == INFINITY) continue;
+                const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
+                const float cq = __shfl_sync(FULL_MASK, sel(h, nat[0], nat[1]), src);
+                const float dc = v - cq;
+                float part = 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj) {
+                    const int i = g.gw * 32 + lane + jj * 32 * G;
+                    const float t = __ldg(jb.ts + i);
+                    float a = 1.0f, b = t, tq = 1.0f;
+                    if (q == 1) tq = t;
+                    for (int e = 2; e <= q; ++e) {
+                        tq = fmaf(2.0f * t, b, -a);
+                        a = b;
+                        b = tq;
+                    }
+                    N0[jj] = dc * tq;
+                    part = fmaf(w[jj] * N0[jj], fmaf(-2.0f, r[jj], N0[jj]), part);
+                }
+                const float dE = 0.5f * group_sum(g, part);
+                if (tj < -beta * dE) {
+#pragma unroll
+                    for (int jj = 0; jj < J; ++jj) r[jj] -= N0[jj];
+                    if (lane == src) {
+                        th[h] = sel(h, un[0], un[1]);
+                        nat[h] = v;
+                        acc[h] += 1u;
+                    }
+                }
+            }
+            if (wf) {
+                const float E = group_energy<J>(g, w, r);
+                const size_t o = (size_t)m * n + sw;
+                if (g.gw == 0) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = lane + 32 * h;
+                        if (j < d) jb.th[(size_t)j * T + o] = th[h];
+                    }
+                    if (lane == 0) jb.E[o] = E;
+                }
+            }
+        }
+        if (!wf) {
+            const float E = group_energy<J>(g, w, r);
+            if (g.gw == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = lane + 32 * h;
+                    if (j < d) jb.th[(size_t)j * T + m] = th[h];
+                }
+                if (lane == 0) jb.E[m] = E;
+            }
+        }
+        if (g.gw == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j < d && kind[h] != PR_FIXED) {
+                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)acc[h]);
+                    atomicAdd(&jobs[slot].prop[j], (unsigned long long)prp[h]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tiles and launch
+// ---------------------------------------------------------------------------
+typedef void (*mh_fn)(JobDev *, const int *, int, int);
+
+template <int FAM>
+static mh_fn pick_j(int J)
+{
+    switch (J) {
+    case 4: return k_mh<FAM, 4>;
+    case 8: return k_mh<FAM, 8>;
+    case 12: return k_mh<FAM, 12>;
+    case 16: return k_mh<FAM, 16>;
+    case 24: return FAM == FAM_PV ? nullptr : k_mh<FAM, 24>;
+    case 32: return FAM == FAM_PV ? nullptr : k_mh<FAM, 32>;
+    default: return nullptr;
+    }
+}
+
+static mh_fn pick(int family, int J)
+{
+    if (family == FAM_GAUSS) return pick_j<FAM_GAUSS>(J);
+    if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ>(J);
+    return pick_j<FAM_PV>(J);
+}
+
+static int block_threads(int G) { return 32 * (G < 4 ? 4 : G); }
+
+bool mh_tile_supported(int family, int J, int G)
+{
+    return pick(family, J) != nullptr && (G == 1 || G == 2 || G == 4 || G == 8);
+}
+
+int mh_resident_grid(int family, int J, int G)
+{
+    mh_fn f = pick(family, J);
+    if (!f) return 0;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)f, block_threads(G), 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
+                      int grid, cudaStream_t s)
+{
+    mh_fn f = pick(family, J);
+    if (!f || !(G == 1 || G == 2 || G == 4 || G == 8)) return cudaErrorInvalidValue;
+    if (nslots <= 0) return cudaSuccess;
+    if (grid <= 0) grid = mh_resident_grid(family, J, G);
+    f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots, G);
+    return cudaGetLastError();
+}
+
+}  // namespace smc

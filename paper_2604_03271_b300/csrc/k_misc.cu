@@ -1,0 +1,392 @@
+// k_misc.cu -- prior draws, full energies, particle copy, stage bookkeeping,
+// posterior summaries.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.h"
+#include "plain_device.cuh"
+
+namespace smc {
+
+// ---------------------------------------------------------------------------
+// Philox words (for parity tests of the generator itself)
+// ---------------------------------------------------------------------------
+__global__ void k_philox(unsigned long long seed, const uint4 *ctr, uint4 *out, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox10(ctr[i], (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n,
+                          cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int b = 256;
+    k_philox<<<(unsigned)((n + b - 1) / b), b, 0, s>>>(seed, (const uint4 *)ctr, (uint4 *)out, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Prior draws at beta_0 = 0 (start of the tempered sequence, Eq. (9)).
+// Counter (256 j + attempt, particle, 0, K); Gamma by Marsaglia & Tsang (2000)
+// with the u^(1/shape) boost below shape 1.  Draws are made in FP64.
+// ---------------------------------------------------------------------------
+__device__ double prior_draw(const PriorDev &p, unsigned long long seed, uint32_t j, uint32_t i,
+                             uint32_t tag)
+{
+    uint4 w;
+    switch (p.kind) {
+    case PR_UNIFORM:
+        w = draw(seed, 256u * j, i, 0u, tag);
+        return p.p1 + (p.p2 - p.p1) * u01d(w.x);
+    case PR_LOG_UNIFORM:
+        w = draw(seed, 256u * j, i, 0u, tag);
+        return p.lo + (p.hi - p.lo) * u01d(w.x);
+    case PR_NORMAL:
+        w = draw(seed, 256u * j, i, 0u, tag);
+        return p.p1 + p.p2 * box_muller_d(w.x, w.y);
+    case PR_GAMMA: {
+        const double a = p.p1 < 1.0 ? p.p1 + 1.0 : p.p1;
+        const double dd = a - 1.0 / 3.0;
+        const double cc = 1.0 / sqrt(9.0 * dd);
+        for (uint32_t att = 0; att < 256u; ++att) {
+            w = draw(seed, 256u * j + att, i, 0u, tag);
+            const double z = box_muller_d(w.x, w.y);
+            const double t = 1.0 + cc * z;
+            if (t <= 0.0) continue;
+            const double v = t * t * t;
+            if (log(u01d(w.z)) < 0.5 * z * z + dd - dd * v + dd * log(v)) {
+                double g = dd * v;
+                if (p.p1 < 1.0) g *= pow(u01d(w.w), 1.0 / p.p1);
+                return g / p.p2;
+            }
+        }
+        return dd / p.p2;
+    }
+    default: return p.p1;  // FIXED
+    }
+}
+
+__global__ void k_prior_init(JobDev *jobs, const int *slots)
+{
+    JobDev &jb = jobs[slots[blockIdx.y]];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= jb.T) return;
+    for (int j = 0; j < jb.d; ++j) {
+        const double v = prior_draw(jb.pri[j], jb.seed, (uint32_t)j, (uint32_t)i, jb.tag);
+        if (jb.fp64)
+            jb.th64[(size_t)j * jb.T + i] = v;
+        else
+            jb.th[(size_t)j * jb.T + i] = (float)v;
+    }
+}
+
+cudaError_t launch_prior_init(JobDev *jobs, const int *slots, int nslots, int max_T,
+                              cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    const int b = 128;
+    dim3 g((max_T + b - 1) / b, nslots);
+    k_prior_init<<<g, b, 0, s>>>(jobs, slots);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Full energy E = 1/2 sum_i w_i r_i^2, r = y - f (forward model Eq. (1)).
+// FP32 jobs: one warp per particle, lanes stride over grid points, FP32
+// Kahan-compensated per lane and a compensated butterfly across lanes.
+// ---------------------------------------------------------------------------
+template <int FAM>
+__device__ __forceinline__ float peak_eval(float x, float A, float mu, float s, float eta)
+{
+    const float dx = x - mu;
+    const float t = dx * s;  // s = 1/(w sqrt(2 ln 2)) for GAUSS, 1/HWHM otherwise
+    const float t2 = t * t;
+    if (FAM == FAM_GAUSS) return A * ex2_approx(-t2);
+    const float L = rcp_approx(1.0f + t2);
+    if (FAM == FAM_LORENTZ) return A * L;
+    const float G = ex2_approx(-t2);
+    return A * fmaf(eta, G - L, L);
+}
+
+template <int FAM>
+__device__ __forceinline__ float energy_warp(const JobDev &jb, const float *P)
+{
+    const int lane = threadIdx.x & 31;
+    const int K = jb.K, p = jb.p, nbg = jb.nbg;
+    float s = 0.0f, c = 0.0f;
+    for (int pt = lane; pt < jb.n_pad; pt += 32) {
+        const float x = jb.xc[pt];
+        float f = 0.0f;
+        for (int k = 0; k < K; ++k)
+            f += peak_eval<FAM>(x, P[k * p], P[k * p + 1], P[k * p + 2],
+                                FAM == FAM_PV ? P[k * p + 3] : 0.0f);
+        if (nbg > 0) {
+            const float t = jb.ts[pt];
+            float a = 1.0f, b = t;
+            f = fmaf(P[p * K], a, f);
+            if (nbg > 1) f = fmaf(P[p * K + 1], b, f);
+            for (int q = 2; q < nbg; ++q) {
+                const float cn = fmaf(2.0f * t, b, -a);
+                a = b;
+                b = cn;
+                f = fmaf(P[p * K + q], b, f);
+            }
+        }
+        const float r = jb.y[pt] - f;
+        const float term = 0.5f * jb.wt[pt] * r * r;
+        const float yk = term - c;  // Kahan: running sum s, lost low part -c
+        const float tk = s + yk;
+        c = (tk - s) - yk;
+        s = tk;
+    }
+    c = -c;
+    warp_sum2(s, c);
+    return s + c;
+}
+
+__global__ void __launch_bounds__(256) k_energy_f32(JobDev *jobs, const int *slots)
+{
+    __shared__ float par[8][SMC_DMAX];
+    JobDev &jb = jobs[slots[blockIdx.y]];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= jb.T) return;
+    const int K = jb.K, p = jb.p, d = jb.d;
+    float *P = par[wib];
+    // natural parameters of this particle, widths turned into inverse scales
+    for (int j = lane; j < d; j += 32) {
+        float v = natural_f(jb.pri[j], jb.th[(size_t)j * jb.T + i]);
+        if (j < p * K && j % p == 2) v = (jb.family == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v;
+        P[j] = v;
+    }
+    __syncwarp();
+    float e;
+    if (jb.family == FAM_GAUSS)
+        e = energy_warp<FAM_GAUSS>(jb, P);
+    else if (jb.family == FAM_LORENTZ)
+        e = energy_warp<FAM_LORENTZ>(jb, P);
+    else
+        e = energy_warp<FAM_PV>(jb, P);
+    if (lane == 0) jb.E[i] = e;
+}
+
+// FP64 jobs: one thread per particle.
+__global__ void k_energy_f64(JobDev *jobs, const int *slots)
+{
+    const JobDev &jb = jobs[slots[blockIdx.y]];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= jb.T) return;
+    double nat[SMC_DMAX];
+    for (int j = 0; j < jb.d; ++j) nat[j] = natural_d(jb.pri[j], jb.th64[(size_t)j * jb.T + i]);
+    jb.E64[i] = energy_plain(jb, nat);
+}
+
+cudaError_t launch_energy(JobDev *jobs, const int *slots, int nslots, int max_T, bool fp64,
+                          cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    if (fp64) {
+        dim3 g((max_T + 127) / 128, nslots);
+        k_energy_f64<<<g, 128, 0, s>>>(jobs, slots);
+        return cudaGetLastError();
+    }
+    dim3 g((unsigned)(((long long)max_T * 32 + 255) / 256), nslots);
+    k_energy_f32<<<g, 256, 0, s>>>(jobs, slots);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Particle copy: chain starts ths[:, m] = th[:, anc[m]], Es[m] = E[anc[m]]
+// (the resampling of Sec. II B 2).  Component-major layout: writes are
+// coalesced, reads follow the non-decreasing ancestors.
+// ---------------------------------------------------------------------------
+template <typename P>
+__global__ void __launch_bounds__(256) k_gather(JobDev *jobs, const int *slots)
+{
+    const JobDev &jb = jobs[slots[blockIdx.y]];
+    if (jb.state != JOB_ACTIVE || jb.status != 0) return;
+    const int S = jb.S, T = jb.T, d = jb.d;
+    const P *th = (const P *)(jb.fp64 ? (const void *)jb.th64 : (const void *)jb.th);
+    const P *E = (const P *)(jb.fp64 ? (const void *)jb.E64 : (const void *)jb.E);
+    P *ths = (P *)(jb.fp64 ? (void *)jb.ths64 : (void *)jb.ths);
+    P *Es = (P *)(jb.fp64 ? (void *)jb.Es64 : (void *)jb.Es);
+    const int *anc = jb.anc;
+    const long long total = (long long)S * (d + 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / S);
+        const int m = (int)(e - (long long)j * S);
+        const int a = __ldg(anc + m);
+        if (j < d)
+            ths[(size_t)j * S + m] = __ldg(th + (size_t)j * T + a);
+        else
+            Es[m] = __ldg(E + a);
+    }
+}
+
+cudaError_t launch_gather(JobDev *jobs, const int *slots, int nslots, int64_t max_elems,
+                          bool fp64, cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    long long blocks = (max_elems + 255) / 256;
+    if (blocks > 8 * 148) blocks = 8 * 148;
+    if (blocks < 1) blocks = 1;
+    dim3 g((unsigned)blocks, nslots);
+    if (fp64)
+        k_gather<double><<<g, 256, 0, s>>>(jobs, slots);
+    else
+        k_gather<float><<<g, 256, 0, s>>>(jobs, slots);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// End of a stage iteration: advance counters, retire finished jobs, count the
+// jobs still active (for the host loop).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_stage_end(JobDev *jobs, const int *slots, int nslots,
+                                                    int *n_active, int *n_active_host)
+{
+    __shared__ int red[32];
+    int cnt = 0;
+    for (int a = threadIdx.x; a < nslots; a += blockDim.x) {
+        JobDev &jb = jobs[slots[a]];
+        if (jb.state != JOB_ACTIVE) continue;
+        if (jb.status != 0) {
+            jb.state = JOB_DONE;
+            continue;
+        }
+        jb.stage += 1;
+        if (jb.final_step) {
+            jb.state = JOB_DONE;
+            continue;
+        }
+        if (jb.stage >= jb.max_stages) {
+            jb.status = 5;  // SMC_EMAXSTAGES
+            jb.state = JOB_DONE;
+            continue;
+        }
+        ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *n_active = t;
+        if (n_active_host) *(volatile int *)n_active_host = t;
+    }
+}
+
+cudaError_t launch_stage_end(JobDev *jobs, const int *slots, int nslots, int *n_active,
+                             int *n_active_host, cudaStream_t s)
+{
+    k_stage_end<<<1, 1024, 0, s>>>(jobs, slots, nslots, n_active, n_active_host);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Posterior summaries of the final (equally weighted) particle set: each
+// sample's peaks are ordered by centre (peaks are exchangeable in Eq. (1)),
+// then mean and population SD per component in FP64; optional FP32 copy of the
+// natural values as samples [T][dim_stride] (unsorted).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_natural(const JobDev &jb, int i, double *v)
+{
+    for (int j = 0; j < jb.d; ++j) {
+        const double u =
+            jb.fp64 ? jb.th64[(size_t)j * jb.T + i] : (double)jb.th[(size_t)j * jb.T + i];
+        double x = natural_d(jb.pri[j], u);
+        if (jb.pri[j].is_centre) x += jb.x_ref;
+        v[j] = x;
+    }
+}
+
+__device__ __forceinline__ void sort_peaks(const JobDev &jb, const double *v, int *perm)
+{
+    for (int k = 0; k < jb.K; ++k) perm[k] = k;
+    for (int k = 1; k < jb.K; ++k) {
+        const int pk = perm[k];
+        const double key = v[pk * jb.p + 1];
+        int m = k - 1;
+        while (m >= 0 && v[perm[m] * jb.p + 1] > key) {
+            perm[m + 1] = perm[m];
+            --m;
+        }
+        perm[m + 1] = pk;
+    }
+}
+
+__device__ __forceinline__ double sorted_value(const JobDev &jb, const double *v, const int *perm,
+                                               int j)
+{
+    if (j < jb.p * jb.K) return v[perm[j / jb.p] * jb.p + j % jb.p];
+    return v[j];
+}
+
+__device__ double block_sum_d(double x, double *red)
+{
+    x = warp_sum_d(x);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_finalize(JobDev *jobs, const int *slots, double *mean,
+                                                  double *sd, float *samples, int dstride,
+                                                  long long sstride)
+{
+    __shared__ double red[8];
+    __shared__ double mu[SMC_DMAX];
+    const JobDev &jb = jobs[slots[blockIdx.x]];
+    const int T = jb.T, d = jb.d;
+    double v[SMC_DMAX], acc[SMC_DMAX];
+    int perm[SMC_KMAX];
+    for (int j = 0; j < d; ++j) acc[j] = 0.0;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        load_natural(jb, i, v);
+        if (samples) {
+            float *row = samples + blockIdx.x * sstride + (long long)i * dstride;
+            for (int j = 0; j < d; ++j) row[j] = (float)v[j];
+        }
+        sort_peaks(jb, v, perm);
+        for (int j = 0; j < d; ++j) acc[j] += sorted_value(jb, v, perm, j);
+    }
+    for (int j = 0; j < d; ++j) {
+        const double t = block_sum_d(acc[j], red);
+        if (threadIdx.x == 0) mu[j] = t / T;
+    }
+    __syncthreads();
+    for (int j = 0; j < d; ++j) acc[j] = 0.0;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        load_natural(jb, i, v);
+        sort_peaks(jb, v, perm);
+        for (int j = 0; j < d; ++j) {
+            const double t = sorted_value(jb, v, perm, j) - mu[j];
+            acc[j] += t * t;
+        }
+    }
+    for (int j = 0; j < d; ++j) {
+        const double t = block_sum_d(acc[j], red);
+        if (threadIdx.x == 0) {
+            mean[(size_t)blockIdx.x * dstride + j] = mu[j];
+            sd[(size_t)blockIdx.x * dstride + j] = sqrt(t / T);
+        }
+    }
+}
+
+cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, double *mean,
+                            double *sd, float *samples, int dim_stride, int64_t sample_stride,
+                            cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    k_finalize<<<nslots, 256, 0, s>>>(jobs, slots, mean, sd, samples, dim_stride,
+                                      (long long)sample_stride);
+    return cudaGetLastError();
+}
+
+}  // namespace smc

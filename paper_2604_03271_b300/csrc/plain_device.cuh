@@ -1,0 +1,49 @@
+// plain_device.cuh -- FP64 forward model and energy of the plain path.
+// One thread evaluates a whole particle: sum over the grid of the K peaks
+// (Eq. (1)) and the Chebyshev background, E = 1/2 sum ((y - f)/sigma)^2.
+#pragma once
+#include "smc_device.cuh"
+
+__device__ __forceinline__ double peak_eval_d(int fam, double x, double A, double mu, double w,
+                                              double eta)
+{
+    const double dx = x - mu;
+    if (fam == FAM_GAUSS) return A * exp(-dx * dx / (2.0 * w * w));
+    const double lor = w * w / (w * w + dx * dx);
+    if (fam == FAM_LORENTZ) return A * lor;
+    const double sg = w / sqrt(2.0 * 0.69314718055994530942);
+    return A * (eta * exp(-dx * dx / (2.0 * sg * sg)) + (1.0 - eta) * lor);
+}
+
+__device__ __forceinline__ double energy_plain(const JobDev &jb, const double *nat)
+{
+    double e = 0.0;
+    for (int pt = 0; pt < jb.n; ++pt) {
+        const double x = jb.x64[pt];
+        double f = 0.0;
+        for (int k = 0; k < jb.K; ++k) {
+            const double *q = nat + jb.p * k;
+            f += peak_eval_d(jb.family, x, q[0], q[1], q[2], jb.p == 4 ? q[3] : 0.0);
+        }
+        if (jb.nbg > 0) {
+            const double t = x * jb.t_scale + jb.t_off;
+            double a = 1.0, b = t;
+            for (int q = 0; q < jb.nbg; ++q) {
+                double tq;
+                if (q == 0)
+                    tq = 1.0;
+                else if (q == 1)
+                    tq = t;
+                else {
+                    tq = 2.0 * t * b - a;
+                    a = b;
+                    b = tq;
+                }
+                f += nat[jb.p * jb.K + q] * tq;
+            }
+        }
+        const double r = (jb.y64[pt] - f) * jb.is64[pt];
+        e += 0.5 * r * r;
+    }
+    return e;
+}
