@@ -1,0 +1,648 @@
+// engine.cpp -- requests, device memory, the batched stage loop and the
+// serving loop behind the C ABI.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace smc {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? SMC_OK : (e == cudaErrorMemoryAllocation ? SMC_ENOMEM : SMC_ECUDA); }
+
+#define CK(expr)                                  \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return cuda_status(_e); \
+    } while (0)
+
+static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int peak_params(int family) { return family == SMC_PSEUDO_VOIGT ? 4 : 3; }
+static int bg_params(int bg, int deg)
+{
+    switch (bg) {
+    case SMC_BG_NONE: return 0;
+    case SMC_BG_CONST: return 1;
+    case SMC_BG_LINEAR: return 2;
+    default: return deg + 1;
+    }
+}
+int job_dim(int family, int K, int bg, int deg) { return peak_params(family) * K + bg_params(bg, deg); }
+
+// ---------------------------------------------------------------------------
+// Tile of the fused Metropolis kernel: J points per lane, G warps per chain,
+// 32 G J >= N.  Chosen to minimise padding, then the number of warps per chain.
+// ---------------------------------------------------------------------------
+Tile choose_tile(int family, int n)
+{
+    static const int Js_pv[] = {4, 8, 12, 16};
+    static const int Js_gl[] = {4, 8, 12, 16, 24, 32};
+    const int *Js = family == SMC_PSEUDO_VOIGT ? Js_pv : Js_gl;
+    const int nJ = family == SMC_PSEUDO_VOIGT ? 4 : 6;
+    Tile best{0, 0};
+    long best_pad = -1;
+    for (int G : {1, 2, 4, 8})
+        for (int a = 0; a < nJ; ++a) {
+            const int J = Js[a];
+            const long pad = 32L * G * J;
+            if (pad < n) continue;
+            if (J > 16 && G > 1) continue;  // large J only for one-warp chains
+            if (best_pad < 0 || pad < best_pad || (pad == best_pad && G < best.G)) {
+                best = {J, G};
+                best_pad = pad;
+            }
+        }
+    return best;
+}
+
+static bool prior_ok(const smc_prior &p, int role)  // role: 0 amp, 1 centre, 2 width, 3 eta, 4 bg
+{
+    if (!std::isfinite(p.p1) || (p.kind != SMC_FIXED && !std::isfinite(p.p2))) return false;
+    switch (p.kind) {
+    case SMC_UNIFORM:
+        if (!(p.p1 < p.p2)) return false;
+        if (role == 2 && !(p.p1 > 0.0)) return false;
+        return true;
+    case SMC_LOG_UNIFORM: return role != 1 && p.p1 > 0.0 && p.p1 < p.p2;
+    case SMC_NORMAL: return role != 2 && p.p2 > 0.0;
+    case SMC_GAMMA: return role != 1 && p.p1 > 0.0 && p.p2 > 0.0;
+    case SMC_FIXED: return role != 2 || p.p1 > 0.0;
+    default: return false;
+    }
+}
+
+static smc_prior comp_prior(const Request &r, int K, int j)
+{
+    if (!r.comp.empty()) return r.comp[j];
+    const int p = r.p;
+    if (j < p * K) {
+        switch (j % p) {
+        case 0: return r.pri.amp;
+        case 1: return r.pri.centre;
+        case 2: return r.pri.width;
+        default: return r.pri.eta;
+        }
+    }
+    return r.pri.bg[j - p * K];
+}
+
+static int comp_role(const Request &r, int K, int j)
+{
+    if (j < r.p * K) return j % r.p;
+    return 4;
+}
+
+int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
+{
+    (void)c;
+    if (!rq.priors || !rq.opts || !rq.x || !rq.y || !rq.sigma) return SMC_EINVAL;
+    const smc_options &o = *rq.opts;
+    if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
+    if (rq.family < 0 || rq.family > 2 || rq.bg < 0 || rq.bg > 3) return SMC_EINVAL;
+    if (rq.bg == SMC_BG_POLY && (rq.bg_degree < 0 || rq.bg_degree >= SMC_MAX_BG)) return SMC_EINVAL;
+    if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
+    if (job_dim(rq.family, rq.k_max, rq.bg, rq.bg_degree) > SMC_MAX_DIM) return SMC_EINVAL;
+    if (o.particles < 2 || o.particles > (1 << 24) || o.sweeps < 1 || o.sweeps > 100000) return SMC_EINVAL;
+    if (!(o.ess_target > 0.0 && o.ess_target < 1.0) || o.max_stages < 1) return SMC_EINVAL;
+    if (o.waste_free) {
+        const int64_t S = (o.particles + o.sweeps - 1) / o.sweeps;
+        if (S * o.sweeps > (1 << 24) || S < 2) return SMC_EINVAL;
+    }
+    Request *r = new Request();
+    r->k_min = rq.k_min;
+    r->k_max = rq.k_max;
+    r->family = rq.family;
+    r->bg = rq.bg;
+    r->bg_degree = rq.bg_degree;
+    r->nbg = bg_params(rq.bg, rq.bg_degree);
+    r->p = peak_params(rq.family);
+    r->n = (int)rq.n;
+    r->opts = o;
+    r->pri = *rq.priors;
+    r->fp64 = o.energy_fp64 != 0;
+    if (rq.priors->n_comp > 0) {
+        if (!rq.priors->comp || rq.k_min != rq.k_max ||
+            rq.priors->n_comp != job_dim(rq.family, rq.k_min, rq.bg, rq.bg_degree)) {
+            delete r;
+            return SMC_EINVAL;
+        }
+        r->comp.assign(rq.priors->comp, rq.priors->comp + rq.priors->n_comp);
+    }
+    r->pri.comp = nullptr;
+    r->pri.n_comp = 0;
+    for (int K = r->k_min; K <= r->k_max; ++K) {
+        const int d = job_dim(r->family, K, r->bg, r->bg_degree);
+        for (int j = 0; j < d; ++j)
+            if (!prior_ok(comp_prior(*r, K, j), comp_role(*r, K, j))) {
+                delete r;
+                return SMC_EINVAL;
+            }
+    }
+    if (!r->fp64) {
+        r->tile = choose_tile(r->family, r->n);
+        if (r->tile.J == 0) {
+            delete r;
+            return SMC_EINVAL;  // grid too long for the FP32 tiles
+        }
+        r->n_pad = 32 * r->tile.G * r->tile.J;
+    } else {
+        r->n_pad = r->n;
+    }
+    if (on_device) {
+        r->dx = rq.x;
+        r->dy = rq.y;
+        r->ds = rq.sigma;
+    } else {
+        r->hx.assign(rq.x, rq.x + rq.n);
+        r->hy.assign(rq.y, rq.y + rq.n);
+        r->hs.assign(rq.sigma, rq.sigma + rq.n);
+        for (int i = 0; i < r->n; ++i)
+            if (!std::isfinite(r->hx[i]) || !std::isfinite(r->hy[i]) || !std::isfinite(r->hs[i]) ||
+                !(r->hs[i] > 0.0)) {
+                delete r;
+                return SMC_EINVAL;
+            }
+    }
+    out = r;
+    return SMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device memory of a request: one arena for the spectrum and results, one per job.
+// ---------------------------------------------------------------------------
+struct SpecLayout {
+    size_t raw, x64, y64, is64, xc, wt, y, ts, scal, slots, off, pk, mean, sd, samples, total;
+};
+
+static SpecLayout spec_layout(const Request &r, int64_t T_out)
+{
+    SpecLayout L{};
+    const size_t n = r.n, np = r.n_pad, nK = r.k_max - r.k_min + 1;
+    const size_t dmax = std::max(1, job_dim(r.family, r.k_max, r.bg, r.bg_degree));
+    size_t o = 0;
+    L.raw = o;  o += al(3 * n * 8);
+    L.x64 = o;  o += al(n * 8);
+    L.y64 = o;  o += al(n * 8);
+    L.is64 = o; o += al(n * 8);
+    L.xc = o;   o += al(np * 4);
+    L.wt = o;   o += al(np * 4);
+    L.y = o;    o += al(np * 4);
+    L.ts = o;   o += al(np * 4);
+    L.scal = o; o += al(sizeof(SpecScal));
+    L.slots = o; o += al(nK * 4);
+    L.off = o;  o += al(2 * 4);
+    L.pk = o;   o += al(nK * 8);
+    L.mean = o; o += al(nK * dmax * 8);
+    L.sd = o;   o += al(nK * dmax * 8);
+    L.samples = o;
+    if (r.opts.keep_samples) o += al(nK * (size_t)T_out * dmax * 4);
+    L.total = o;
+    return L;
+}
+
+struct JobLayout {
+    size_t th, E, ths, Es, w64, q, anc, lam, step, stepf, acc, prop, pri, total;
+};
+
+static JobLayout job_layout(int d, int64_t T, int64_t S, bool fp64)
+{
+    JobLayout L{};
+    const size_t e = fp64 ? 8 : 4, dd = std::max(d, 1);
+    size_t o = 0;
+    L.th = o;   o += al(dd * T * e);
+    L.E = o;    o += al(T * e);
+    L.ths = o;  o += al(dd * S * e);
+    L.Es = o;   o += al(S * e);
+    L.w64 = o;  o += al(T * 8);
+    L.q = o;    o += al(T * 8);
+    L.anc = o;  o += al(S * 4);
+    L.lam = o;  o += al(dd * 8);
+    L.step = o; o += al(dd * 8);
+    L.stepf = o; o += al(dd * 4);
+    L.acc = o;  o += al(dd * 8);
+    L.prop = o; o += al(dd * 8);
+    L.pri = o;  o += al(dd * sizeof(PriorDev));
+    L.total = o;
+    return L;
+}
+
+static void chains(const Request &r, int64_t &T, int64_t &S)
+{
+    const int64_t n = r.opts.sweeps;
+    if (r.opts.waste_free) {
+        S = (r.opts.particles + n - 1) / n;
+        T = S * n;
+    } else {
+        S = T = r.opts.particles;
+    }
+}
+
+size_t request_bytes(const Request &r)
+{
+    int64_t T, S;
+    chains(r, T, S);
+    size_t b = spec_layout(r, T).total;
+    for (int K = r.k_min; K <= r.k_max; ++K)
+        b += job_layout(job_dim(r.family, K, r.bg, r.bg_degree), T, S, r.fp64).total;
+    return b;
+}
+
+static PriorDev to_dev(const smc_prior &p, int is_centre)
+{
+    PriorDev d{};
+    d.kind = p.kind;
+    d.is_centre = is_centre;
+    d.p1 = p.p1;
+    d.p2 = p.p2;
+    d.lo = -INFINITY;
+    d.hi = INFINITY;
+    if (p.kind == SMC_UNIFORM) {
+        d.lo = p.p1;
+        d.hi = p.p2;
+    } else if (p.kind == SMC_LOG_UNIFORM) {
+        d.lo = std::log(p.p1);
+        d.hi = std::log(p.p2);
+    }
+    d.lof = (float)d.lo;
+    d.hif = (float)d.hi;
+    d.a = (float)p.p1;
+    d.b = (float)p.p2;
+    return d;
+}
+
+void free_request_device(Ctx &c, Request &r)
+{
+    for (size_t a = 0; a < r.slots.size(); ++a) {
+        const int sl = r.slots[a];
+        c.h_jobs[sl].state = JOB_FREE;
+        c.free_slots.push_back(sl);
+        if (r.job_arena[a]) cudaFreeAsync(r.job_arena[a], c.stream);
+        c.used -= r.job_bytes[a];
+    }
+    r.slots.clear();
+    r.job_arena.clear();
+    r.job_bytes.clear();
+    if (r.spec_arena) {
+        cudaFreeAsync(r.spec_arena, c.stream);
+        c.used -= r.spec_bytes;
+        r.spec_arena = nullptr;
+    }
+}
+
+// Allocate, upload and prepare a request's spectrum and jobs, then draw the
+// prior particles and their energies.  T_override / S_override replace the
+// particle counts (step-level entry points).
+int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
+{
+    int64_t T, S;
+    chains(r, T, S);
+    if (T_override > 0) {
+        T = T_override;
+        S = S_override > 0 ? S_override : T_override;
+    }
+    const int nK = r.k_max - r.k_min + 1;
+    if ((int)c.free_slots.size() < nK) return SMC_ENOMEM;
+    const SpecLayout SL = spec_layout(r, T);
+    size_t need = SL.total;
+    for (int K = r.k_min; K <= r.k_max; ++K)
+        need += job_layout(job_dim(r.family, K, r.bg, r.bg_degree), T, S, r.fp64).total;
+    if (c.used + need > c.budget) return SMC_ENOMEM;
+
+    char *sa = nullptr;
+    CK(cudaMallocAsync((void **)&sa, SL.total, c.stream));
+    r.spec_arena = sa;
+    r.spec_bytes = SL.total;
+    c.used += SL.total;
+    r.sd.xc = (float *)(sa + SL.xc);
+    r.sd.wt = (float *)(sa + SL.wt);
+    r.sd.y = (float *)(sa + SL.y);
+    r.sd.ts = (float *)(sa + SL.ts);
+    r.sd.x64 = (double *)(sa + SL.x64);
+    r.sd.y64 = (double *)(sa + SL.y64);
+    r.sd.is64 = (double *)(sa + SL.is64);
+    r.sd.scal = (SpecScal *)(sa + SL.scal);
+    const double *ix = r.dx, *iy = r.dy, *is = r.ds;
+    if (!ix) {
+        double *raw = (double *)(sa + SL.raw);
+        CK(cudaMemcpyAsync(raw, r.hx.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(raw + r.n, r.hy.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(raw + 2 * r.n, r.hs.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
+        ix = raw;
+        iy = raw + r.n;
+        is = raw + 2 * r.n;
+    }
+    CK(launch_spec_prep(ix, iy, is, r.n, r.n_pad, r.fp64 ? 0 : 1, r.sd, c.stream));
+
+    std::vector<int> slots;
+    for (int K = r.k_min; K <= r.k_max; ++K) {
+        const int d = job_dim(r.family, K, r.bg, r.bg_degree);
+        const JobLayout JL = job_layout(d, T, S, r.fp64);
+        char *ja = nullptr;
+        CK(cudaMallocAsync((void **)&ja, JL.total, c.stream));
+        c.used += JL.total;
+        const int sl = c.free_slots.back();
+        c.free_slots.pop_back();
+        r.slots.push_back(sl);
+        r.job_arena.push_back(ja);
+        r.job_bytes.push_back(JL.total);
+        slots.push_back(sl);
+
+        std::vector<PriorDev> pri(std::max(d, 1));
+        for (int j = 0; j < d; ++j) {
+            const int role = comp_role(r, K, j);
+            pri[j] = to_dev(comp_prior(r, K, j), role == 1 ? 1 : 0);
+        }
+        CK(cudaMemcpyAsync(ja + JL.pri, pri.data(), sizeof(PriorDev) * std::max(d, 1),
+                           cudaMemcpyHostToDevice, c.stream));
+        std::vector<double> lam(std::max(d, 1), 2.38);
+        CK(cudaMemcpyAsync(ja + JL.lam, lam.data(), 8 * lam.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemsetAsync(ja + JL.acc, 0, 8 * std::max(d, 1), c.stream));
+        CK(cudaMemsetAsync(ja + JL.prop, 0, 8 * std::max(d, 1), c.stream));
+        JobDev jb{};
+        jb.xc = r.sd.xc;
+        jb.wt = r.sd.wt;
+        jb.y = r.sd.y;
+        jb.ts = r.sd.ts;
+        jb.x64 = r.sd.x64;
+        jb.y64 = r.sd.y64;
+        jb.is64 = r.sd.is64;
+        jb.n = r.n;
+        jb.n_pad = r.n_pad;
+        jb.family = r.family;
+        jb.K = K;
+        jb.p = r.p;
+        jb.nbg = r.nbg;
+        jb.d = d;
+        jb.J = r.tile.J;
+        jb.G = r.tile.G;
+        jb.T = (int)T;
+        jb.S = (int)S;
+        jb.sweeps = r.opts.sweeps;
+        jb.waste_free = r.opts.waste_free ? 1 : 0;
+        jb.fp64 = r.fp64 ? 1 : 0;
+        if (r.fp64) {
+            jb.th64 = (double *)(ja + JL.th);
+            jb.E64 = (double *)(ja + JL.E);
+            jb.ths64 = (double *)(ja + JL.ths);
+            jb.Es64 = (double *)(ja + JL.Es);
+        } else {
+            jb.th = (float *)(ja + JL.th);
+            jb.E = (float *)(ja + JL.E);
+            jb.ths = (float *)(ja + JL.ths);
+            jb.Es = (float *)(ja + JL.Es);
+        }
+        jb.w64 = (double *)(ja + JL.w64);
+        jb.q = (unsigned long long *)(ja + JL.q);
+        jb.anc = (int *)(ja + JL.anc);
+        jb.lam = (double *)(ja + JL.lam);
+        jb.step = (double *)(ja + JL.step);
+        jb.stepf = (float *)(ja + JL.stepf);
+        jb.acc = (unsigned long long *)(ja + JL.acc);
+        jb.prop = (unsigned long long *)(ja + JL.prop);
+        jb.pri = (const PriorDev *)(ja + JL.pri);
+        jb.beta = 0.0;
+        jb.rho = r.opts.ess_target;
+        jb.stage = 0;
+        jb.max_stages = r.opts.max_stages;
+        jb.status = 0;
+        jb.state = JOB_ACTIVE;
+        jb.seed = r.opts.seed;
+        jb.tag = (unsigned)K;
+        c.h_jobs[sl] = jb;
+        CK(cudaMemcpyAsync(c.d_jobs + sl, &c.h_jobs[sl], sizeof(JobDev), cudaMemcpyHostToDevice,
+                           c.stream));
+    }
+    int *dslots = (int *)(sa + SL.slots);
+    CK(cudaMemcpyAsync(dslots, slots.data(), 4 * nK, cudaMemcpyHostToDevice, c.stream));
+    const int off[2] = {0, nK};
+    CK(cudaMemcpyAsync(sa + SL.off, off, 8, cudaMemcpyHostToDevice, c.stream));
+    CK(launch_job_setup(c.d_jobs, dslots, r.sd.scal, nK, c.stream));
+    CK(launch_prior_init(c.d_jobs, dslots, nK, (int)T, c.stream));
+    CK(launch_energy(c.d_jobs, dslots, nK, (int)T, r.fp64, c.stream));
+    // pageable sources of the copies above must stay valid until consumed
+    CK(cudaStreamSynchronize(c.stream));
+    return SMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stage loop.
+// ---------------------------------------------------------------------------
+struct Bucket {
+    int family, J, G;
+    std::vector<int> slots;
+};
+
+struct Plan {
+    std::vector<int> all;
+    std::vector<Bucket> buckets;
+    std::vector<size_t> boff;
+    std::vector<int> grids;
+    int64_t max_elems = 0;
+    int max_stages = 1;
+};
+
+// Slot lists of every FP32 job of the requests: all jobs (per-job kernels)
+// and one list per Metropolis tile bucket, uploaded to the device list area.
+static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
+{
+    for (Request *r : reqs) {
+        if (r->fp64) continue;
+        for (int sl : r->slots) {
+            P.all.push_back(sl);
+            const JobDev &jb = c.h_jobs[sl];
+            P.max_elems = std::max<int64_t>(P.max_elems, (int64_t)jb.S * (jb.d + 1));
+            P.max_stages = std::max(P.max_stages, jb.max_stages);
+            Bucket *b = nullptr;
+            for (Bucket &x : P.buckets)
+                if (x.family == jb.family && x.J == jb.J && x.G == jb.G) b = &x;
+            if (!b) {
+                P.buckets.push_back({jb.family, jb.J, jb.G, {}});
+                b = &P.buckets.back();
+            }
+            b->slots.push_back(sl);
+        }
+    }
+    if (P.all.empty()) return SMC_OK;
+    // costliest chains first inside each bucket (dynamic scheduling drains them first)
+    for (Bucket &b : P.buckets)
+        std::stable_sort(b.slots.begin(), b.slots.end(), [&](int a, int z) {
+            const JobDev &A = c.h_jobs[a], &Z = c.h_jobs[z];
+            return (long)A.d * A.sweeps > (long)Z.d * Z.sweeps;
+        });
+    std::vector<int> host_lists(P.all);
+    for (Bucket &b : P.buckets) {
+        P.boff.push_back(host_lists.size());
+        host_lists.insert(host_lists.end(), b.slots.begin(), b.slots.end());
+        P.grids.push_back(mh_resident_grid(b.family, b.J, b.G));
+    }
+    if ((int)host_lists.size() > LIST_AREA) return SMC_ENOMEM;
+    CK(cudaMemcpyAsync(c.d_lists, host_lists.data(), 4 * host_lists.size(), cudaMemcpyHostToDevice,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return SMC_OK;
+}
+
+// One tempering stage of every active job of the plan.
+static cudaError_t iteration(Ctx &c, const Plan &P)
+{
+    const int nall = (int)P.all.size();
+    cudaError_t e;
+    if ((e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream)) != cudaSuccess) return e;
+    if ((e = launch_resample(c.d_jobs, c.d_lists, nall, c.stream)) != cudaSuccess) return e;
+    if ((e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream)) != cudaSuccess)
+        return e;
+    for (size_t b = 0; b < P.buckets.size(); ++b)
+        if ((e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
+                           P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b],
+                           c.stream)) != cudaSuccess)
+            return e;
+    return launch_stage_end(c.d_jobs, c.d_lists, nall, c.d_nactive, c.h_nactive_dev, c.stream);
+}
+
+int run_chunk(Ctx &c, std::vector<Request *> &reqs, int iters)
+{
+    Plan P;
+    int st = build_plan(c, reqs, P);
+    if (st != SMC_OK || P.all.empty()) return st;
+    for (int k = 0; k < iters; ++k) CK(iteration(c, P));
+    CK(cudaStreamSynchronize(c.stream));
+    return SMC_OK;
+}
+
+static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
+{
+    Plan P;
+    int st = build_plan(c, reqs, P);
+    if (st != SMC_OK || P.all.empty()) return st;
+    // capture a few stages into a CUDA graph and replay it until no job is active
+    const int chunk = 4;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = iteration(c, P);
+        cudaError_t e2 = cudaStreamEndCapture(c.stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+            use_graph = false;
+    } else {
+        use_graph = false;
+    }
+    cudaGetLastError();
+    const int max_iters = P.max_stages + 8;
+    int done_iters = 0;
+    int status = SMC_OK;
+    while (done_iters < max_iters) {
+        cudaError_t e;
+        if (use_graph) {
+            e = cudaGraphLaunch(exec, c.stream);
+            done_iters += chunk;
+        } else {
+            e = iteration(c, P);
+            done_iters += 1;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) {
+            status = cuda_status(e);
+            break;
+        }
+        if (*(volatile int *)c.h_nactive == 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return status;
+}
+
+static int run_fp64(Ctx &c, Request &r)
+{
+    // plain path: one job at a time, one launch sequence per stage, the host
+    // checks completion after every stage
+    int *list = c.d_lists;
+    for (int sl : r.slots) {
+        CK(cudaMemcpyAsync(list, &sl, 4, cudaMemcpyHostToDevice, c.stream));
+        const JobDev &jb = c.h_jobs[sl];
+        const int64_t elems = (int64_t)jb.S * (jb.d + 1);
+        for (int it = 0; it < jb.max_stages + 2; ++it) {
+            CK(launch_reweight(c.d_jobs, list, 1, true, c.stream));
+            CK(launch_resample(c.d_jobs, list, 1, c.stream));
+            CK(launch_gather(c.d_jobs, list, 1, elems, true, c.stream));
+            CK(launch_mh_plain(c.d_jobs, list, 1, jb.S, c.stream));
+            CK(launch_stage_end(c.d_jobs, list, 1, c.d_nactive, c.h_nactive_dev, c.stream));
+            CK(cudaStreamSynchronize(c.stream));
+            if (*(volatile int *)c.h_nactive == 0) break;
+        }
+    }
+    return SMC_OK;
+}
+
+int run_requests(Ctx &c, std::vector<Request *> &reqs)
+{
+    int st = run_fp32(c, reqs);
+    if (st != SMC_OK) return st;
+    for (Request *r : reqs)
+        if (r->fp64) {
+            st = run_fp64(c, *r);
+            if (st != SMC_OK) return st;
+        }
+    return finalize_requests(c, reqs);
+}
+
+// Posterior summaries, p(K|D), results to the host; frees the request's device memory.
+int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
+{
+    for (Request *r : reqs) {
+        int64_t T, S;
+        chains(*r, T, S);
+        const JobDev &j0 = c.h_jobs[r->slots[0]];
+        T = j0.T;
+        const SpecLayout SL = spec_layout(*r, T);
+        char *sa = (char *)r->spec_arena;
+        const int nK = r->k_max - r->k_min + 1;
+        const int dmax = std::max(1, job_dim(r->family, r->k_max, r->bg, r->bg_degree));
+        const int *dslots = (const int *)(sa + SL.slots);
+        float *samples = r->opts.keep_samples ? (float *)(sa + SL.samples) : nullptr;
+        CK(launch_finalize(c.d_jobs, dslots, nK, (double *)(sa + SL.mean), (double *)(sa + SL.sd),
+                           samples, dmax, (int64_t)T * dmax, c.stream));
+        CK(launch_posterior(c.d_jobs, dslots, (const int *)(sa + SL.off), 1, (double *)(sa + SL.pk),
+                            c.stream));
+        r->dim_max = dmax;
+        r->n_samples = T;
+        r->mean.resize((size_t)nK * dmax);
+        r->sdv.resize((size_t)nK * dmax);
+        r->p_k.resize(nK);
+        CK(cudaMemcpyAsync(r->mean.data(), sa + SL.mean, 8 * r->mean.size(), cudaMemcpyDeviceToHost,
+                           c.stream));
+        CK(cudaMemcpyAsync(r->sdv.data(), sa + SL.sd, 8 * r->sdv.size(), cudaMemcpyDeviceToHost,
+                           c.stream));
+        CK(cudaMemcpyAsync(r->p_k.data(), sa + SL.pk, 8 * nK, cudaMemcpyDeviceToHost, c.stream));
+        if (samples) {
+            r->samples.resize((size_t)nK * T * dmax);
+            CK(cudaMemcpyAsync(r->samples.data(), samples, 4 * r->samples.size(),
+                               cudaMemcpyDeviceToHost, c.stream));
+        }
+        std::vector<JobDev> jobs(nK);
+        for (int a = 0; a < nK; ++a)
+            CK(cudaMemcpyAsync(&jobs[a], c.d_jobs + r->slots[a], sizeof(JobDev),
+                               cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+        r->log_z.resize(nK);
+        r->n_stages.resize(nK);
+        r->job_status.resize(nK);
+        r->status = SMC_OK;
+        for (int a = 0; a < nK; ++a) {
+            r->log_z[a] = jobs[a].logz;
+            r->n_stages[a] = jobs[a].stage;
+            r->job_status[a] = jobs[a].status;
+            if (jobs[a].status != 0 && r->status == SMC_OK) r->status = jobs[a].status;
+        }
+        free_request_device(c, *r);
+        r->state = 2;
+        r->t_done = std::chrono::steady_clock::now();
+        r->latency_ms =
+            std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    }
+    return SMC_OK;
+}
+
+}  // namespace smc

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
                                                     int centre, SpecDev sd)
 {
     __shared__ double r0[32], r1[32], r2[32];
-    __shared__ double s_lo, s_hi, s_ln;
+    __shared__ double s_lo, s_hi;
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double lo = INFINITY, hi = -INFINITY, ln = 0.0;
@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
         }
         s_lo = a;
         s_hi = b;
-        s_ln = c;
         s_bad = bad || !(b > a);
         sd.scal->xmin = a;
         sd.scal->xmax = b;
@@ -110,10 +109,10 @@ __device__ void shift_prior(PriorDev &p, double off)
     p.b = (float)p.p2;
 }
 
-__global__ void k_job_setup(JobDev *jobs, const int *slots, const SpecScal *const *scal)
+__global__ void k_job_setup(JobDev *jobs, const int *slots, const SpecScal *scal)
 {
     JobDev &jb = jobs[slots[blockIdx.x]];
-    const SpecScal &sc = *scal[blockIdx.x];
+    const SpecScal &sc = *scal;
     if (threadIdx.x == 0) {
         jb.x_ref = sc.x_ref;
         jb.t_scale = sc.t_scale;
@@ -129,7 +128,7 @@ __global__ void k_job_setup(JobDev *jobs, const int *slots, const SpecScal *cons
     for (int j = threadIdx.x; j < jb.d; j += blockDim.x) shift_prior(pri[j], sc.x_ref);
 }
 
-cudaError_t launch_job_setup(JobDev *jobs, const int *slots, const SpecScal *const *scal, int nslots,
+cudaError_t launch_job_setup(JobDev *jobs, const int *slots, const SpecScal *scal, int nslots,
                              cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;

@@ -20,7 +20,7 @@ struct SpecDev {
 
 cudaError_t launch_spec_prep(const double *x, const double *y, const double *sg, int n, int n_pad,
                              int centre, const SpecDev &sd, cudaStream_t s);
-cudaError_t launch_job_setup(JobDev *jobs, const int *slots, const SpecScal *const *scal,
+cudaError_t launch_job_setup(JobDev *jobs, const int *slots, const SpecScal *scal,
                              int nslots, cudaStream_t s);
 cudaError_t launch_posterior(const JobDev *jobs, const int *slots, const int *off, int nreq,
                              double *pk, cudaStream_t s);

@@ -1,0 +1,283 @@
+"""Parity of every CUDA step with the FP64 oracle, through the C ABI.
+
+Tolerances (stated per test) follow from the arithmetic:
+  * integer work (Philox words, resampling ancestors): bit-exact;
+  * FP64 kernels (plain path): same formulas, different summation order and
+    FMA contraction -> relative 1e-12 on energies, replayed trajectories equal
+    to 1e-9 (a knife-edge accept/reject flip would show as a large difference);
+  * FP32 energies: each term 1/2 w r^2 carries relative error ~ few ulp of the
+    largest of (y, f) over sigma; Kahan keeps the sum's error at that level, so
+    |E32 - E64| <= 2e-5 (E64 + N) (measured ~1e-6);
+  * full runs: |delta log Z| <= 0.05 nats and the same argmax K.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_03271_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_03271_b300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+# --------------------------------------------------------------------------
+# Philox
+# --------------------------------------------------------------------------
+
+def test_philox_bit_exact(ctx):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    for seed in (0, 1, 0xDEADBEEF12345678):
+        dev = ctx.philox(seed, ctr)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i in range(0, 4096, 97):
+            assert list(dev[i]) == list(oracle.philox(ctr[i], key))
+
+
+# --------------------------------------------------------------------------
+# Energies (forward model Eq. (1), energy of Eq. (C2))
+# --------------------------------------------------------------------------
+
+def _specs():
+    return [(W.gaussian_small(1), 3), (W.xps_like(2), 4), (W.xrd_like(3, n=1500, k_true=6, k_max=6), 6),
+            (W.mixed_batch(5, count=4)[3][0], 2)]
+
+
+@pytest.mark.parametrize("which", range(4))
+def test_energy_fp32_and_fp64(ctx, which):
+    spec, K = _specs()[which]
+    opts = W.Options(particles=300, seed=9)
+    nat, E_or = oracle.init_particles(spec, K, opts, 300)
+    # natural values: oracle returns sampling coordinates
+    nat = nat.copy()
+    d = nat.shape[1]
+    p = 4 if spec.family == W.PSEUDO_VOIGT else 3
+    for j in range(d):
+        pr = spec.priors.amp if j < p * K and j % p == 0 else None
+        kind = _prior_kind(spec, K, j)
+        if kind == W.LOG_UNIFORM:
+            nat[:, j] = np.exp(nat[:, j])
+    E64 = ctx.energy(spec, K, opts, nat, precision=1)
+    E32 = ctx.energy(spec, K, opts, nat, precision=0)
+    np.testing.assert_allclose(E64, E_or, rtol=1e-12)
+    assert np.all(np.abs(E32 - E_or) <= 2e-5 * (E_or + spec.n))
+
+
+def _prior_kind(spec, K, j):
+    p = 4 if spec.family == W.PSEUDO_VOIGT else 3
+    if spec.comp_priors:
+        return spec.comp_priors[j].kind
+    if j < p * K:
+        return [spec.priors.amp, spec.priors.centre, spec.priors.width, spec.priors.eta][j % p].kind
+    return spec.priors.bg[j - p * K].kind
+
+
+# --------------------------------------------------------------------------
+# Prior draws
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", range(3))
+def test_prior_draws_match_oracle(ctx, which):
+    spec, K = _specs()[which]
+    opts = W.Options(particles=500, seed=21)
+    u_or, E_or = oracle.init_particles(spec, K, opts, 500)
+    nat64, E64 = ctx.prior(spec, K, opts, 500, precision=1)
+    nat32, E32 = ctx.prior(spec, K, opts, 500, precision=0)
+    nat_or = u_or.copy()
+    for j in range(u_or.shape[1]):
+        if _prior_kind(spec, K, j) == W.LOG_UNIFORM:
+            nat_or[:, j] = np.exp(u_or[:, j])
+    np.testing.assert_allclose(nat64, nat_or, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(E64, E_or, rtol=1e-11)
+    np.testing.assert_allclose(nat32, nat_or, rtol=2e-6, atol=1e-5 * (1 + np.abs(nat_or)).max())
+
+
+# --------------------------------------------------------------------------
+# Tempering step: ESS bisection and evidence increment
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T,scale,beta", [(1000, 1e5, 0.0), (4097, 50.0, 0.3), (65536, 3e3, 0.01),
+                                           (257, 1e-4, 0.9)])
+def test_reweight_fp64_matches_oracle(ctx, T, scale, beta):
+    rng = np.random.default_rng(T)
+    E = rng.gamma(2.0, scale, T) + 123.0
+    d, lz, fin, q = ctx.reweight(E, beta, 0.5, precision=1)
+    e = E - E.min()
+    d_or, fin_or, _ = oracle.choose_delta(e, beta, 0.5)
+    assert fin == fin_or
+    assert d == pytest.approx(d_or, rel=1e-12)
+    w = np.exp(-d_or * e)
+    lz_or = -d_or * E.min() + math.log(w.mean())
+    assert lz == pytest.approx(lz_or, rel=1e-12, abs=1e-12)
+    q_or = oracle.quantise(w)
+    diff = np.abs(q.astype(np.int64) - q_or.astype(np.int64))
+    assert diff.max() <= 1 and np.mean(diff > 0) < 1e-3
+    if not fin:
+        g = oracle.ess_frac(e, d)
+        assert 0.5 <= g <= 0.5 * (1 + 1e-6)
+
+
+def test_reweight_fp32_energies(ctx):
+    rng = np.random.default_rng(3)
+    E = (rng.gamma(2.0, 200.0, 8192) + 1000.0).astype(np.float32).astype(np.float64)
+    d, lz, fin, q = ctx.reweight(E, 0.0, 0.5, precision=0)
+    d_or, fin_or, _ = oracle.choose_delta(E - E.min(), 0.0, 0.5)
+    assert fin == fin_or and d == pytest.approx(d_or, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Systematic resampling: bit-exact
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T,M", [(1, 1), (2, 5), (7, 7), (1000, 1000), (1000, 77), (4096, 4096),
+                                 (65536, 65536), (100003, 33334), (1 << 20, 1 << 20)])
+def test_resample_bit_exact(ctx, T, M):
+    rng = np.random.default_rng(T + 7 * M)
+    w = rng.uniform(0, 1, T) ** 6
+    w[rng.integers(0, T)] = 1.0
+    q = oracle.quantise(w)
+    for u32 in (0, 2 ** 32 - 1, int(rng.integers(0, 2 ** 32))):
+        a = ctx.resample(q, M, u32)
+        np.testing.assert_array_equal(a, oracle.resample(q, M, u32))
+
+
+def test_resample_degenerate_weights(ctx):
+    T = 5000
+    q = np.zeros(T, dtype=np.uint64)
+    q[1234] = 2 ** 40
+    assert np.all(ctx.resample(q, T, 12345) == 1234)
+    q = np.full(T, 2 ** 40, dtype=np.uint64)
+    np.testing.assert_array_equal(ctx.resample(q, T, 2 ** 31), np.arange(T))
+
+
+# --------------------------------------------------------------------------
+# Metropolis stage
+# --------------------------------------------------------------------------
+
+def _starts(spec, K, opts, S, seed=4):
+    u, E = oracle.init_particles(spec, K, W.Options(particles=S, seed=seed), S)
+    nat = u.copy()
+    for j in range(u.shape[1]):
+        if _prior_kind(spec, K, j) == W.LOG_UNIFORM:
+            nat[:, j] = np.exp(u[:, j])
+    return u, nat, E
+
+
+@pytest.mark.parametrize("which,beta,wf", [(0, 0.02, 0), (1, 1e-5, 0), (0, 0.5, 1)])
+def test_mh_fp64_replays_oracle(ctx, which, beta, wf):
+    spec, K = _specs()[which]
+    opts = W.Options(particles=96, sweeps=3, seed=13, waste_free=wf)
+    u, nat, E = _starts(spec, K, opts, 96)
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, beta, 7)
+    nat_g, E_g, acc_g, prop_g = ctx.mh_stage(spec, K, opts, nat, E, step, beta, 7, precision=1)
+    nat_or = u_or.copy()
+    for j in range(u.shape[1]):
+        if _prior_kind(spec, K, j) == W.LOG_UNIFORM:
+            nat_or[:, j] = np.exp(u_or[:, j])
+    np.testing.assert_array_equal(acc_g, acc_or)
+    np.testing.assert_array_equal(prop_g, prop_or)
+    np.testing.assert_allclose(nat_g, nat_or, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(E_g, E_or, rtol=1e-9)
+
+
+@pytest.mark.parametrize("which,beta", [(0, 0.05), (1, 1e-4), (2, 1e-3), (3, 0.3)])
+def test_mh_fp32_tracks_oracle(ctx, which, beta):
+    spec, K = _specs()[which]
+    opts = W.Options(particles=256, sweeps=4, seed=17)
+    u, nat, E = _starts(spec, K, opts, 256)
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, beta, 3)
+    nat_g, E_g, acc_g, prop_g = ctx.mh_stage(spec, K, opts, nat, E, step, beta, 3, precision=0)
+    np.testing.assert_array_equal(prop_g, prop_or)
+    # the same random streams: accept counts agree up to FP32 knife-edge flips
+    assert np.abs(acc_g - acc_or).sum() <= 0.02 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, _to_sampling(spec, K, nat_g))
+    assert np.all(np.abs(E_g - E_true) <= 2e-5 * (E_true + spec.n))
+    same = np.mean(np.abs(E_g - E_or) <= 1e-4 * (E_or + spec.n))
+    assert same > 0.9
+
+
+def _to_sampling(spec, K, nat):
+    u = np.array(nat, dtype=np.float64, copy=True)
+    for j in range(u.shape[1]):
+        if _prior_kind(spec, K, j) == W.LOG_UNIFORM:
+            u[:, j] = np.log(u[:, j])
+    return u
+
+
+# --------------------------------------------------------------------------
+# Full sampler
+# --------------------------------------------------------------------------
+
+def test_full_run_fp64_replays_oracle(ctx):
+    spec = W.gaussian_small(1)
+    opts = W.Options(particles=384, sweeps=4, seed=5)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=384, sweeps=4, seed=5, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7, rtol=0)
+    np.testing.assert_array_equal(r["n_stages"], [j["n_stages"] for j in ref["jobs"]])
+
+
+def test_full_run_fp32_matches_oracle_gaussian(ctx):
+    spec = W.gaussian_small(1)
+    opts = W.Options(particles=1024, sweeps=10, seed=1)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, opts)
+    assert r["status"] == 0
+    assert np.max(np.abs(r["log_z"] - np.array(ref["log_z"]))) <= 0.05
+    assert r["argmax_k"] == ref["argmax_k"] == 2
+    np.testing.assert_allclose(r["p_k"], ref["p_k"], atol=0.05)
+
+
+def test_full_run_waste_free(ctx):
+    spec = W.gaussian_small(2)
+    opts = W.Options(particles=600, sweeps=6, seed=3, waste_free=1)
+    ref = oracle.run(spec, opts, k_range=[1, 2])
+    spec2 = W.gaussian_small(2)
+    spec2.k_max = 2
+    r = ctx.run(spec2, opts)
+    assert r["n_samples"] == 100 * 6
+    assert np.max(np.abs(r["log_z"] - np.array(ref["log_z"]))) <= 0.05
+
+
+def test_batch_invariance_bit_identical(ctx):
+    a = W.gaussian_small(1)
+    b = W.xps_like(4, n=400, k_max=2)
+    oa = W.Options(particles=512, sweeps=3, seed=2)
+    ob = W.Options(particles=1024, sweeps=2, seed=9)
+    alone = ctx.run(a, oa, keep_samples=False)
+    mixed = ctx.run_batch([(b, ob), (a, oa)], keep_samples=False)
+    np.testing.assert_array_equal(alone["log_z"], mixed[1]["log_z"])
+    np.testing.assert_array_equal(alone["n_stages"], mixed[1]["n_stages"])
+    for x, y in zip(alone["post_mean"], mixed[1]["post_mean"]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_invalid_inputs_rejected(ctx):
+    from paper_2604_03271_b300 import api
+    spec = W.gaussian_small(1)
+    spec.sigma = spec.sigma.copy()
+    spec.sigma[3] = -1.0
+    with pytest.raises(api.SmcError) as e:
+        ctx.run(spec, W.Options(particles=64))
+    assert e.value.status == api.SMC_EINVAL
+
+
+def test_max_stages_reported(ctx):
+    spec = W.gaussian_small(1)
+    r = ctx.run(spec, W.Options(particles=128, sweeps=1, seed=1, max_stages=2))
+    assert np.all(r["job_status"] == 5) and np.all(r["n_stages"] == 2)
+    ref = oracle.run_job(spec, 2, W.Options(particles=128, sweeps=1, seed=1, max_stages=2))
+    assert ref["status"] == oracle.EMAXSTAGES
