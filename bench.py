@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched FP32-energy SMC sampler.
+
+Workload (default): XPS-shaped spectra -- N = 1001 points on a 20 eV binding
+energy axis at 280 eV, 4 true pseudo-Voigt peaks on a linear background,
+counting-like noise -- fitted with pseudo-Voigt peaks + linear background for
+every K = 1..6 at once, 16384 particles per K, 20 Metropolis sweeps per stage,
+ESS target 0.5 (seeded synthetic data, see paper_2604_03271_b300/workloads.py).
+One step = one full SMC run (prior to beta = 1, every K) over a batch of B
+spectra.  Metric: spectra/s (higher is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 the driver launches one rank per GPU with torchrun; spectra are
+sharded across ranks (independent jobs, no collective on the data path).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_03271_b300 import workloads as W  # noqa: E402
+
+METRIC = "spectra/s (all candidate K per spectrum, |dlogZ|<=0.05 vs FP64)"
+SM_COUNT = 148
+SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
+
+
+def workload(name: str, seed: int):
+    if name == "xps":
+        return W.xps_like(seed), W.Options(particles=16384, sweeps=20, seed=seed)
+    if name == "xrd":
+        return W.xrd_like(seed), W.Options(particles=65536, sweeps=20, seed=seed)
+    if name == "gauss":
+        return W.gaussian_small(seed), W.Options(particles=1024, sweeps=10, seed=seed)
+    raise ValueError(name)
+
+
+def config_of(name: str, batch: int) -> dict:
+    s, o = workload(name, 1)
+    return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301"}[name],
+            "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
+            "sweeps": o.sweeps, "ess_target": o.ess_target, "spectra_per_step": batch,
+            "family": "pseudo-voigt" if s.family == W.PSEUDO_VOIGT else "gauss",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on a bounded sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_rate(name: str, seconds: float = 12.0) -> dict:
+    """Particle-point evaluations per second of the FP64 oracle on a bounded
+    sample of the workload: one Metropolis stage (beta = 1e-3) of a few chains
+    for every candidate K, from prior draws."""
+    import oracle
+
+    spec, opts = workload(name, 1)
+    t0 = time.perf_counter()
+    units = 0.0
+    chains = 0
+    ks = list(range(spec.k_min, spec.k_max + 1))
+    o = W.Options(particles=4, sweeps=1, seed=3)
+    while time.perf_counter() - t0 < seconds:
+        for K in ks:
+            u, E = oracle.init_particles(spec, K, o, 4)
+            d = u.shape[1]
+            step = 0.05 * np.maximum(np.abs(u).mean(0), 1e-3)
+            _, _, acc, prop = oracle.mh_stage(spec, K, o, u, E, step, 1e-3, 1)
+            units += float(prop.sum()) * spec.n
+            chains += 4
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"units_per_s": units / dt, "seconds": dt,
+            "sample": f"{chains} chains x 1 sweep over K={ks[0]}..{ks[-1]} (FP64 oracle, full energy "
+                      f"per proposal), scaled by the GPU run's particle-point evaluations per spectrum"}
+
+
+def reference_arm(args, world: int, rank: int):
+    if rank != 0:
+        return
+    name = args.workload
+    # particle-point evaluations per spectrum of this workload (measured on the
+    # GPU arm; stated constant so the reference arm needs no GPU)
+    per_spec = UNITS_PER_SPECTRUM.get(name)
+    step_s = []
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_rate(name, seconds=max(2.0, 60.0 / (args.warmup + args.steps)))
+        if k >= args.warmup:
+            step_s.append(r["seconds"])
+            rates.append(r["units_per_s"])
+    rate = float(np.mean(rates))
+    value = rate / per_spec
+    line = {"metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(step_s)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(name, args.batch), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": 1, "kind": "oracle",
+                             "sample": r["sample"], "units_per_s": rate},
+            "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# particle-point evaluations per spectrum (prior energies + every evaluated
+# proposal x N), from the GPU arm's own counters on the same seeds
+UNITS_PER_SPECTRUM = {"xps": 1.0e11, "xrd": 1.0e13, "gauss": 5.0e8}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss"])
+    ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-sample", type=int, default=1, help="time the plain FP64 path on a sample")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_03271_b300 import api
+
+    stream = torch.cuda.current_stream(dev)
+    ctx = api.Context(local, stream=stream.cuda_stream)
+    B = args.batch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def batch_for(step: int):
+        items = []
+        for b in range(B):
+            seed = 1 + (step * world + rank) * B + b
+            items.append(workload(args.workload, seed))
+        return items
+
+    def to_dev(items):
+        out = []
+        for s, _ in items:
+            out.append(tuple(torch.tensor(a, dtype=torch.float64, device=dev) for a in (s.x, s.y, s.sigma)))
+        return out
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- warm-up (untimed)
+    for k in range(args.warmup):
+        items = batch_for(k)
+        ctx.run_batch(items, keep_samples=False, device_arrays=to_dev(items))
+
+    # ---- timed: inputs resident in HBM
+    steps = [batch_for(args.warmup + k) for k in range(args.steps)]
+    dev_in = [to_dev(it) for it in steps]
+    ctx.profile_reset(events=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in steps]
+    results = []
+    t_wall = time.perf_counter()
+    for k, items in enumerate(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        results.append(ctx.run_batch(items, keep_samples=False, device_arrays=dev_in[k]))
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = ctx.profile()
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    spectra = args.steps * B * world
+    value = spectra / (total_ms / 1000.0)
+
+    # ---- end to end through the public API: host inputs, results to host
+    ctx.profile_reset(events=False)
+    barrier()
+    e2e_ms = 0.0
+    for k, items in enumerate(steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.run_batch(items, keep_samples=False)
+        e2e_ms += 1000.0 * (time.perf_counter() - t0)
+    prof_e2e = ctx.profile()
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": spectra / (e2e_ms / 1000.0), "unit": "spectra/s",
+           "h2d_bytes_per_step": prof_e2e["h2d_bytes"] / args.steps,
+           "d2h_bytes_per_step": prof_e2e["d2h_bytes"] / args.steps}
+
+    # ---- roofline of the dominant kernel (fused Metropolis, SFU-issue bound)
+    mh_ms = prof["ms"]["metropolis"]
+    mh_n = max(1, prof["launches"]["metropolis"])
+    sfu_per_launch = prof["sfu_ops"] / mh_n
+    achieved = sfu_per_launch / (mh_ms / mh_n / 1000.0) / 1e9 if mh_ms > 0 else 0.0
+    peak = SM_COUNT * SFU_PER_SM_CLK * 2032e6 / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_mh (fused Metropolis)", "avg_launch_ms": mh_ms / mh_n,
+                "peak_note": "148 SMs x 16 SFU/clk x 2032 MHz (nominal max clock)"}
+    shares = {k: prof["ms"][k] for k in prof["ms"]}
+    tot = sum(shares.values()) or 1.0
+    gather_gbs = prof["gather_bytes"] / (prof["ms"]["gather"] / 1000.0) / 1e9 if prof["ms"]["gather"] else None
+    resample_gbs = (prof["resample_bytes"] / (prof["ms"]["resample"] / 1000.0) / 1e9
+                    if prof["ms"]["resample"] else None)
+    units_per_spec = prof["point_evals"] / (args.steps * B)
+
+    # ---- parity spot check against the plain FP64 path and the oracle is in
+    # the tests; here: model selection summary
+    lz = [list(map(float, r["log_z"])) for res in results for r in res]
+    sel = [int(r["argmax_k"]) if r["argmax_k"] is not None else None for res in results for r in res]
+
+    line = {"metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 energies (Kahan), f64 tempering/logZ",
+            "data": "synthetic", "config": config_of(args.workload, B), "impl": "ours",
+            "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())) + 5 * prof["jobs"],
+            "clocks": clk, "roofline": roofline,
+            "particle_point_evals_per_s": prof["point_evals"] / (total_ms / 1000.0) * world,
+            "kernel_ms_share": {k: v / tot for k, v in shares.items()},
+            "gather_gbs": gather_gbs, "resample_gbs": resample_gbs,
+            "stages": prof["stages"], "jobs": prof["jobs"], "selected_k": sel,
+            "units_per_spectrum": units_per_spec, "wall_s": t_wall}
+
+    if rank == 0 and args.plain_sample:
+        line["plain_fp64"] = plain_sample(ctx, args.workload, units_per_spec)
+    if rank == 0 and not args.no_cpu_baseline:
+        r = oracle_rate(args.workload, seconds=12.0)
+        line["cpu_baseline"] = {"value": r["units_per_s"] / units_per_spec, "unit": "spectra/s", "cores": 1,
+                                "kind": "oracle", "sample": r["sample"], "units_per_s": r["units_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def plain_sample(ctx, name: str, units_per_spec: float) -> dict:
+    """The plain one-spectrum-per-launch FP64 path on a bounded sample: two
+    tempering stages of one spectrum, all K, at 1/16 of the particles.  Its
+    particle-point evaluation rate, scaled by the workload's evaluations per
+    spectrum, gives its spectra/s."""
+    spec, o = workload(name, 1)
+    opts = W.Options(particles=max(64, o.particles // 16), sweeps=o.sweeps, seed=1, energy_fp64=1,
+                     max_stages=2)
+    ctx.profile_reset(events=False)
+    t0 = time.perf_counter()
+    ctx.run(spec, opts, keep_samples=False)
+    dt = time.perf_counter() - t0
+    p = ctx.profile()
+    rate = p["point_evals"] / dt
+    return {"units_per_s": rate, "spectra_per_s": rate / units_per_spec, "seconds": dt,
+            "sample": f"2 stages, T={opts.particles}, K={spec.k_min}..{spec.k_max}, FP64 thread-per-chain"}
+
+
+if __name__ == "__main__":
+    main()

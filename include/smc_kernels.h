@@ -58,6 +58,32 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
                    uint32_t stage, int32_t precision, double *nat_out, double *E_out,
                    int64_t *acc, int64_t *prop);
 
+/* Profiling counters of a context, accumulated over the runs finished since
+ * the last smc_profile_reset.  Kernel classes: 0 reweight (tempering step),
+ * 1 resample, 2 gather (particle copy), 3 Metropolis, 4 stage end.  With
+ * events enabled, every batched stage records CUDA events around each kernel
+ * class on the context's stream (inside the CUDA graph); `launches` counts
+ * kernel launches of stages in which at least one job was active and `ms` the
+ * summed event time of those launches.  The algorithmic counters are exact
+ * counts made by the kernels themselves:
+ *   point_evals  grid-point evaluations of evaluated proposals (plus the
+ *                prior-draw energies), the "particle-point evaluations";
+ *   sfu_ops      SFU operations (EX2, RCP) the centre/width proposals need:
+ *                N per Gaussian or Lorentzian evaluation, 2 N per pseudo-Voigt;
+ *   gather_bytes bytes the particle copy must move (read + write), per stage;
+ *   resample_bytes bytes the resampler must move (q read, ancestors written);
+ *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied. */
+typedef struct {
+    int64_t launches[5];
+    double ms[5];
+    double point_evals, sfu_ops, gather_bytes, resample_bytes;
+    double h2d_bytes, d2h_bytes;
+    int64_t stages, jobs;
+} smc_profile;
+
+int smc_profile_reset(smc_ctx *ctx, int32_t enable_events);
+int smc_profile_read(smc_ctx *ctx, smc_profile *out);
+
 #ifdef __cplusplus
 }
 #endif

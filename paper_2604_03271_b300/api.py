@@ -54,6 +54,16 @@ class Request(C.Structure):
                 ("priors", C.POINTER(Priors)), ("opts", C.POINTER(Options))]
 
 
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("point_evals", C.c_double),
+                ("sfu_ops", C.c_double), ("gather_bytes", C.c_double), ("resample_bytes", C.c_double),
+                ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
+                ("stages", C.c_int64), ("jobs", C.c_int64)]
+
+
+KERNEL_CLASSES = ("reweight", "resample", "gather", "metropolis", "stage_end")
+
+
 class ResultView(C.Structure):
     _fields_ = [("k_min", C.c_int32), ("k_max", C.c_int32), ("dim_max", C.c_int32),
                 ("status", C.c_int32), ("log_z", C.POINTER(C.c_double)),
@@ -94,7 +104,9 @@ def lib():
     L.smc_k_reweight.argtypes = [vp, vp, i64, dbl, dbl, i32, P(dbl), P(dbl), P(i32), vp]
     L.smc_k_resample.argtypes = [vp, vp, i64, i64, u32, vp]
     L.smc_k_mh_stage.argtypes = [vp, P(Request), i32, vp, vp, i64, vp, dbl, u32, i32, vp, vp, vp, vp]
-    for f in ("smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_poll",
+    L.smc_profile_reset.argtypes = [vp, i32]
+    L.smc_profile_read.argtypes = [vp, P(Profile)]
+    for f in ("smc_profile_reset", "smc_profile_read", "smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_poll",
               "smc_wait", "smc_result", "smc_release", "smc_k_philox", "smc_k_energy",
               "smc_k_prior", "smc_k_reweight", "smc_k_resample", "smc_k_mh_stage"):
         getattr(L, f).restype = C.c_int
@@ -249,6 +261,20 @@ class Context:
 
     def wait(self, job: int, timeout_s: float = -1.0):
         _check(self._L.smc_wait(self.h, C.c_uint64(job), float(timeout_s)), "smc_wait")
+
+    # -- profiling ---------------------------------------------------------
+    def profile_reset(self, events: bool = False):
+        _check(self._L.smc_profile_reset(self.h, 1 if events else 0), "smc_profile_reset")
+
+    def profile(self) -> dict:
+        p = Profile()
+        _check(self._L.smc_profile_read(self.h, C.byref(p)), "smc_profile_read")
+        return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))),
+                "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
+                "point_evals": p.point_evals, "sfu_ops": p.sfu_ops,
+                "gather_bytes": p.gather_bytes, "resample_bytes": p.resample_bytes,
+                "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes,
+                "stages": p.stages, "jobs": p.jobs}
 
     # -- step-level entry points (include/smc_kernels.h) -------------------
     def philox(self, seed: int, ctr: np.ndarray) -> np.ndarray:

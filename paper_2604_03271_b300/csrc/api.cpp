@@ -177,13 +177,13 @@ int smc_create(smc_ctx **out, const smc_create_opts *opts)
               cudaMemset(c.d_jobs, 0, sizeof(JobDev) * MAX_SLOTS) == cudaSuccess &&
               cudaMalloc((void **)&c.d_lists, sizeof(int) * LIST_AREA) == cudaSuccess &&
               cudaMalloc((void **)&c.d_nactive, sizeof(int)) == cudaSuccess &&
-              cudaHostAlloc((void **)&c.h_nactive, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc((void **)&c.h_nactive, sizeof(int) * NACTIVE_SLOTS, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&c.h_nactive_dev, c.h_nactive, 0) == cudaSuccess;
     if (!ok) {
         smc_destroy(ctx);
         return SMC_ECUDA;
     }
-    *c.h_nactive = 0;
+    for (int k = 0; k < NACTIVE_SLOTS; ++k) c.h_nactive[k] = 0;
     *out = ctx;
     return SMC_OK;
 }
@@ -730,6 +730,23 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
     }
     drop(ctx, r);
     return st;
+}
+
+int smc_profile_reset(smc_ctx *ctx, int32_t enable_events)
+{
+    if (!ctx) return SMC_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(ctx->c.mu);
+    ctx->c.prof = smc_profile{};
+    ctx->c.prof_events = enable_events != 0;
+    return SMC_OK;
+}
+
+int smc_profile_read(smc_ctx *ctx, smc_profile *out)
+{
+    if (!ctx || !out) return SMC_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(ctx->c.mu);
+    *out = ctx->c.prof;
+    return SMC_OK;
 }
 
 }  // extern "C"

@@ -328,6 +328,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         CK(cudaMemcpyAsync(raw, r.hx.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
         CK(cudaMemcpyAsync(raw + r.n, r.hy.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
         CK(cudaMemcpyAsync(raw + 2 * r.n, r.hs.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
+        c.prof.h2d_bytes += 24.0 * r.n;
         ix = raw;
         iy = raw + r.n;
         is = raw + 2 * r.n;
@@ -483,21 +484,32 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
     return SMC_OK;
 }
 
-// One tempering stage of every active job of the plan.
-static cudaError_t iteration(Ctx &c, const Plan &P)
+// One tempering stage of every active job of the plan.  ev (optional) holds
+// six events recorded between the kernel classes; k selects the host-mapped
+// slot that receives the number of jobs still active afterwards.
+static cudaError_t iteration(Ctx &c, const Plan &P, cudaEvent_t *ev, int k)
 {
     const int nall = (int)P.all.size();
     cudaError_t e;
+    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], c.stream) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return e;
     if ((e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream)) != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_resample(c.d_jobs, c.d_lists, nall, c.stream)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream)) != cudaSuccess)
         return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
     for (size_t b = 0; b < P.buckets.size(); ++b)
         if ((e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
                            P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b],
                            c.stream)) != cudaSuccess)
             return e;
-    return launch_stage_end(c.d_jobs, c.d_lists, nall, c.d_nactive, c.h_nactive_dev, c.stream);
+    if ((e = mark(4)) != cudaSuccess) return e;
+    if ((e = launch_stage_end(c.d_jobs, c.d_lists, nall, c.d_nactive, c.h_nactive_dev + k, c.stream)) !=
+        cudaSuccess)
+        return e;
+    return mark(5);
 }
 
 int run_chunk(Ctx &c, std::vector<Request *> &reqs, int iters)
@@ -505,7 +517,7 @@ int run_chunk(Ctx &c, std::vector<Request *> &reqs, int iters)
     Plan P;
     int st = build_plan(c, reqs, P);
     if (st != SMC_OK || P.all.empty()) return st;
-    for (int k = 0; k < iters; ++k) CK(iteration(c, P));
+    for (int k = 0; k < iters; ++k) CK(iteration(c, P, nullptr, 0));
     CK(cudaStreamSynchronize(c.stream));
     return SMC_OK;
 }
@@ -515,14 +527,19 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
     Plan P;
     int st = build_plan(c, reqs, P);
     if (st != SMC_OK || P.all.empty()) return st;
-    // capture a few stages into a CUDA graph and replay it until no job is active
-    const int chunk = 4;
+    // capture CHUNK stages into a CUDA graph and replay it until no job is active
+    std::vector<cudaEvent_t> ev;
+    if (c.prof_events) {
+        ev.resize(6 * CHUNK);
+        for (auto &x : ev) CK(cudaEventCreate(&x));
+    }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = iteration(c, P);
+        for (int k = 0; k < CHUNK && e == cudaSuccess; ++k)
+            e = iteration(c, P, ev.empty() ? nullptr : &ev[6 * k], k);
         cudaError_t e2 = cudaStreamEndCapture(c.stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
             use_graph = false;
@@ -530,27 +547,46 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
         use_graph = false;
     }
     cudaGetLastError();
-    const int max_iters = P.max_stages + 8;
+    const int max_iters = P.max_stages + 2 * CHUNK;
     int done_iters = 0;
     int status = SMC_OK;
+    int prev_active = 1;
     while (done_iters < max_iters) {
-        cudaError_t e;
+        cudaError_t e = cudaSuccess;
+        int ran = 0;
         if (use_graph) {
             e = cudaGraphLaunch(exec, c.stream);
-            done_iters += chunk;
+            ran = CHUNK;
         } else {
-            e = iteration(c, P);
-            done_iters += 1;
+            for (int k = 0; k < CHUNK && e == cudaSuccess; ++k, ++ran)
+                e = iteration(c, P, ev.empty() ? nullptr : &ev[6 * k], k);
         }
+        done_iters += ran;
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
         if (e != cudaSuccess) {
             status = cuda_status(e);
             break;
         }
-        if (*(volatile int *)c.h_nactive == 0) break;
+        int last = 0;
+        for (int k = 0; k < ran; ++k) {
+            const int now = ((volatile int *)c.h_nactive)[k];
+            if (!ev.empty() && prev_active > 0) {
+                for (int q = 0; q < 5; ++q) {
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, ev[6 * k + q], ev[6 * k + q + 1]);
+                    c.prof.ms[q] += ms;
+                    c.prof.launches[q] += (q == 3) ? (int64_t)P.buckets.size() : 1;
+                }
+            }
+            if (prev_active > 0) c.prof.stages += 1;
+            prev_active = now;
+            last = now;
+        }
+        if (last == 0) break;
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (auto &x : ev) cudaEventDestroy(x);
     return status;
 }
 
@@ -570,6 +606,7 @@ static int run_fp64(Ctx &c, Request &r)
             CK(launch_mh_plain(c.d_jobs, list, 1, jb.S, c.stream));
             CK(launch_stage_end(c.d_jobs, list, 1, c.d_nactive, c.h_nactive_dev, c.stream));
             CK(cudaStreamSynchronize(c.stream));
+            c.prof.stages += 1;
             if (*(volatile int *)c.h_nactive == 0) break;
         }
     }
@@ -626,11 +663,20 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             CK(cudaMemcpyAsync(&jobs[a], c.d_jobs + r->slots[a], sizeof(JobDev),
                                cudaMemcpyDeviceToHost, c.stream));
         CK(cudaStreamSynchronize(c.stream));
+        c.prof.d2h_bytes += 16.0 * r->mean.size() + 8.0 * nK + (double)sizeof(JobDev) * nK +
+                            4.0 * r->samples.size();
         r->log_z.resize(nK);
         r->n_stages.resize(nK);
         r->job_status.resize(nK);
         r->status = SMC_OK;
         for (int a = 0; a < nK; ++a) {
+            const JobDev &jd = jobs[a];
+            const double esz = jd.fp64 ? 8.0 : 4.0;
+            c.prof.point_evals += (double)jd.point_evals + (double)jd.T * jd.n;
+            c.prof.sfu_ops += (double)jd.sfu_ops;
+            c.prof.gather_bytes += (double)jd.stage * ((double)jd.S * (jd.d + 1) * 2.0 * esz + 4.0 * jd.S);
+            c.prof.resample_bytes += (double)jd.stage * (8.0 * jd.T + 4.0 * jd.S);
+            c.prof.jobs += 1;
             r->log_z[a] = jobs[a].logz;
             r->n_stages[a] = jobs[a].stage;
             r->job_status[a] = jobs[a].status;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/smc.h"
+#include "../../include/smc_kernels.h"
 #include "kernels.h"
 #include "prep.h"
 
@@ -25,6 +26,8 @@ namespace smc {
 
 constexpr int MAX_SLOTS = 4096;
 constexpr int LIST_AREA = 24 * MAX_SLOTS;  // ints of the device slot-list area
+constexpr int CHUNK = 4;                   // stages per CUDA-graph launch
+constexpr int NACTIVE_SLOTS = 64;
 
 struct Tile {
     int J, G;
@@ -72,8 +75,11 @@ struct Ctx {
     std::vector<int> free_slots;
     int *d_lists = nullptr;
     int *d_nactive = nullptr;
-    int *h_nactive = nullptr;      // pinned, device-mapped
+    int *h_nactive = nullptr;      // pinned, device-mapped, one entry per stage of a chunk
     int *h_nactive_dev = nullptr;  // its device alias
+    // profiling
+    bool prof_events = false;
+    smc_profile prof{};
     std::map<smc_job, Request *> reqs;
     uint64_t next_id = 1;
     // serving

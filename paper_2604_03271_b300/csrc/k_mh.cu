@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
         int kind[2];
         float plo[2], phi[2], pa[2], pb[2];
         unsigned acc[2] = {0u, 0u}, prp[2] = {0u, 0u};
+        unsigned long long n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = lane + 32 * h;
@@ -290,6 +291,8 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                     const float tj = __shfl_sync(FULL_MASK, sel(h, thr[0], thr[1]), src);
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
                     const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
+                    ++n_eval;
+                    if (c == 1 || c == 2) ++n_shape;
                     float part = 0.0f;
                     if (c == 0) {  // amplitude: D = (A' - A) u
                         const float dA = v - A;
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                 if (tj == INFINITY) continue;
                 const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
                 const float cq = __shfl_sync(FULL_MASK, sel(h, nat[0], nat[1]), src);
+                ++n_eval;
                 const float dc = v - cq;
                 float part = 0.0f;
 #pragma unroll
@@ -415,6 +419,11 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                     atomicAdd(&jobs[slot].acc[j], (unsigned long long)acc[h]);
                     atomicAdd(&jobs[slot].prop[j], (unsigned long long)prp[h]);
                 }
+            }
+            if (lane == 0) {
+                const unsigned long long npts = (unsigned long long)jb.n;
+                atomicAdd(&jobs[slot].point_evals, n_eval * npts);
+                atomicAdd(&jobs[slot].sfu_ops, n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
             }
         }
     }

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(128) k_mh_plain(JobDev *jobs, const int *slots
         acc[j] = prp[j] = 0u;
     }
     double Ec = jb.Es64[m];
+    unsigned long long n_eval = 0;
     for (int t = 0; t < n; ++t) {
         for (int j = 0; j < d; ++j) {
             const PriorDev &pr = jb.pri[j];
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(128) k_mh_plain(JobDev *jobs, const int *slots
             prp[j] += 1u;
             if (!in_support_d(pr, up)) continue;
             const double dlp = log_prior_d(pr, up) - log_prior_d(pr, u[j]);
+            ++n_eval;
             const double old = u[j], oldn = nat[j];
             u[j] = up;
             nat[j] = natural_d(pr, up);
@@ -59,6 +61,7 @@ __global__ void __launch_bounds__(128) k_mh_plain(JobDev *jobs, const int *slots
         for (int j = 0; j < d; ++j) jb.th64[(size_t)j * T + m] = u[j];
         jb.E64[m] = Ec;
     }
+    atomicAdd(&jb.point_evals, n_eval * (unsigned long long)jb.n);
     for (int j = 0; j < d; ++j)
         if (jb.pri[j].kind != PR_FIXED) {
             atomicAdd(&jb.acc[j], (unsigned long long)acc[j]);

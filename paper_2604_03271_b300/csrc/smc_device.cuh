@@ -62,6 +62,10 @@ struct JobDev {
     int next_chain;  // dynamic work counter of the Metropolis kernel
     unsigned tag;
     unsigned long long seed;
+    // cumulative algorithmic work of the Metropolis kernel: grid-point
+    // evaluations of in-support proposals, and SFU operations of the
+    // shape-changing (centre, width) proposals among them
+    unsigned long long point_evals, sfu_ops;
 };
 
 // ---------------------------------------------------------------------------
