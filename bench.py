@@ -165,7 +165,7 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 1.0e11, "xrd": 1.0e13, "gauss": 5.0e8}
+UNITS_PER_SPECTRUM = {"xps": 7.6e11, "xrd": 1.0e13, "gauss": 8.0e8}
 
 
 # ---------------------------------------------------------------------------

@@ -491,7 +491,10 @@ static cudaError_t iteration(Ctx &c, const Plan &P, cudaEvent_t *ev, int k)
 {
     const int nall = (int)P.all.size();
     cudaError_t e;
-    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], c.stream) : cudaSuccess; };
+    auto mark = [&](int i) {
+        // external record nodes keep the events timeable when captured in a graph
+        return ev ? cudaEventRecordWithFlags(ev[i], c.stream, cudaEventRecordExternal) : cudaSuccess;
+    };
     if ((e = mark(0)) != cudaSuccess) return e;
     if ((e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
@@ -573,7 +576,10 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
             if (!ev.empty() && prev_active > 0) {
                 for (int q = 0; q < 5; ++q) {
                     float ms = 0.0f;
-                    cudaEventElapsedTime(&ms, ev[6 * k + q], ev[6 * k + q + 1]);
+                    if (cudaEventElapsedTime(&ms, ev[6 * k + q], ev[6 * k + q + 1]) != cudaSuccess) {
+                        cudaGetLastError();
+                        ms = 0.0f;
+                    }
                     c.prof.ms[q] += ms;
                     c.prof.launches[q] += (q == 3) ? (int64_t)P.buckets.size() : 1;
                 }
