@@ -42,6 +42,24 @@ int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double
                    int32_t precision, double *delta, double *logz_inc, int32_t *final_step,
                    uint64_t *q_out);
 
+/* Allocation-free variant of smc_k_reweight, for callers that cannot
+ * allocate device memory (a host framework that owns every allocation, or a
+ * service that must not grow device memory once running).  No counterpart in
+ * the paper: same kernel and results as smc_k_reweight, but the caller passes
+ * DEVICE arrays -- E_dev (T floats if precision is 0, T doubles if 1) and
+ * q_dev (T uint64 outputs) -- and the kernel's scratch (its job descriptor and
+ * FP64 weights) is a fixed static device array of this library, sized for at
+ * most SMC_STATIC_MAX_PARTICLES particles (about 8 MiB, held by every GPU that
+ * loads the library until exit).  Runs on the current device and cuda_stream
+ * (NULL = default stream) and returns after the stream has finished the step.
+ * T above the maximum returns SMC_EINVAL.  The first call on each device looks
+ * up the scratch address (cudaGetSymbolAddress); make it before any stream
+ * capture.  Calls share the scratch: calls that overlap on the GPU race. */
+#define SMC_STATIC_MAX_PARTICLES (1 << 20)
+int smc_k_reweight_static(const void *E_dev, int64_t T, double beta, double rho,
+                          int32_t precision, uint64_t *q_dev, double *delta, double *logz_inc,
+                          int32_t *final_step, void *cuda_stream);
+
 /* Systematic resampling of M ancestors from integer weights q[T] with the
  * uniform word u32: a_m = min{i : C_i > floor((m Q + floor(u32 Q / 2^32)) / M)},
  * C the inclusive prefix sum of q, Q = C_{T-1}. */
