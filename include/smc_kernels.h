@@ -76,6 +76,14 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
                    uint32_t stage, int32_t precision, double *nat_out, double *E_out,
                    int64_t *acc, int64_t *prop);
 
+/* Tile of the fused Metropolis kernel for FP32 jobs of `family` whose grid
+ * has at most n_max points: J points per lane (4, 8, 12, 16; also 24, 32 for
+ * Gaussian/Lorentzian) and G warps per chain (1, 2, 4, 8), 32 G J >= N.
+ * Entries are matched in the order they were set; the first whose family
+ * matches and n_max >= N wins; without a match a padding-minimising default
+ * is used.  J = 0 clears the table.  Used by the autotuner. */
+int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G);
+
 /* Profiling counters of a context, accumulated over the runs finished since
  * the last smc_profile_reset.  Kernel classes: 0 reweight (tempering step),
  * 1 resample, 2 gather (particle copy), 3 Metropolis, 4 stage end.  With

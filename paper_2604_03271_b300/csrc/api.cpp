@@ -732,6 +732,21 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
     return st;
 }
 
+int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G)
+{
+    if (!ctx) return SMC_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(ctx->c.mu);
+    if (J == 0) {
+        ctx->c.tiles.clear();
+        return SMC_OK;
+    }
+    if (family < 0 || family > 2 || n_max < 1 || !mh_tile_supported(family, J, G) ||
+        32L * J * G < 1)
+        return SMC_EINVAL;
+    ctx->c.tiles.push_back({family, n_max, J, G});
+    return SMC_OK;
+}
+
 int smc_profile_reset(smc_ctx *ctx, int32_t enable_events)
 {
     if (!ctx) return SMC_EINVAL;

@@ -95,7 +95,6 @@ static int comp_role(const Request &r, int K, int j)
 
 int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 {
-    (void)c;
     if (!rq.priors || !rq.opts || !rq.x || !rq.y || !rq.sigma) return SMC_EINVAL;
     const smc_options &o = *rq.opts;
     if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
@@ -141,6 +140,12 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     }
     if (!r->fp64) {
         r->tile = choose_tile(r->family, r->n);
+        for (const auto &t : c.tiles)
+            if (t[0] == r->family && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
+                mh_tile_supported(r->family, (int)t[2], (int)t[3])) {
+                r->tile = {(int)t[2], (int)t[3]};
+                break;
+            }
         if (r->tile.J == 0) {
             delete r;
             return SMC_EINVAL;  // grid too long for the FP32 tiles

@@ -9,6 +9,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
+#include <array>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -77,6 +78,8 @@ struct Ctx {
     int *d_nactive = nullptr;
     int *h_nactive = nullptr;      // pinned, device-mapped, one entry per stage of a chunk
     int *h_nactive_dev = nullptr;  // its device alias
+    // autotuned tiles: (family, n_max, J, G)
+    std::vector<std::array<int64_t, 4>> tiles;
     // profiling
     bool prof_events = false;
     smc_profile prof{};

@@ -106,7 +106,35 @@ __device__ __forceinline__ float group_energy(GroupCtx &g, const float *w, const
     return S - Cc;
 }
 
-__device__ __forceinline__ float sel(int h, float a0, float a1) { return h ? a1 : a0; }
+template <int FAM>
+__device__ __forceinline__ float sc2_of(float w)
+{
+    return (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / w : 1.0f / w;
+}
+
+// Per-warp copy of the chain's component state (every warp of a group keeps
+// an identical copy, so no cross-warp synchronisation is needed for it).
+struct WarpComp {
+    float th[SMC_DMAX];   // current value, sampling coordinate
+    float nat[SMC_DMAX];  // current value, natural
+    float un[SMC_DMAX];   // this sweep's proposal, sampling coordinate
+    float vn[SMC_DMAX];   // this sweep's proposal, natural
+    float thr[SMC_DMAX];  // accept iff thr < -beta dE (INFINITY: not proposed)
+    unsigned acc[SMC_DMAX];
+};
+
+// Chebyshev T_q(t) by the three-term recurrence
+__device__ __forceinline__ float cheb(int q, float t)
+{
+    if (q == 0) return 1.0f;
+    float a = 1.0f, b = t;
+    for (int e = 2; e <= q; ++e) {
+        const float c = fmaf(2.0f * t, b, -a);
+        a = b;
+        b = c;
+    }
+    return b;
+}
 
 template <int FAM, int J>
 __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots,
@@ -114,6 +142,7 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
 {
     __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
+    __shared__ WarpComp comp_sh[8];
     GroupCtx g;
     g.lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -125,6 +154,7 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
     if (g.grp >= ngroups) return;
     g.red = &red_sh[g.grp][0][0];
     const int lane = g.lane;
+    WarpComp &cs = comp_sh[warp];
     constexpr int P = (FAM == FAM_PV) ? 4 : 3;
 
     int li = 0;
@@ -167,48 +197,31 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
         const float beta = (float)jb.beta;
         const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
         const unsigned long long seed = jb.seed;
+        const int base = g.gw * 32 + lane;
+        const int stride = 32 * G;
 
-        // ---- grid points of this lane
+        // ---- components of the chain start
+        for (int j = lane; j < d; j += 32) {
+            const float u = jb.ths[(size_t)j * S + m];
+            cs.th[j] = u;
+            cs.nat[j] = natural_f(jb.pri[j], u);
+            cs.acc[j] = 0u;
+        }
+        __syncwarp();
+
+        // ---- grid points of this lane and the residual r = y - f(theta)
         float x[J], w[J], r[J], S0[J], S1[J], N0[J], N1[J];
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) {
-            const int i = g.gw * 32 + lane + jj * 32 * G;
+            const int i = base + jj * stride;
             x[jj] = __ldg(jb.xc + i);
             w[jj] = __ldg(jb.wt + i);
             r[jj] = __ldg(jb.y + i);
         }
-        // ---- components held by this lane (j = lane, lane + 32)
-        float th[2], nat[2], stp[2];
-        int kind[2];
-        float plo[2], phi[2], pa[2], pb[2];
-        unsigned acc[2] = {0u, 0u}, prp[2] = {0u, 0u};
-        unsigned long long n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = lane + 32 * h;
-            if (j < d) {
-                const PriorDev &pr = jb.pri[j];
-                kind[h] = pr.kind;
-                plo[h] = pr.lof;
-                phi[h] = pr.hif;
-                pa[h] = pr.a;
-                pb[h] = pr.b;
-                th[h] = jb.ths[(size_t)j * S + m];
-                nat[h] = natural_f(pr, th[h]);
-                stp[h] = jb.stepf[j];
-            } else {
-                kind[h] = PR_FIXED;
-                th[h] = nat[h] = stp[h] = plo[h] = phi[h] = pa[h] = pb[h] = 0.0f;
-            }
-        }
-        // ---- residual r = y - f(theta)
         for (int k = 0; k < K; ++k) {
             const int j0 = k * P;
-            const float A = __shfl_sync(FULL_MASK, sel(j0 >> 5, nat[0], nat[1]), j0 & 31);
-            const float mu = __shfl_sync(FULL_MASK, sel((j0 + 1) >> 5, nat[0], nat[1]), (j0 + 1) & 31);
-            const float wd = __shfl_sync(FULL_MASK, sel((j0 + 2) >> 5, nat[0], nat[1]), (j0 + 2) & 31);
-            float eta = 0.0f;
-            if (FAM == FAM_PV) eta = __shfl_sync(FULL_MASK, sel((j0 + 3) >> 5, nat[0], nat[1]), (j0 + 3) & 31);
+            const float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
+            const float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
             const float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
 #pragma unroll
             for (int jj = 0; jj < J; ++jj) {
@@ -218,68 +231,39 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
             }
         }
         for (int q = 0; q < nbg; ++q) {
-            const int jq = K * P + q;
-            const float cq = __shfl_sync(FULL_MASK, sel(jq >> 5, nat[0], nat[1]), jq & 31);
+            const float cq = cs.nat[K * P + q];
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) {
-                const int i = g.gw * 32 + lane + jj * 32 * G;
-                const float t = __ldg(jb.ts + i);
-                float a = 1.0f, b = t, tq = 1.0f;
-                if (q == 1) tq = t;
-                for (int e = 2; e <= q; ++e) {
-                    tq = fmaf(2.0f * t, b, -a);
-                    a = b;
-                    b = tq;
-                }
-                r[jj] -= cq * tq;
-            }
+            for (int jj = 0; jj < J; ++jj) r[jj] -= cq * cheb(q, __ldg(jb.ts + base + jj * stride));
         }
 
+        unsigned long long n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
         for (int sw = 0; sw < n; ++sw) {
-            // ---- this lane's proposals for the sweep
-            float thr[2], un[2], vn[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                thr[h] = INFINITY;
-                un[h] = vn[h] = 0.0f;
-                if (kind[h] != PR_FIXED) {
+            // ---- this sweep's proposals: lane j draws component j
+            for (int j = lane; j < d; j += 32) {
+                const PriorDev &pr = jb.pri[j];
+                float thr = INFINITY, u = 0.0f, v = 0.0f;
+                if (pr.kind != PR_FIXED) {
                     const uint4 wv = draw(seed, (uint32_t)(sw * d + j), (uint32_t)m, stage, tag);
                     const float z = box_muller_f(wv.x, wv.y);
                     const float lu = logf(u01f(wv.z));
-                    const float u = fmaf(stp[h], z, th[h]);
-                    prp[h] += 1u;
-                    un[h] = u;
-                    bool ok;
-                    if (kind[h] == PR_UNIFORM || kind[h] == PR_LOG_UNIFORM)
-                        ok = u >= plo[h] && u <= phi[h];
-                    else if (kind[h] == PR_GAMMA)
-                        ok = u > 0.0f;
-                    else
-                        ok = true;
-                    if (ok) {
-                        float dlp = 0.0f;
-                        if (kind[h] == PR_NORMAL) {
-                            const float z1 = (u - pa[h]) / pb[h], z0 = (th[h] - pa[h]) / pb[h];
-                            dlp = -0.5f * (z1 * z1 - z0 * z0);
-                        } else if (kind[h] == PR_GAMMA) {
-                            dlp = (pa[h] - 1.0f) * (logf(u) - logf(th[h])) - pb[h] * (u - th[h]);
-                        }
-                        thr[h] = lu - dlp;
-                        vn[h] = kind[h] == PR_LOG_UNIFORM ? expf(u) : u;
+                    const float t0 = cs.th[j];
+                    u = fmaf(jb.stepf[j], z, t0);
+                    if (in_support_f(pr, u)) {
+                        thr = lu - (log_prior_f(pr, u) - log_prior_f(pr, t0));
+                        v = pr.kind == PR_LOG_UNIFORM ? expf(u) : u;
                     }
                 }
+                cs.thr[j] = thr;
+                cs.un[j] = u;
+                cs.vn[j] = v;
             }
+            __syncwarp();
 
             // ---- peak blocks
             for (int k = 0; k < K; ++k) {
                 const int j0 = k * P;
-                float A = __shfl_sync(FULL_MASK, sel(j0 >> 5, nat[0], nat[1]), j0 & 31);
-                float mu = __shfl_sync(FULL_MASK, sel((j0 + 1) >> 5, nat[0], nat[1]), (j0 + 1) & 31);
-                float wd = __shfl_sync(FULL_MASK, sel((j0 + 2) >> 5, nat[0], nat[1]), (j0 + 2) & 31);
-                float eta = 0.0f;
-                if (FAM == FAM_PV)
-                    eta = __shfl_sync(FULL_MASK, sel((j0 + 3) >> 5, nat[0], nat[1]), (j0 + 3) & 31);
+                float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
+                float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
                 float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
@@ -287,28 +271,31 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                     shape<FAM>(x[jj], mu, sc, S0[jj], S1[jj]);
                 }
                 for (int c = 0; c < P; ++c) {
-                    const int j = j0 + c, src = j & 31, h = j >> 5;
-                    const float tj = __shfl_sync(FULL_MASK, sel(h, thr[0], thr[1]), src);
+                    const int j = j0 + c;
+                    const float tj = cs.thr[j];
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
-                    const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
+                    const float v = cs.vn[j];
                     ++n_eval;
-                    if (c == 1 || c == 2) ++n_shape;
-                    float part = 0.0f;
+                    // two independent accumulators shorten the FMA dependency chain
+                    float p0 = 0.0f, p1 = 0.0f;
                     if (c == 0) {  // amplitude: D = (A' - A) u
                         const float dA = v - A;
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             const float D = dA * unit<FAM>(S0[jj], S1[jj], eta);
-                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
+                            if (jj & 1) p1 += t; else p0 += t;
                         }
                     } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
                         const float dd = A * (v - eta);
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             const float D = dd * S0[jj];
-                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
+                            if (jj & 1) p1 += t; else p0 += t;
                         }
                     } else {  // centre or width: new shape
+                        ++n_shape;
                         const float mu2 = (c == 1) ? v : mu;
                         const float sc2 = (c == 2) ? ((FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v) : sc;
 #pragma unroll
@@ -316,14 +303,16 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                             N1[jj] = 0.0f;
                             shape<FAM>(x[jj], mu2, sc2, N0[jj], N1[jj]);
                             const float D = A * (unit<FAM>(N0[jj], N1[jj], eta) - unit<FAM>(S0[jj], S1[jj], eta));
-                            part = fmaf(w[jj] * D, fmaf(-2.0f, r[jj], D), part);
+                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
+                            if (jj & 1) p1 += t; else p0 += t;
                         }
                     }
-                    const float dE = 0.5f * group_sum(g, part);
+                    const float dE = 0.5f * group_sum(g, p0 + p1);
                     if (tj < -beta * dE) {
                         if (c == 0) {
+                            const float dA = v - A;
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] -= (v - A) * unit<FAM>(S0[jj], S1[jj], eta);
+                            for (int jj = 0; jj < J; ++jj) r[jj] -= dA * unit<FAM>(S0[jj], S1[jj], eta);
                             A = v;
                         } else if (c == 3) {
                             const float dd = A * (v - eta);
@@ -337,65 +326,54 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
                                 S0[jj] = N0[jj];
                                 S1[jj] = N1[jj];
                             }
-                            if (c == 1)
+                            if (c == 1) {
                                 mu = v;
-                            else {
+                            } else {
                                 wd = v;
-                                sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v;
+                                sc = sc2_of<FAM>(v);
                             }
                         }
-                        if (lane == src) {
-                            th[h] = sel(h, un[0], un[1]);
-                            nat[h] = v;
-                            acc[h] += 1u;
+                        if (lane == 0) {
+                            cs.th[j] = cs.un[j];
+                            cs.nat[j] = v;
+                            cs.acc[j] += 1u;
                         }
+                        __syncwarp();
                     }
                 }
             }
             // ---- background coefficients: D = (c' - c) T_q(t)
             for (int q = 0; q < nbg; ++q) {
-                const int j = K * P + q, src = j & 31, h = j >> 5;
-                const float tj = __shfl_sync(FULL_MASK, sel(h, thr[0], thr[1]), src);
+                const int j = K * P + q;
+                const float tj = cs.thr[j];
                 if (tj == INFINITY) continue;
-                const float v = __shfl_sync(FULL_MASK, sel(h, vn[0], vn[1]), src);
-                const float cq = __shfl_sync(FULL_MASK, sel(h, nat[0], nat[1]), src);
+                const float v = cs.vn[j];
+                const float dc = v - cs.nat[j];
                 ++n_eval;
-                const float dc = v - cq;
-                float part = 0.0f;
+                float p0 = 0.0f, p1 = 0.0f;
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
-                    const int i = g.gw * 32 + lane + jj * 32 * G;
-                    const float t = __ldg(jb.ts + i);
-                    float a = 1.0f, b = t, tq = 1.0f;
-                    if (q == 1) tq = t;
-                    for (int e = 2; e <= q; ++e) {
-                        tq = fmaf(2.0f * t, b, -a);
-                        a = b;
-                        b = tq;
-                    }
-                    N0[jj] = dc * tq;
-                    part = fmaf(w[jj] * N0[jj], fmaf(-2.0f, r[jj], N0[jj]), part);
+                    N0[jj] = dc * cheb(q, __ldg(jb.ts + base + jj * stride));
+                    const float t = w[jj] * N0[jj] * fmaf(-2.0f, r[jj], N0[jj]);
+                    if (jj & 1) p1 += t; else p0 += t;
                 }
-                const float dE = 0.5f * group_sum(g, part);
+                const float dE = 0.5f * group_sum(g, p0 + p1);
                 if (tj < -beta * dE) {
 #pragma unroll
                     for (int jj = 0; jj < J; ++jj) r[jj] -= N0[jj];
-                    if (lane == src) {
-                        th[h] = sel(h, un[0], un[1]);
-                        nat[h] = v;
-                        acc[h] += 1u;
+                    if (lane == 0) {
+                        cs.th[j] = cs.un[j];
+                        cs.nat[j] = v;
+                        cs.acc[j] += 1u;
                     }
+                    __syncwarp();
                 }
             }
             if (wf) {
                 const float E = group_energy<J>(g, w, r);
                 const size_t o = (size_t)m * n + sw;
                 if (g.gw == 0) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = lane + 32 * h;
-                        if (j < d) jb.th[(size_t)j * T + o] = th[h];
-                    }
+                    for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
                     if (lane == 0) jb.E[o] = E;
                 }
             }
@@ -403,29 +381,23 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
         if (!wf) {
             const float E = group_energy<J>(g, w, r);
             if (g.gw == 0) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = lane + 32 * h;
-                    if (j < d) jb.th[(size_t)j * T + m] = th[h];
-                }
+                for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
                 if (lane == 0) jb.E[m] = E;
             }
         }
         if (g.gw == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                if (j < d && kind[h] != PR_FIXED) {
-                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)acc[h]);
-                    atomicAdd(&jobs[slot].prop[j], (unsigned long long)prp[h]);
+            for (int j = lane; j < d; j += 32)
+                if (jb.pri[j].kind != PR_FIXED) {
+                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)cs.acc[j]);
+                    atomicAdd(&jobs[slot].prop[j], (unsigned long long)n);
                 }
-            }
             if (lane == 0) {
                 const unsigned long long npts = (unsigned long long)jb.n;
                 atomicAdd(&jobs[slot].point_evals, n_eval * npts);
                 atomicAdd(&jobs[slot].sfu_ops, n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
             }
         }
+        __syncwarp();
     }
 }
 
