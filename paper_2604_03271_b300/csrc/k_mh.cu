@@ -136,9 +136,20 @@ __device__ __forceinline__ float cheb(int q, float t)
     return b;
 }
 
-template <int FAM, int J>
-__global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots,
-                                               int nslots, int G)
+// Register budget per tile: blocks of NT threads, at least MINB of them
+// resident per SM (J <= 8: 128 registers; J = 12, and J = 16 without the
+// Lorentzian+Gaussian pair of PV: 170; otherwise up to 255), chosen so that
+// no tile spills.
+template <int FAM, int J, int NT>
+struct MhBounds {
+    static constexpr int MINB =
+        (NT == 128) ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2)) : (J <= 8 ? 2 : 1);
+};
+
+template <int FAM, int J, int NT>
+__global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev *__restrict__ jobs,
+                                                                  const int *__restrict__ slots,
+                                                                  int nslots, int G)
 {
     __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
@@ -406,37 +417,44 @@ __global__ void __launch_bounds__(256, 1) k_mh(JobDev *__restrict__ jobs, const 
 // ---------------------------------------------------------------------------
 typedef void (*mh_fn)(JobDev *, const int *, int, int);
 
-template <int FAM>
+static int block_threads(int G) { return G <= 4 ? 128 : 256; }
+
+template <int FAM, int NT>
 static mh_fn pick_j(int J)
 {
     switch (J) {
-    case 4: return k_mh<FAM, 4>;
-    case 8: return k_mh<FAM, 8>;
-    case 12: return k_mh<FAM, 12>;
-    case 16: return k_mh<FAM, 16>;
-    case 24: return FAM == FAM_PV ? nullptr : k_mh<FAM, 24>;
-    case 32: return FAM == FAM_PV ? nullptr : k_mh<FAM, 32>;
+    case 4: return k_mh<FAM, 4, NT>;
+    case 8: return k_mh<FAM, 8, NT>;
+    case 12: return k_mh<FAM, 12, NT>;
+    case 16: return k_mh<FAM, 16, NT>;
+    case 24:
+        if constexpr (FAM != FAM_PV && NT == 128) return k_mh<FAM, 24, NT>;
+        return nullptr;
+    case 32:
+        if constexpr (FAM != FAM_PV && NT == 128) return k_mh<FAM, 32, NT>;
+        return nullptr;
     default: return nullptr;
     }
 }
 
-static mh_fn pick(int family, int J)
+static mh_fn pick(int family, int J, int G)
 {
-    if (family == FAM_GAUSS) return pick_j<FAM_GAUSS>(J);
-    if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ>(J);
-    return pick_j<FAM_PV>(J);
+    if (!(G == 1 || G == 2 || G == 4 || G == 8)) return nullptr;
+    if (block_threads(G) == 128) {
+        if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 128>(J);
+        if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 128>(J);
+        return pick_j<FAM_PV, 128>(J);
+    }
+    if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 256>(J);
+    if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 256>(J);
+    return pick_j<FAM_PV, 256>(J);
 }
 
-static int block_threads(int G) { return 32 * (G < 4 ? 4 : G); }
-
-bool mh_tile_supported(int family, int J, int G)
-{
-    return pick(family, J) != nullptr && (G == 1 || G == 2 || G == 4 || G == 8);
-}
+bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
 
 int mh_resident_grid(int family, int J, int G)
 {
-    mh_fn f = pick(family, J);
+    mh_fn f = pick(family, J, G);
     if (!f) return 0;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -449,8 +467,8 @@ int mh_resident_grid(int family, int J, int G)
 cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
                       int grid, cudaStream_t s)
 {
-    mh_fn f = pick(family, J);
-    if (!f || !(G == 1 || G == 2 || G == 4 || G == 8)) return cudaErrorInvalidValue;
+    mh_fn f = pick(family, J, G);
+    if (!f) return cudaErrorInvalidValue;
     if (nslots <= 0) return cudaSuccess;
     if (grid <= 0) grid = mh_resident_grid(family, J, G);
     f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots, G);
