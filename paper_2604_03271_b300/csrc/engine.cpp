@@ -36,22 +36,27 @@ int job_dim(int family, int K, int bg, int deg) { return peak_params(family) * K
 // ---------------------------------------------------------------------------
 Tile choose_tile(int family, int n)
 {
-    static const int Js_pv[] = {4, 8, 12, 16};
-    static const int Js_gl[] = {4, 8, 12, 16, 24, 32};
+    // measured on B300 (XPS-shaped N = 1001): PV fastest at J = 8 (127
+    // registers, 16 warps/SM), Gaussian / Lorentzian at J = 16 (~160
+    // registers, 12 warps/SM); other J only when they pad much less
+    static const int Js_pv[] = {8, 4, 12, 16};
+    static const int Js_gl[] = {16, 8, 12, 4, 24, 32};
     const int *Js = family == SMC_PSEUDO_VOIGT ? Js_pv : Js_gl;
     const int nJ = family == SMC_PSEUDO_VOIGT ? 4 : 6;
     Tile best{0, 0};
-    long best_pad = -1;
-    for (int G : {1, 2, 4, 8})
-        for (int a = 0; a < nJ; ++a) {
+    double best_cost = -1.0;
+    for (int a = 0; a < nJ; ++a)
+        for (int G : {1, 2, 4, 8}) {
             const int J = Js[a];
+            if (!mh_tile_supported(family, J, G)) continue;
             const long pad = 32L * G * J;
             if (pad < n) continue;
-            if (J > 16 && G > 1) continue;  // large J only for one-warp chains
-            if (best_pad < 0 || pad < best_pad || (pad == best_pad && G < best.G)) {
+            const double cost = (double)pad * (1.0 + 0.1 * a);  // preferred J first
+            if (best_cost < 0.0 || cost < best_cost) {
                 best = {J, G};
-                best_pad = pad;
+                best_cost = cost;
             }
+            break;  // smallest G for this J
         }
     return best;
 }

@@ -41,9 +41,11 @@ __device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, fl
     }
 }
 
-// unit-amplitude profile from the cached shapes
+// Cached per point during a peak's block: S0 = G - L (PV) or the unit shape
+// (Gaussian / Lorentzian), and for PV U = eta (G - L) + L, the unit-amplitude
+// profile; the current peak contributes A U (A S0 for the other families).
 template <int FAM>
-__device__ __forceinline__ float unit(float S0, float S1, float eta)
+__device__ __forceinline__ float unit_of(float S0, float S1, float eta)
 {
     return FAM == FAM_PV ? fmaf(eta, S0, S1) : S0;
 }
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
             for (int jj = 0; jj < J; ++jj) {
                 float a0, a1 = 0.0f;
                 shape<FAM>(x[jj], mu, sc, a0, a1);
-                r[jj] -= A * unit<FAM>(a0, a1, eta);
+                r[jj] -= A * unit_of<FAM>(a0, a1, eta);
             }
         }
         for (int q = 0; q < nbg; ++q) {
@@ -278,8 +280,9 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                 float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
-                    S1[jj] = 0.0f;
-                    shape<FAM>(x[jj], mu, sc, S0[jj], S1[jj]);
+                    float l = 0.0f;
+                    shape<FAM>(x[jj], mu, sc, S0[jj], l);
+                    if (FAM == FAM_PV) S1[jj] = fmaf(eta, S0[jj], l);  // U
                 }
                 for (int c = 0; c < P; ++c) {
                     const int j = j0 + c;
@@ -289,33 +292,43 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                     ++n_eval;
                     // two independent accumulators shorten the FMA dependency chain
                     float p0 = 0.0f, p1 = 0.0f;
-                    if (c == 0) {  // amplitude: D = (A' - A) u
+                    if (c == 0) {  // amplitude: D = (A' - A) U
                         const float dA = v - A;
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
-                            const float D = dA * unit<FAM>(S0[jj], S1[jj], eta);
-                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
-                            if (jj & 1) p1 += t; else p0 += t;
+                            const float D = dA * (FAM == FAM_PV ? S1[jj] : S0[jj]);
+                            const float wd2 = w[jj] * D;
+                            if (jj & 1)
+                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                            else
+                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
                         }
                     } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
                         const float dd = A * (v - eta);
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             const float D = dd * S0[jj];
-                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
-                            if (jj & 1) p1 += t; else p0 += t;
+                            const float wd2 = w[jj] * D;
+                            if (jj & 1)
+                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                            else
+                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
                         }
-                    } else {  // centre or width: new shape
+                    } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
                         const float mu2 = (c == 1) ? v : mu;
-                        const float sc2 = (c == 2) ? ((FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v) : sc;
+                        const float sc2 = (c == 2) ? sc2_of<FAM>(v) : sc;
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
-                            N1[jj] = 0.0f;
-                            shape<FAM>(x[jj], mu2, sc2, N0[jj], N1[jj]);
-                            const float D = A * (unit<FAM>(N0[jj], N1[jj], eta) - unit<FAM>(S0[jj], S1[jj], eta));
-                            const float t = w[jj] * D * fmaf(-2.0f, r[jj], D);
-                            if (jj & 1) p1 += t; else p0 += t;
+                            float l = 0.0f;
+                            shape<FAM>(x[jj], mu2, sc2, N0[jj], l);
+                            if (FAM == FAM_PV) N1[jj] = fmaf(eta, N0[jj], l);
+                            const float D = A * (FAM == FAM_PV ? N1[jj] - S1[jj] : N0[jj] - S0[jj]);
+                            const float wd2 = w[jj] * D;
+                            if (jj & 1)
+                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                            else
+                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
                         }
                     }
                     const float dE = 0.5f * group_sum(g, p0 + p1);
@@ -323,19 +336,27 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                         if (c == 0) {
                             const float dA = v - A;
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] -= dA * unit<FAM>(S0[jj], S1[jj], eta);
+                            for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(-dA, FAM == FAM_PV ? S1[jj] : S0[jj], r[jj]);
                             A = v;
                         } else if (c == 3) {
-                            const float dd = A * (v - eta);
+                            const float de = v - eta;
+                            const float dd = A * de;
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] -= dd * S0[jj];
+                            for (int jj = 0; jj < J; ++jj) {
+                                r[jj] = fmaf(-dd, S0[jj], r[jj]);
+                                S1[jj] = fmaf(de, S0[jj], S1[jj]);
+                            }
                             eta = v;
                         } else {
 #pragma unroll
                             for (int jj = 0; jj < J; ++jj) {
-                                r[jj] -= A * (unit<FAM>(N0[jj], N1[jj], eta) - unit<FAM>(S0[jj], S1[jj], eta));
+                                if (FAM == FAM_PV) {
+                                    r[jj] = fmaf(-A, N1[jj] - S1[jj], r[jj]);
+                                    S1[jj] = N1[jj];
+                                } else {
+                                    r[jj] = fmaf(-A, N0[jj] - S0[jj], r[jj]);
+                                }
                                 S0[jj] = N0[jj];
-                                S1[jj] = N1[jj];
                             }
                             if (c == 1) {
                                 mu = v;
@@ -365,8 +386,11 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
                     N0[jj] = dc * cheb(q, __ldg(jb.ts + base + jj * stride));
-                    const float t = w[jj] * N0[jj] * fmaf(-2.0f, r[jj], N0[jj]);
-                    if (jj & 1) p1 += t; else p0 += t;
+                    const float wd2 = w[jj] * N0[jj];
+                    if (jj & 1)
+                        p1 = fmaf(wd2, fmaf(-2.0f, r[jj], N0[jj]), p1);
+                    else
+                        p0 = fmaf(wd2, fmaf(-2.0f, r[jj], N0[jj]), p0);
                 }
                 const float dE = 0.5f * group_sum(g, p0 + p1);
                 if (tj < -beta * dE) {
