@@ -28,7 +28,7 @@ constexpr int MH_MAX_GROUPS = 8;
 template <int FAM>
 __device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, float &S1)
 {
-    const float t = (x - mu) * sc;
+    const float t = fmaf(x, sc, -mu * sc);
     const float t2 = t * t;
     if (FAM == FAM_GAUSS) {
         S0 = ex2_approx(-t2);
