@@ -295,3 +295,25 @@ def test_max_stages_reported(ctx):
     assert np.all(r["job_status"] == 5) and np.all(r["n_stages"] == 2)
     ref = oracle.run_job(spec, 2, W.Options(particles=128, sweeps=1, seed=1, max_stages=2))
     assert ref["status"] == oracle.EMAXSTAGES
+
+
+# --------------------------------------------------------------------------
+# XPS-shaped workload (pseudo-Voigt + linear background, offset axis) at
+# reduced size: FP32 batched path vs the FP64 path over seeds
+# --------------------------------------------------------------------------
+
+def test_xps_shaped_fp32_vs_fp64_statistical(ctx):
+    spec = W.xps_like(7, n=301, k_true=2, k_max=3)
+    lz32, lz64 = [], []
+    for s in range(1, 9):
+        o32 = W.Options(particles=1024, sweeps=4, seed=s)
+        o64 = W.Options(particles=1024, sweeps=4, seed=s, energy_fp64=1)
+        lz32.append(ctx.run(spec, o32, keep_samples=False)["log_z"])
+        lz64.append(ctx.run(spec, o64, keep_samples=False)["log_z"])
+    ref = oracle.run(spec, W.Options(particles=1024, sweeps=4, seed=1))
+    np.testing.assert_allclose(lz64[0], ref["log_z"], atol=1e-6)
+    lz32, lz64 = np.array(lz32), np.array(lz64)
+    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 8)
+    diff = np.abs(lz32.mean(0) - lz64.mean(0))
+    assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
+    assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0))

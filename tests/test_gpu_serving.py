@@ -1,0 +1,75 @@
+"""Serving loop: continuous batching of submitted requests.
+
+Requests submitted while others run are admitted as memory allows, share the
+same launches, and each result is identical to the same request run alone
+(per-job random streams and fixed-order reductions; tolerance 0)."""
+import numpy as np
+import pytest
+
+from paper_2604_03271_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    out = []
+    for i in range(6):
+        if i % 2 == 0:
+            s = W.gaussian_small(i + 1)
+            o = W.Options(particles=512 * (1 + i % 3), sweeps=3, seed=100 + i)
+        else:
+            s = W.xps_like(i, n=400, k_true=2, k_max=3)
+            o = W.Options(particles=1024, sweeps=2, seed=200 + i)
+        out.append((s, o))
+    return out
+
+
+def test_served_results_equal_alone_results():
+    from paper_2604_03271_b300 import api
+    reqs = _requests()
+    with api.Context(0) as ctx:
+        alone = [ctx.run(s, o, keep_samples=False) for s, o in reqs]
+        jobs = []
+        for s, o in reqs:
+            jobs.append(ctx.submit(s, o))
+        for j in jobs:
+            ctx.wait(j, 120.0)
+        served = []
+        for j, (s, _) in zip(jobs, reqs):
+            served.append(ctx.result(j, s))
+            ctx.release(j)
+    for a, b in zip(alone, served):
+        assert b["status"] == 0
+        np.testing.assert_array_equal(a["log_z"], b["log_z"])
+        np.testing.assert_array_equal(a["n_stages"], b["n_stages"])
+        for x, y in zip(a["post_mean"], b["post_mean"]):
+            np.testing.assert_array_equal(x, y)
+        assert b["latency_ms"] > 0
+
+
+def test_admission_by_memory_budget():
+    from paper_2604_03271_b300 import api
+    reqs = _requests()[:4]
+    # a budget that holds one request at a time forces sequential admission
+    with api.Context(0, mem_budget_bytes=96 << 20) as ctx:
+        jobs = [ctx.submit(s, o) for s, o in reqs]
+        for j in jobs:
+            ctx.wait(j, 120.0)
+        for j, (s, _) in zip(jobs, reqs):
+            r = ctx.result(j, s)
+            assert r["status"] == 0
+            ctx.release(j)
+
+
+def test_oversized_request_fails_cleanly():
+    from paper_2604_03271_b300 import api
+    s, o = W.gaussian_small(1), W.Options(particles=1 << 20, sweeps=2, seed=1)
+    with api.Context(0, mem_budget_bytes=8 << 20) as ctx:
+        j = ctx.submit(s, o)
+        ctx.wait(j, 30.0)
+        with pytest.raises(api.SmcError) as e:
+            r = ctx.result(j, s)
+            if r["status"] != 0:
+                raise api.SmcError(r["status"], "request")
+        assert e.value.status == api.SMC_ENOMEM
+        ctx.release(j)
