@@ -204,13 +204,17 @@ class Context:
         _check(self._L.smc_result(self.h, C.c_uint64(job), C.byref(v)), "smc_result")
         nK = v.k_max - v.k_min + 1
         ks = list(range(v.k_min, v.k_max + 1))
+        out = {"K": ks, "status": v.status, "latency_ms": v.latency_ms, "n_samples": v.n_samples}
+        if not v.log_z:  # the request failed before producing results
+            out.update({"log_z": None, "p_k": None, "n_stages": None, "job_status": None,
+                        "post_mean": None, "post_sd": None, "argmax_k": None})
+            return out
         dm = v.dim_max
         log_z = np.ctypeslib.as_array(v.log_z, (nK,)).copy()
-        out = {"K": ks, "status": v.status, "log_z": log_z,
-               "p_k": np.ctypeslib.as_array(v.p_k, (nK,)).copy(),
-               "n_stages": np.ctypeslib.as_array(v.n_stages, (nK,)).copy(),
-               "job_status": np.ctypeslib.as_array(v.job_status, (nK,)).copy(),
-               "latency_ms": v.latency_ms, "n_samples": v.n_samples}
+        out.update({"log_z": log_z,
+                    "p_k": np.ctypeslib.as_array(v.p_k, (nK,)).copy(),
+                    "n_stages": np.ctypeslib.as_array(v.n_stages, (nK,)).copy(),
+                    "job_status": np.ctypeslib.as_array(v.job_status, (nK,)).copy()})
         mean = np.ctypeslib.as_array(v.post_mean, (nK, dm))
         sd = np.ctypeslib.as_array(v.post_sd, (nK, dm))
         dims = [_dim(spec.family, K, spec.bg, spec.bg_degree) for K in ks]

@@ -46,7 +46,7 @@ Tile choose_tile(int family, int n)
     Tile best{0, 0};
     double best_cost = -1.0;
     for (int a = 0; a < nJ; ++a)
-        for (int G : {1, 2, 4, 8}) {
+        for (int G : {1, 2, 4, 8, 16}) {
             const int J = Js[a];
             if (!mh_tile_supported(family, J, G)) continue;
             const long pad = 32L * G * J;

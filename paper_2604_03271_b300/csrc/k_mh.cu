@@ -23,7 +23,7 @@
 
 namespace smc {
 
-constexpr int MH_MAX_GROUPS = 8;
+constexpr int MH_MAX_GROUPS = 16;  // warps per chain at most, and chains per block at most
 
 template <int FAM>
 __device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, float &S1)
@@ -144,8 +144,9 @@ __device__ __forceinline__ float cheb(int q, float t)
 // no tile spills.
 template <int FAM, int J, int NT>
 struct MhBounds {
-    static constexpr int MINB =
-        (NT == 128) ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2)) : (J <= 8 ? 2 : 1);
+    static constexpr int MINB = (NT == 128)   ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2))
+                                : (NT == 256) ? (J <= 8 ? 2 : 1)
+                                              : 1;
 };
 
 template <int FAM, int J, int NT>
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
 {
     __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
-    __shared__ WarpComp comp_sh[8];
+    __shared__ WarpComp comp_sh[NT / 32];
     GroupCtx g;
     g.lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
 // ---------------------------------------------------------------------------
 typedef void (*mh_fn)(JobDev *, const int *, int, int);
 
-static int block_threads(int G) { return G <= 4 ? 128 : 256; }
+static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 
 template <int FAM, int NT>
 static mh_fn pick_j(int J)
@@ -449,8 +450,12 @@ static mh_fn pick_j(int J)
     switch (J) {
     case 4: return k_mh<FAM, 4, NT>;
     case 8: return k_mh<FAM, 8, NT>;
-    case 12: return k_mh<FAM, 12, NT>;
-    case 16: return k_mh<FAM, 16, NT>;
+    case 12:
+        if constexpr (NT <= 256) return k_mh<FAM, 12, NT>;
+        return nullptr;
+    case 16:
+        if constexpr (NT <= 256) return k_mh<FAM, 16, NT>;
+        return nullptr;
     case 24:
         if constexpr (FAM != FAM_PV && NT == 128) return k_mh<FAM, 24, NT>;
         return nullptr;
@@ -463,7 +468,13 @@ static mh_fn pick_j(int J)
 
 static mh_fn pick(int family, int J, int G)
 {
-    if (!(G == 1 || G == 2 || G == 4 || G == 8)) return nullptr;
+    if (!(G == 1 || G == 2 || G == 4 || G == 8 || G == 16)) return nullptr;
+    if (G == 16) {  // 512-thread chains: only the 128-register tiles fit
+        if (J > 8) return nullptr;
+        if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 512>(J);
+        if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 512>(J);
+        return pick_j<FAM_PV, 512>(J);
+    }
     if (block_threads(G) == 128) {
         if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 128>(J);
         if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 128>(J);

@@ -67,9 +67,6 @@ def test_oversized_request_fails_cleanly():
     with api.Context(0, mem_budget_bytes=8 << 20) as ctx:
         j = ctx.submit(s, o)
         ctx.wait(j, 30.0)
-        with pytest.raises(api.SmcError) as e:
-            r = ctx.result(j, s)
-            if r["status"] != 0:
-                raise api.SmcError(r["status"], "request")
-        assert e.value.status == api.SMC_ENOMEM
+        r = ctx.result(j, s)
+        assert r["status"] == api.SMC_ENOMEM and r["log_z"] is None
         ctx.release(j)
