@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2604_03271_b300 import workloads as W  # noqa: E402
+from paper_2604_03271_b300.sharding import max_over_ranks, shard_seeds  # noqa: E402
 
 METRIC = "spectra/s (all candidate K per spectrum, |dlogZ|<=0.05 vs FP64)"
 SM_COUNT = 148
@@ -203,15 +204,13 @@ def main():
 
     stream = torch.cuda.current_stream(dev)
     ctx = api.Context(local, stream=stream.cuda_stream)
+    from paper_2604_03271_b300 import autotune
+    n_tiles = autotune.load(ctx)  # tuned Metropolis tiles, if a table is present
     B = args.batch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def batch_for(step: int):
-        items = []
-        for b in range(B):
-            seed = 1 + (step * world + rank) * B + b
-            items.append(workload(args.workload, seed))
-        return items
+        return [workload(args.workload, seed) for seed in shard_seeds(step, world, rank, B)]
 
     def to_dev(items):
         out = []
@@ -249,11 +248,7 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     prof = ctx.profile()
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     spectra = args.steps * B * world
     value = spectra / (total_ms / 1000.0)
 
@@ -268,10 +263,7 @@ def main():
         ctx.run_batch(items, keep_samples=False)
         e2e_ms += 1000.0 * (time.perf_counter() - t0)
     prof_e2e = ctx.profile()
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     e2e = {"value": spectra / (e2e_ms / 1000.0), "unit": "spectra/s",
            "h2d_bytes_per_step": prof_e2e["h2d_bytes"] / args.steps,
            "d2h_bytes_per_step": prof_e2e["d2h_bytes"] / args.steps}
@@ -308,7 +300,7 @@ def main():
             "kernel_ms_share": {k: v / tot for k, v in shares.items()},
             "gather_gbs": gather_gbs, "resample_gbs": resample_gbs,
             "stages": prof["stages"], "jobs": prof["jobs"], "selected_k": sel,
-            "units_per_spectrum": units_per_spec, "wall_s": t_wall}
+            "units_per_spectrum": units_per_spec, "wall_s": t_wall, "tuned_tiles": n_tiles}
 
     if rank == 0 and args.plain_sample:
         line["plain_fp64"] = plain_sample(ctx, args.workload, units_per_spec)

@@ -49,3 +49,13 @@ def test_tile_choice_covers_grid():
         for fam in (W.GAUSS, W.PSEUDO_VOIGT):
             Js = [4, 8, 12, 16] if fam == W.PSEUDO_VOIGT else [4, 8, 12, 16, 24, 32]
             assert any(32 * G * J >= n for G in (1, 2, 4, 8) for J in Js)
+
+
+def test_autotune_candidates_cover_every_bucket():
+    from paper_2604_03271_b300 import autotune as A
+    from paper_2604_03271_b300 import workloads as W
+    for fam in (W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT):
+        for n in A.BUCKETS + (2, 100, 1001, 3999):
+            c = A.candidates(fam, n)
+            assert c and all(32 * G * J >= n for J, G in c)
+            assert all(not (G == 16 and J > 8) for J, G in c)
