@@ -119,10 +119,16 @@ __device__ __forceinline__ float sc2_of(float w)
 struct WarpComp {
     float th[SMC_DMAX];   // current value, sampling coordinate
     float nat[SMC_DMAX];  // current value, natural
-    float un[SMC_DMAX];   // this sweep's proposal, sampling coordinate
-    float vn[SMC_DMAX];   // this sweep's proposal, natural
-    float thr[SMC_DMAX];  // accept iff thr < -beta dE (INFINITY: not proposed)
     unsigned acc[SMC_DMAX];
+};
+
+// One sweep's proposals of a chain, drawn once by the group's first warp and
+// read by all of its warps (double-buffered by sweep parity: the group
+// barrier after each table write keeps every warp within one sweep).
+struct PropTable {
+    float un[SMC_DMAX];   // proposal, sampling coordinate
+    float vn[SMC_DMAX];   // proposal, natural
+    float thr[SMC_DMAX];  // accept iff thr < -beta dE (INFINITY: not proposed)
 };
 
 // Chebyshev T_q(t) by the three-term recurrence
@@ -157,6 +163,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
     __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
     __shared__ WarpComp comp_sh[NT / 32];
+    __shared__ PropTable prop_sh[NT / 32][2];
     GroupCtx g;
     g.lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -250,9 +257,11 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
             for (int jj = 0; jj < J; ++jj) r[jj] -= cq * cheb(q, __ldg(jb.ts + base + jj * stride));
         }
 
-        unsigned long long n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
+        unsigned n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
         for (int sw = 0; sw < n; ++sw) {
-            // ---- this sweep's proposals: lane j draws component j
+            // ---- this sweep's proposals: lane j of the first warp draws component j
+            PropTable &tb = prop_sh[g.grp][sw & 1];
+            if (g.gw == 0)
             for (int j = lane; j < d; j += 32) {
                 const PriorDev &pr = jb.pri[j];
                 float thr = INFINITY, u = 0.0f, v = 0.0f;
@@ -267,11 +276,11 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                         v = pr.kind == PR_LOG_UNIFORM ? expf(u) : u;
                     }
                 }
-                cs.thr[j] = thr;
-                cs.un[j] = u;
-                cs.vn[j] = v;
+                tb.thr[j] = thr;
+                tb.un[j] = u;
+                tb.vn[j] = v;
             }
-            __syncwarp();
+            group_sync(g);
 
             // ---- peak blocks
             for (int k = 0; k < K; ++k) {
@@ -287,9 +296,9 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                 }
                 for (int c = 0; c < P; ++c) {
                     const int j = j0 + c;
-                    const float tj = cs.thr[j];
+                    const float tj = tb.thr[j];
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
-                    const float v = cs.vn[j];
+                    const float v = tb.vn[j];
                     ++n_eval;
                     // two independent accumulators shorten the FMA dependency chain
                     float p0 = 0.0f, p1 = 0.0f;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                             }
                         }
                         if (lane == 0) {
-                            cs.th[j] = cs.un[j];
+                            cs.th[j] = tb.un[j];
                             cs.nat[j] = v;
                             cs.acc[j] += 1u;
                         }
@@ -378,9 +387,9 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
             // ---- background coefficients: D = (c' - c) T_q(t)
             for (int q = 0; q < nbg; ++q) {
                 const int j = K * P + q;
-                const float tj = cs.thr[j];
+                const float tj = tb.thr[j];
                 if (tj == INFINITY) continue;
-                const float v = cs.vn[j];
+                const float v = tb.vn[j];
                 const float dc = v - cs.nat[j];
                 ++n_eval;
                 float p0 = 0.0f, p1 = 0.0f;
@@ -398,7 +407,7 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
 #pragma unroll
                     for (int jj = 0; jj < J; ++jj) r[jj] -= N0[jj];
                     if (lane == 0) {
-                        cs.th[j] = cs.un[j];
+                        cs.th[j] = tb.un[j];
                         cs.nat[j] = v;
                         cs.acc[j] += 1u;
                     }
@@ -429,8 +438,9 @@ __global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev 
                 }
             if (lane == 0) {
                 const unsigned long long npts = (unsigned long long)jb.n;
-                atomicAdd(&jobs[slot].point_evals, n_eval * npts);
-                atomicAdd(&jobs[slot].sfu_ops, n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
+                atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
+                atomicAdd(&jobs[slot].sfu_ops,
+                          (unsigned long long)n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
             }
         }
         __syncwarp();
