@@ -39,7 +39,8 @@ from paper_2604_03271_b300.sharding import max_over_ranks, shard_seeds  # noqa: 
 METRIC = "spectra/s (all candidate K per spectrum, |dlogZ|<=0.05 vs FP64)"
 SM_COUNT = 148
 # DRAM bytes per k_mh launch from the ncu capture summarised in
-# profiles/k_mh_xps-pv-1001.md, valid only for the kernel source it was taken on
+# profiles/k_mh_xps-pv-1001.md, valid only for the kernel source (k_mh_impl.cuh)
+# it was taken on
 MH_TRAFFIC = {"sha1": "f4d2c9a50f69", "bytes": 6.41e6 + 256, "workload": "xps"}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
@@ -278,7 +279,7 @@ def main():
     achieved = sfu_per_launch / (mh_ms / mh_n / 1000.0) / 1e9 if mh_ms > 0 else 0.0
     peak = SM_COUNT * SFU_PER_SM_CLK * 2032e6 / 1e9
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2604_03271_b300", "csrc", "k_mh.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2604_03271_b300", "csrc", "k_mh_impl.cuh"), "rb").read()
     same_kernel = hashlib.sha1(src).hexdigest()[:12] == MH_TRAFFIC["sha1"]
     traffic = MH_TRAFFIC["bytes"] if same_kernel and args.workload == MH_TRAFFIC["workload"] else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",

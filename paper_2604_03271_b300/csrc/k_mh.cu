@@ -1,498 +1,21 @@
-// k_mh.cu -- fused FP32 Metropolis rejuvenation (Sec. II B 4).
-//
-// One chain is owned by a group of G warps; its N grid points are spread over
-// the group's lanes (J points per lane, point i = 32 g + lane + 32 G jj), and
-// the chain's residual r_i = y_i - f_i stays in registers for the whole stage.
-// A component-wise random-walk proposal (Sec. II B 4) therefore costs one pass
-// over the lane's points and one group reduction:
-//   dE = 1/2 sum_i w_i D_i (D_i - 2 r_i),   D_i = g'_i - g_i (change of the peak)
-// which is E(theta') - E(theta) of the Gaussian energy (App. C Eq. (C2)).
-// Within a peak's block of components the unit-amplitude shapes of the peak
-// (the Gaussian and Lorentzian parts) are cached per point, so amplitude and
-// mixing-ratio proposals need no transcendental at all and centre / width
-// proposals need one EX2 (+ one RCP for Lorentzian parts) per point.
-//
-// Random numbers: Philox4x32-10, counter (t d + j, chain, stage, K).  At the
-// start of a sweep lane j draws component j's proposal (words 0,1 -> Box-Muller
-// normal, word 2 -> accept uniform) and folds the prior ratio into a threshold;
-// proposal j is accepted iff thr_j < -beta dE.
-#include <cfloat>
-#include <cmath>
-
+// k_mh.cu -- tile dispatch and launch of the fused FP32 Metropolis kernel
+// (kernel in k_mh_impl.cuh, instantiated per family in k_mh_{gauss,lor,pv}.cu).
 #include "kernels.h"
 
 namespace smc {
 
-constexpr int MH_MAX_GROUPS = 16;  // warps per chain at most, and chains per block at most
-
-template <int FAM>
-__device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, float &S1)
-{
-    const float t = fmaf(x, sc, -mu * sc);
-    const float t2 = t * t;
-    if (FAM == FAM_GAUSS) {
-        S0 = ex2_approx(-t2);
-    } else if (FAM == FAM_LORENTZ) {
-        S0 = rcp_approx(1.0f + t2);
-    } else {
-        const float L = rcp_approx(1.0f + t2);
-        S0 = ex2_approx(-t2) - L;  // Gaussian minus Lorentzian part
-        S1 = L;
-    }
-}
-
-// Cached per point during a peak's block: S0 = G - L (PV) or the unit shape
-// (Gaussian / Lorentzian), and for PV U = eta (G - L) + L, the unit-amplitude
-// profile; the current peak contributes A U (A S0 for the other families).
-template <int FAM>
-__device__ __forceinline__ float unit_of(float S0, float S1, float eta)
-{
-    return FAM == FAM_PV ? fmaf(eta, S0, S1) : S0;
-}
-
-struct GroupCtx {
-    int lane, gw, grp, G;
-    float *red;  // [2][G] for this group
-    int par;
-};
-
-__device__ __forceinline__ void group_sync(const GroupCtx &g)
-{
-    if (g.G == 1)
-        __syncwarp();
-    else
-        named_barrier(1 + g.grp, 32 * g.G);
-}
-
-__device__ __forceinline__ float group_sum(GroupCtx &g, float v)
-{
-    v = warp_sum(v);
-    if (g.G == 1) return v;
-    float *slot = g.red + g.par * MH_MAX_GROUPS;
-    if (g.lane == 0) slot[g.gw] = v;
-    named_barrier(1 + g.grp, 32 * g.G);
-    float s = 0.0f;
-    for (int w = 0; w < g.G; ++w) s += slot[w];
-    g.par ^= 1;
-    return s;
-}
-
-// Kahan-compensated energy 1/2 sum w r^2 over the group
-template <int J>
-__device__ __forceinline__ float group_energy(GroupCtx &g, const float *w, const float *r)
-{
-    float s = 0.0f, c = 0.0f;
-#pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
-        const float term = 0.5f * w[jj] * r[jj] * r[jj];
-        const float yk = term - c;
-        const float tk = s + yk;
-        c = (tk - s) - yk;
-        s = tk;
-    }
-    c = -c;
-    warp_sum2(s, c);
-    if (g.G == 1) return s + c;
-    float *slot = g.red + g.par * MH_MAX_GROUPS;
-    if (g.lane == 0) slot[g.gw] = s + c;
-    named_barrier(1 + g.grp, 32 * g.G);
-    // compensated sum of the warps' totals in a fixed order
-    float S = 0.0f, Cc = 0.0f;
-    for (int w2 = 0; w2 < g.G; ++w2) {
-        const float yk = slot[w2] - Cc;
-        const float tk = S + yk;
-        Cc = (tk - S) - yk;
-        S = tk;
-    }
-    g.par ^= 1;
-    return S - Cc;
-}
-
-template <int FAM>
-__device__ __forceinline__ float sc2_of(float w)
-{
-    return (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / w : 1.0f / w;
-}
-
-// Per-warp copy of the chain's component state (every warp of a group keeps
-// an identical copy, so no cross-warp synchronisation is needed for it).
-struct WarpComp {
-    float th[SMC_DMAX];   // current value, sampling coordinate
-    float nat[SMC_DMAX];  // current value, natural
-    unsigned acc[SMC_DMAX];
-};
-
-// One sweep's proposals of a chain, drawn once by the group's first warp and
-// read by all of its warps (double-buffered by sweep parity: the group
-// barrier after each table write keeps every warp within one sweep).
-struct PropTable {
-    float un[SMC_DMAX];   // proposal, sampling coordinate
-    float vn[SMC_DMAX];   // proposal, natural
-    float thr[SMC_DMAX];  // accept iff thr < -beta dE (INFINITY: not proposed)
-};
-
-// Chebyshev T_q(t) by the three-term recurrence
-__device__ __forceinline__ float cheb(int q, float t)
-{
-    if (q == 0) return 1.0f;
-    float a = 1.0f, b = t;
-    for (int e = 2; e <= q; ++e) {
-        const float c = fmaf(2.0f * t, b, -a);
-        a = b;
-        b = c;
-    }
-    return b;
-}
-
-// Register budget per tile: blocks of NT threads, at least MINB of them
-// resident per SM (J <= 8: 128 registers; J = 12, and J = 16 without the
-// Lorentzian+Gaussian pair of PV: 170; otherwise up to 255), chosen so that
-// no tile spills.
-template <int FAM, int J, int NT>
-struct MhBounds {
-    static constexpr int MINB = (NT == 128)   ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2))
-                                : (NT == 256) ? (J <= 8 ? 2 : 1)
-                                              : 1;
-};
-
-template <int FAM, int J, int NT>
-__global__ void __launch_bounds__(NT, (MhBounds<FAM, J, NT>::MINB)) k_mh(JobDev *__restrict__ jobs,
-                                                                  const int *__restrict__ slots,
-                                                                  int nslots, int G)
-{
-    __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
-    __shared__ int work_sh[MH_MAX_GROUPS][2];
-    __shared__ WarpComp comp_sh[NT / 32];
-    __shared__ PropTable prop_sh[NT / 32][2];
-    GroupCtx g;
-    g.lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    g.G = G;
-    g.grp = warp / G;
-    g.gw = warp - g.grp * G;
-    g.par = 0;
-    const int ngroups = (blockDim.x >> 5) / G;
-    if (g.grp >= ngroups) return;
-    g.red = &red_sh[g.grp][0][0];
-    const int lane = g.lane;
-    WarpComp &cs = comp_sh[warp];
-    constexpr int P = (FAM == FAM_PV) ? 4 : 3;
-
-    int li = 0;
-    for (;;) {
-        // ---- claim the next chain (dynamic scheduling over the bucket's jobs)
-        int slot = -1, m = 0;
-        if (g.gw == 0 && lane == 0) {
-            while (li < nslots) {
-                const int sl = slots[li];
-                JobDev &jq = jobs[sl];
-                if (jq.state == JOB_ACTIVE && jq.status == 0) {
-                    const int c = atomicAdd(&jq.next_chain, 1);
-                    if (c < jq.S) {
-                        slot = sl;
-                        m = c;
-                        break;
-                    }
-                }
-                ++li;
-            }
-            if (G > 1) {
-                work_sh[g.grp][0] = slot;
-                work_sh[g.grp][1] = m;
-            }
-        }
-        if (G == 1) {
-            slot = __shfl_sync(FULL_MASK, slot, 0);
-            m = __shfl_sync(FULL_MASK, m, 0);
-        } else {
-            named_barrier(1 + g.grp, 32 * G);
-            slot = work_sh[g.grp][0];
-            m = work_sh[g.grp][1];
-            named_barrier(1 + g.grp, 32 * G);
-        }
-        if (slot < 0) break;
-
-        const JobDev &jb = jobs[slot];
-        const int K = jb.K, d = jb.d, nbg = jb.nbg, S = jb.S, T = jb.T, n = jb.sweeps;
-        const int wf = jb.waste_free;
-        const float beta = (float)jb.beta;
-        const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
-        const unsigned long long seed = jb.seed;
-        const int base = g.gw * 32 + lane;
-        const int stride = 32 * G;
-
-        // ---- components of the chain start
-        for (int j = lane; j < d; j += 32) {
-            const float u = jb.ths[(size_t)j * S + m];
-            cs.th[j] = u;
-            cs.nat[j] = natural_f(jb.pri[j], u);
-            cs.acc[j] = 0u;
-        }
-        __syncwarp();
-
-        // ---- grid points of this lane and the residual r = y - f(theta)
-        float x[J], w[J], r[J], S0[J], S1[J], N0[J], N1[J];
-#pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-            const int i = base + jj * stride;
-            x[jj] = __ldg(jb.xc + i);
-            w[jj] = __ldg(jb.wt + i);
-            r[jj] = __ldg(jb.y + i);
-        }
-        for (int k = 0; k < K; ++k) {
-            const int j0 = k * P;
-            const float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
-            const float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
-            const float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
-#pragma unroll
-            for (int jj = 0; jj < J; ++jj) {
-                float a0, a1 = 0.0f;
-                shape<FAM>(x[jj], mu, sc, a0, a1);
-                r[jj] -= A * unit_of<FAM>(a0, a1, eta);
-            }
-        }
-        for (int q = 0; q < nbg; ++q) {
-            const float cq = cs.nat[K * P + q];
-#pragma unroll
-            for (int jj = 0; jj < J; ++jj) r[jj] -= cq * cheb(q, __ldg(jb.ts + base + jj * stride));
-        }
-
-        unsigned n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
-        for (int sw = 0; sw < n; ++sw) {
-            // ---- this sweep's proposals: lane j of the first warp draws component j
-            PropTable &tb = prop_sh[g.grp][sw & 1];
-            if (g.gw == 0)
-            for (int j = lane; j < d; j += 32) {
-                const PriorDev &pr = jb.pri[j];
-                float thr = INFINITY, u = 0.0f, v = 0.0f;
-                if (pr.kind != PR_FIXED) {
-                    const uint4 wv = draw(seed, (uint32_t)(sw * d + j), (uint32_t)m, stage, tag);
-                    const float z = box_muller_f(wv.x, wv.y);
-                    const float lu = logf(u01f(wv.z));
-                    const float t0 = cs.th[j];
-                    u = fmaf(jb.stepf[j], z, t0);
-                    if (in_support_f(pr, u)) {
-                        thr = lu - (log_prior_f(pr, u) - log_prior_f(pr, t0));
-                        v = pr.kind == PR_LOG_UNIFORM ? expf(u) : u;
-                    }
-                }
-                tb.thr[j] = thr;
-                tb.un[j] = u;
-                tb.vn[j] = v;
-            }
-            group_sync(g);
-
-            // ---- peak blocks
-            for (int k = 0; k < K; ++k) {
-                const int j0 = k * P;
-                float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
-                float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
-                float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
-#pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    float l = 0.0f;
-                    shape<FAM>(x[jj], mu, sc, S0[jj], l);
-                    if (FAM == FAM_PV) S1[jj] = fmaf(eta, S0[jj], l);  // U
-                }
-                for (int c = 0; c < P; ++c) {
-                    const int j = j0 + c;
-                    const float tj = tb.thr[j];
-                    if (tj == INFINITY) continue;  // fixed or outside the prior's support
-                    const float v = tb.vn[j];
-                    ++n_eval;
-                    // two independent accumulators shorten the FMA dependency chain
-                    float p0 = 0.0f, p1 = 0.0f;
-                    if (c == 0) {  // amplitude: D = (A' - A) U
-                        const float dA = v - A;
-#pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            const float D = dA * (FAM == FAM_PV ? S1[jj] : S0[jj]);
-                            const float wd2 = w[jj] * D;
-                            if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
-                            else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
-                        }
-                    } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
-                        const float dd = A * (v - eta);
-#pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            const float D = dd * S0[jj];
-                            const float wd2 = w[jj] * D;
-                            if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
-                            else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
-                        }
-                    } else {  // centre or width: new shape, D = A (U' - U)
-                        ++n_shape;
-                        const float mu2 = (c == 1) ? v : mu;
-                        const float sc2 = (c == 2) ? sc2_of<FAM>(v) : sc;
-#pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            float l = 0.0f;
-                            shape<FAM>(x[jj], mu2, sc2, N0[jj], l);
-                            if (FAM == FAM_PV) N1[jj] = fmaf(eta, N0[jj], l);
-                            const float D = A * (FAM == FAM_PV ? N1[jj] - S1[jj] : N0[jj] - S0[jj]);
-                            const float wd2 = w[jj] * D;
-                            if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
-                            else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
-                        }
-                    }
-                    const float dE = 0.5f * group_sum(g, p0 + p1);
-                    if (tj < -beta * dE) {
-                        if (c == 0) {
-                            const float dA = v - A;
-#pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(-dA, FAM == FAM_PV ? S1[jj] : S0[jj], r[jj]);
-                            A = v;
-                        } else if (c == 3) {
-                            const float de = v - eta;
-                            const float dd = A * de;
-#pragma unroll
-                            for (int jj = 0; jj < J; ++jj) {
-                                r[jj] = fmaf(-dd, S0[jj], r[jj]);
-                                S1[jj] = fmaf(de, S0[jj], S1[jj]);
-                            }
-                            eta = v;
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < J; ++jj) {
-                                if (FAM == FAM_PV) {
-                                    r[jj] = fmaf(-A, N1[jj] - S1[jj], r[jj]);
-                                    S1[jj] = N1[jj];
-                                } else {
-                                    r[jj] = fmaf(-A, N0[jj] - S0[jj], r[jj]);
-                                }
-                                S0[jj] = N0[jj];
-                            }
-                            if (c == 1) {
-                                mu = v;
-                            } else {
-                                wd = v;
-                                sc = sc2_of<FAM>(v);
-                            }
-                        }
-                        if (lane == 0) {
-                            cs.th[j] = tb.un[j];
-                            cs.nat[j] = v;
-                            cs.acc[j] += 1u;
-                        }
-                        __syncwarp();
-                    }
-                }
-            }
-            // ---- background coefficients: D = (c' - c) T_q(t)
-            for (int q = 0; q < nbg; ++q) {
-                const int j = K * P + q;
-                const float tj = tb.thr[j];
-                if (tj == INFINITY) continue;
-                const float v = tb.vn[j];
-                const float dc = v - cs.nat[j];
-                ++n_eval;
-                float p0 = 0.0f, p1 = 0.0f;
-#pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    N0[jj] = dc * cheb(q, __ldg(jb.ts + base + jj * stride));
-                    const float wd2 = w[jj] * N0[jj];
-                    if (jj & 1)
-                        p1 = fmaf(wd2, fmaf(-2.0f, r[jj], N0[jj]), p1);
-                    else
-                        p0 = fmaf(wd2, fmaf(-2.0f, r[jj], N0[jj]), p0);
-                }
-                const float dE = 0.5f * group_sum(g, p0 + p1);
-                if (tj < -beta * dE) {
-#pragma unroll
-                    for (int jj = 0; jj < J; ++jj) r[jj] -= N0[jj];
-                    if (lane == 0) {
-                        cs.th[j] = tb.un[j];
-                        cs.nat[j] = v;
-                        cs.acc[j] += 1u;
-                    }
-                    __syncwarp();
-                }
-            }
-            if (wf) {
-                const float E = group_energy<J>(g, w, r);
-                const size_t o = (size_t)m * n + sw;
-                if (g.gw == 0) {
-                    for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
-                    if (lane == 0) jb.E[o] = E;
-                }
-            }
-        }
-        if (!wf) {
-            const float E = group_energy<J>(g, w, r);
-            if (g.gw == 0) {
-                for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
-                if (lane == 0) jb.E[m] = E;
-            }
-        }
-        if (g.gw == 0) {
-            for (int j = lane; j < d; j += 32)
-                if (jb.pri[j].kind != PR_FIXED) {
-                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)cs.acc[j]);
-                    atomicAdd(&jobs[slot].prop[j], (unsigned long long)n);
-                }
-            if (lane == 0) {
-                const unsigned long long npts = (unsigned long long)jb.n;
-                atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
-                atomicAdd(&jobs[slot].sfu_ops,
-                          (unsigned long long)n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// tiles and launch
-// ---------------------------------------------------------------------------
-typedef void (*mh_fn)(JobDev *, const int *, int, int);
+typedef void (*mh_fn)(JobDev *, const int *, int);
+mh_fn mh_pick_gauss(int J, int G);
+mh_fn mh_pick_lor(int J, int G);
+mh_fn mh_pick_pv(int J, int G);
 
 static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 
-template <int FAM, int NT>
-static mh_fn pick_j(int J)
-{
-    switch (J) {
-    case 4: return k_mh<FAM, 4, NT>;
-    case 8: return k_mh<FAM, 8, NT>;
-    case 12:
-        if constexpr (NT <= 256) return k_mh<FAM, 12, NT>;
-        return nullptr;
-    case 16:
-        if constexpr (NT <= 256) return k_mh<FAM, 16, NT>;
-        return nullptr;
-    case 24:
-        if constexpr (FAM != FAM_PV && NT == 128) return k_mh<FAM, 24, NT>;
-        return nullptr;
-    case 32:
-        if constexpr (FAM != FAM_PV && NT == 128) return k_mh<FAM, 32, NT>;
-        return nullptr;
-    default: return nullptr;
-    }
-}
-
 static mh_fn pick(int family, int J, int G)
 {
-    if (!(G == 1 || G == 2 || G == 4 || G == 8 || G == 16)) return nullptr;
-    if (G == 16) {  // 512-thread chains: only the 128-register tiles fit
-        if (J > 8) return nullptr;
-        if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 512>(J);
-        if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 512>(J);
-        return pick_j<FAM_PV, 512>(J);
-    }
-    if (block_threads(G) == 128) {
-        if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 128>(J);
-        if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 128>(J);
-        return pick_j<FAM_PV, 128>(J);
-    }
-    if (family == FAM_GAUSS) return pick_j<FAM_GAUSS, 256>(J);
-    if (family == FAM_LORENTZ) return pick_j<FAM_LORENTZ, 256>(J);
-    return pick_j<FAM_PV, 256>(J);
+    if (family == FAM_GAUSS) return mh_pick_gauss(J, G);
+    if (family == FAM_LORENTZ) return mh_pick_lor(J, G);
+    return mh_pick_pv(J, G);
 }
 
 bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
@@ -516,7 +39,7 @@ cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, in
     if (!f) return cudaErrorInvalidValue;
     if (nslots <= 0) return cudaSuccess;
     if (grid <= 0) grid = mh_resident_grid(family, J, G);
-    f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots, G);
+    f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,6 @@
+// k_mh_lor.cu -- Lorentzian instantiations of the fused Metropolis kernel.
+#include "k_mh_impl.cuh"
+
+namespace smc {
+mh_fn mh_pick_lor(int J, int G) { return mh_pick_family<FAM_LORENTZ>(J, G); }
+}  // namespace smc

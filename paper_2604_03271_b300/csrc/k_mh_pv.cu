@@ -1,0 +1,6 @@
+// k_mh_pv.cu -- pseudo-Voigt instantiations of the fused Metropolis kernel.
+#include "k_mh_impl.cuh"
+
+namespace smc {
+mh_fn mh_pick_pv(int J, int G) { return mh_pick_family<FAM_PV>(J, G); }
+}  // namespace smc
