@@ -77,8 +77,19 @@ __device__ __forceinline__ float group_sum(GroupCtx<G> &g, float v)
     if (g.lane == 0) slot[g.gw] = v;
     named_barrier(1 + g.grp, 32 * G);
     float s = 0.0f;
+    if constexpr (G % 4 == 0) {
 #pragma unroll
-    for (int w = 0; w < G; ++w) s += slot[w];
+        for (int w = 0; w < G; w += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(slot + w);
+            s += q.x;
+            s += q.y;
+            s += q.z;
+            s += q.w;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < G; ++w) s += slot[w];
+    }
     g.par ^= 1;
     return s;
 }
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
     k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots, int nslots)
 {
     constexpr int NT = MhThreads<G>::NT;
-    __shared__ float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
+    __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
     __shared__ WarpComp comp_sh[NT / 32];
     __shared__ PropTable prop_sh[NT / 32][2];
@@ -328,12 +339,18 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
                     shape<FAM>(x[jj], mu, sc, S0[jj], l);
                     if (FAM == FAM_PV) S1[jj] = fmaf(eta, S0[jj], l);  // U
                 }
+                float tq[P], vq[P];
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    tq[c] = tb.thr[j0 + c];
+                    vq[c] = tb.vn[j0 + c];
+                }
 #pragma unroll
                 for (int c = 0; c < P; ++c) {
                     const int j = j0 + c;
-                    const float tj = tb.thr[j];
+                    const float tj = tq[c];
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
-                    const float v = tb.vn[j];
+                    const float v = vq[c];
                     ++n_eval;
                     // two independent accumulators shorten the FMA dependency chain
                     float p0 = 0.0f, p1 = 0.0f;
