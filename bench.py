@@ -45,7 +45,15 @@ MH_TRAFFIC = {"sha1": "f4d2c9a50f69", "bytes": 6.41e6 + 256, "workload": "xps"}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
+_MIXED = None
+
+
 def workload(name: str, seed: int):
+    global _MIXED
+    if name == "mixed":
+        if _MIXED is None:
+            _MIXED = W.mixed_batch(1, count=256)
+        return _MIXED[(seed - 1) % len(_MIXED)]
     if name == "xps":
         return W.xps_like(seed), W.Options(particles=16384, sweeps=20, seed=seed)
     if name == "xrd":
@@ -57,7 +65,8 @@ def workload(name: str, seed: int):
 
 def config_of(name: str, batch: int) -> dict:
     s, o = workload(name, 1)
-    return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301"}[name],
+    return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301",
+                         "mixed": "mixed-256"}[name],
             "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
             "sweeps": o.sweeps, "ess_target": o.ess_target, "spectra_per_step": batch,
             "family": "pseudo-voigt" if s.family == W.PSEUDO_VOIGT else "gauss",
@@ -186,6 +195,8 @@ def main():
     ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=1, help="time the plain FP64 path on a sample")
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="Poisson arrivals per s (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=12)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -310,6 +321,8 @@ def main():
             "stages": prof["stages"], "jobs": prof["jobs"], "selected_k": sel,
             "units_per_spectrum": units_per_spec, "wall_s": t_wall, "tuned_tiles": n_tiles}
 
+    if rank == 0 and args.serve_rate > 0:
+        line["serving"] = serve_sample(api, local, args.workload, args.serve_rate, args.serve_requests)
     if rank == 0 and args.plain_sample:
         line["plain_fp64"] = plain_sample(ctx, args.workload, units_per_spec)
     if rank == 0 and not args.no_cpu_baseline:
@@ -323,13 +336,54 @@ def main():
         dist.destroy_process_group()
 
 
+def serve_sample(api, device: int, name: str, rate: float, count: int) -> dict:
+    """Continuous-batching serving loop: requests arrive as a Poisson stream,
+    are submitted on arrival (smc_submit) and waited for; latency is the
+    library's submit-to-result time."""
+    import threading
+
+    from paper_2604_03271_b300 import autotune
+    ctx = api.Context(device)
+    autotune.load(ctx)
+    items = [workload(name, 1000 + i) for i in range(count)]
+    arrivals = W.poisson_arrivals(rate, count, seed=7)
+    jobs = [None] * count
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (s, o) in enumerate(items):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            jobs[i] = ctx.submit(s, o)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    t_done = 0.0
+    for i in range(count):
+        while jobs[i] is None:
+            time.sleep(0.001)
+        ctx.wait(jobs[i], 600.0)
+        r = ctx.result(jobs[i], items[i][0])
+        lat.append(r["latency_ms"])
+        t_done = time.perf_counter() - t0
+        ctx.release(jobs[i])
+    th.join()
+    ctx.close()
+    lat = np.array(lat)
+    return {"offered_per_s": rate, "requests": count, "achieved_per_s": count / max(t_done, 1e-9),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "note": "FP32 batched path; arrivals from t = 0"}
+
+
 def plain_sample(ctx, name: str, units_per_spec: float) -> dict:
     """The plain one-spectrum-per-launch FP64 path on a bounded sample: two
     tempering stages of one spectrum, all K, at 1/16 of the particles.  Its
     particle-point evaluation rate, scaled by the workload's evaluations per
     spectrum, gives its spectra/s."""
     spec, o = workload(name, 1)
-    opts = W.Options(particles=max(64, o.particles // 16), sweeps=o.sweeps, seed=1, energy_fp64=1,
+    opts = W.Options(particles=max(64, o.particles // 64), sweeps=o.sweeps, seed=1, energy_fp64=1,
                      max_stages=2)
     ctx.profile_reset(events=False)
     t0 = time.perf_counter()
