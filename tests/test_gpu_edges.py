@@ -1,0 +1,141 @@
+"""Edge cases and full-size checks of the CUDA path against the oracle.
+
+Full-size runs (the bench's XPS-shaped configuration, in the launch
+configuration the bench uses) are checked on sampled outputs the oracle can
+compute one by one and on properties that hold at any size."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_03271_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_03271_b300 import api, autotune
+    c = api.Context(0)
+    autotune.load(c)
+    yield c
+    c.close()
+
+
+def _lognorm(spec):
+    return -float(np.sum(np.log(np.sqrt(2 * np.pi) * spec.sigma)))
+
+
+def test_all_fixed_parameters_give_exact_likelihood(ctx):
+    # nothing is sampled: one stage (every weight equal) and log Z = log p(D | theta)
+    spec = W.gaussian_small(1)
+    spec.k_min = spec.k_max = 2
+    nat = [1.0, 3.5, 0.5, 0.6, 6.0, 0.8]
+    spec.comp_priors = [W.Prior(W.FIXED, v) for v in nat]
+    exact = -oracle.energy_natural(W.GAUSS, 2, 0, nat, spec.x, spec.y, spec.sigma) + _lognorm(spec)
+    for fp64 in (0, 1):
+        r = ctx.run(spec, W.Options(particles=64, sweeps=2, seed=1, energy_fp64=fp64))
+        assert r["status"] == 0 and r["n_stages"][0] == 1
+        assert abs(r["log_z"][0] - exact) <= (1e-9 if fp64 else 2e-5 * abs(exact))
+
+
+@pytest.mark.parametrize("n,T", [(2, 2), (33, 7), (5, 64)])
+def test_minimal_sizes_replay(ctx, n, T):
+    rng = np.random.default_rng(n)
+    x = np.linspace(0, 1, n)
+    y = rng.normal(0.5, 0.1, n)
+    pri = W.Priors(amp=W.Prior(W.UNIFORM, 0.0, 2.0), centre=W.Prior(W.UNIFORM, 0.0, 1.0),
+                   width=W.Prior(W.LOG_UNIFORM, 0.05, 1.0), bg=[W.Prior(W.UNIFORM, -1, 1)])
+    spec = W.Spectrum(x, y, np.full(n, 0.1), W.GAUSS, 0, 1, W.BG_CONST, 0, pri, truth={})
+    opts = W.Options(particles=T, sweeps=2, seed=4)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=T, sweeps=2, seed=4, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7)
+    r32 = ctx.run(spec, opts)
+    assert r32["status"] == 0 and np.all(np.isfinite(r32["log_z"]))
+
+
+def test_background_only_k0_replay(ctx):
+    spec = W.xps_like(3, n=200, k_true=1, k_max=0)
+    spec.k_min = spec.k_max = 0
+    opts = W.Options(particles=256, sweeps=3, seed=2)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=256, sweeps=3, seed=2, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7)
+
+
+def test_maximum_dimension_k16_pv(ctx):
+    # d = 4 * 16 = 64 components, the largest job: FP64 replay of two stages
+    spec = W.xps_like(5, n=64, k_true=3, k_max=16)
+    spec.k_min = 16
+    opts = W.Options(particles=32, sweeps=1, seed=3, max_stages=2)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=32, sweeps=1, seed=3, max_stages=2, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7)
+    r32 = ctx.run(spec, W.Options(particles=32, sweeps=1, seed=3, max_stages=2))
+    assert r32["job_status"][0] == 5 and np.isfinite(r32["log_z"][0])
+
+
+def test_grid_too_long_for_fp32_tiles_rejected(ctx):
+    from paper_2604_03271_b300 import api
+    spec = W.xrd_like(1, n=4097, k_true=2, k_max=2)
+    with pytest.raises(api.SmcError) as e:
+        ctx.run(spec, W.Options(particles=64, sweeps=1))
+    assert e.value.status == api.SMC_EINVAL
+
+
+def _sort_peaks(samples, p, K):
+    s = samples.copy()
+    peaks = s[:, :p * K].reshape(-1, K, p)
+    order = np.argsort(peaks[:, :, 1], axis=1, kind="stable")
+    s[:, :p * K] = np.take_along_axis(peaks, order[:, :, None], axis=1).reshape(-1, p * K)
+    return s
+
+
+def test_full_size_xps_sampled_outputs(ctx):
+    """The bench configuration (N = 1001, K = 1..6, T = 16384, 20 sweeps):
+    energies of sampled final particles against the FP64 oracle, summaries
+    against the returned samples, p(K|D) normalised."""
+    spec = W.xps_like(1)
+    opts = W.Options(particles=16384, sweeps=20, seed=1)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["status"] == 0
+    assert abs(r["p_k"].sum() - 1.0) < 1e-12
+    assert r["argmax_k"] == r["K"][int(np.argmax(r["log_z"]))]
+    rng = np.random.default_rng(0)
+    for a, K in enumerate(r["K"]):
+        smp = r["samples"][a].astype(np.float64)
+        assert smp.shape == (16384, 4 * K + 2)
+        # summaries are the mean / SD of the (peak-sorted) samples
+        srt = _sort_peaks(smp, 4, K)
+        np.testing.assert_allclose(r["post_mean"][a], srt.mean(0), rtol=1e-5, atol=1e-3)
+        np.testing.assert_allclose(r["post_sd"][a], srt.std(0), rtol=1e-3, atol=1e-3)
+        # every sample inside the prior support
+        assert np.all((smp[:, 1:4 * K:4] >= spec.x.min() - 1e-3) & (smp[:, 1:4 * K:4] <= spec.x.max() + 1e-3))
+        assert np.all((smp[:, 3:4 * K:4] >= 0) & (smp[:, 3:4 * K:4] <= 1))
+        # energies of sampled particles: oracle (FP64) vs the FP32 kernel
+        idx = rng.choice(16384, 64, replace=False)
+        nat = smp[idx]
+        e64 = np.array([oracle.energy_natural(W.PSEUDO_VOIGT, K, 2, v, spec.x, spec.y, spec.sigma)
+                        for v in nat])
+        e32 = ctx.energy(spec, K, opts, nat, precision=0)
+        assert np.all(np.abs(e32 - e64) <= 2e-5 * (e64 + spec.n))
+        # at beta = 1 the particles sit near the posterior: energies of order N/2
+        assert np.median(e64) < 5.0 * spec.n
+
+
+def test_full_size_xrd_g16_tile_energies(ctx):
+    """N = 4096 (16-warp chains): three stages at the XRD configuration's
+    particle count, then sampled energies against the oracle."""
+    spec = W.xrd_like(1)
+    spec.k_min = spec.k_max = 6
+    opts = W.Options(particles=65536, sweeps=2, seed=2, max_stages=3)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["job_status"][0] == 5
+    smp = r["samples"][0].astype(np.float64)
+    idx = np.random.default_rng(1).choice(65536, 24, replace=False)
+    e64 = np.array([oracle.energy_natural(W.PSEUDO_VOIGT, 6, 4, v, spec.x, spec.y, spec.sigma)
+                    for v in smp[idx]])
+    e32 = ctx.energy(spec, 6, opts, smp[idx], precision=0)
+    assert np.all(np.abs(e32 - e64) <= 2e-5 * (e64 + spec.n))
