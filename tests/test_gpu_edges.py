@@ -69,12 +69,21 @@ def test_maximum_dimension_k16_pv(ctx):
     # d = 4 * 16 = 64 components, the largest job: FP64 replay of two stages
     spec = W.xps_like(5, n=64, k_true=3, k_max=16)
     spec.k_min = 16
+    spec.bg, spec.priors.bg = W.BG_NONE, []
     opts = W.Options(particles=32, sweeps=1, seed=3, max_stages=2)
     ref = oracle.run(spec, opts)
     r = ctx.run(spec, W.Options(particles=32, sweeps=1, seed=3, max_stages=2, energy_fp64=1))
     np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7)
     r32 = ctx.run(spec, W.Options(particles=32, sweeps=1, seed=3, max_stages=2))
     assert r32["job_status"][0] == 5 and np.isfinite(r32["log_z"][0])
+
+
+def test_dimension_above_64_rejected(ctx):
+    from paper_2604_03271_b300 import api
+    spec = W.xps_like(5, n=64, k_true=3, k_max=16)  # 4 * 16 + 2 = 66 components
+    with pytest.raises(api.SmcError) as e:
+        ctx.run(spec, W.Options(particles=32, sweeps=1))
+    assert e.value.status == api.SMC_EINVAL
 
 
 def test_grid_too_long_for_fp32_tiles_rejected(ctx):
@@ -121,8 +130,10 @@ def test_full_size_xps_sampled_outputs(ctx):
                         for v in nat])
         e32 = ctx.energy(spec, K, opts, nat, precision=0)
         assert np.all(np.abs(e32 - e64) <= 2e-5 * (e64 + spec.n))
-        # at beta = 1 the particles sit near the posterior: energies of order N/2
-        assert np.median(e64) < 5.0 * spec.n
+        # at beta = 1 the selected model's particles sit near the posterior:
+        # energies of order N/2
+        if K == r["argmax_k"]:
+            assert np.median(e64) < 2.0 * spec.n
 
 
 def test_full_size_xrd_g16_tile_energies(ctx):
