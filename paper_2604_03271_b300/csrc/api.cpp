@@ -176,7 +176,7 @@ int smc_create(smc_ctx **out, const smc_create_opts *opts)
     bool ok = cudaMalloc((void **)&c.d_jobs, sizeof(JobDev) * MAX_SLOTS) == cudaSuccess &&
               cudaMemset(c.d_jobs, 0, sizeof(JobDev) * MAX_SLOTS) == cudaSuccess &&
               cudaMalloc((void **)&c.d_lists, sizeof(int) * LIST_AREA) == cudaSuccess &&
-              cudaMalloc((void **)&c.d_nactive, sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void **)&c.d_nactive, 2 * sizeof(int)) == cudaSuccess &&
               cudaHostAlloc((void **)&c.h_nactive, sizeof(int) * NACTIVE_SLOTS, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&c.h_nactive_dev, c.h_nactive, 0) == cudaSuccess;
     if (!ok) {

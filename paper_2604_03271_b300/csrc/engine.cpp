@@ -535,11 +535,69 @@ int run_chunk(Ctx &c, std::vector<Request *> &reqs, int iters)
     return SMC_OK;
 }
 
+// The whole run as one graph launch: a conditional while node whose body is
+// one stage iteration; its last kernel clears the condition when no job is
+// active (or after max_iter stages).  Returns false if the graph could not be
+// built, so the caller falls back to replaying chunks of stages.
+static bool run_whole_graph(Ctx &c, const Plan &P, int *status)
+{
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = false;
+    const int max_iter = P.max_stages + 2;
+    do {
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            break;
+        const int nall = (int)P.all.size();
+        cudaError_t e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream);
+        if (e == cudaSuccess) e = launch_resample(c.d_jobs, c.d_lists, nall, c.stream);
+        if (e == cudaSuccess) e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream);
+        for (size_t b = 0; b < P.buckets.size() && e == cudaSuccess; ++b)
+            e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
+                          P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream);
+        if (e == cudaSuccess)
+            e = launch_stage_end_cond(c.d_jobs, c.d_lists, nall, c.d_nactive, h, c.d_nactive + 1,
+                                      max_iter, c.stream);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c.stream, &captured);
+        if (e != cudaSuccess || e2 != cudaSuccess) break;
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+        ok = true;
+    } while (false);
+    cudaGetLastError();
+    if (ok) {
+        cudaError_t e = cudaMemsetAsync(c.d_nactive + 1, 0, sizeof(int), c.stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        int iters = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&iters, c.d_nactive + 1, sizeof(int), cudaMemcpyDeviceToHost);
+        c.prof.stages += iters;
+        *status = cuda_status(e);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return ok;
+}
+
 static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
 {
     Plan P;
     int st = build_plan(c, reqs, P);
     if (st != SMC_OK || P.all.empty()) return st;
+    // without per-kernel events the whole run is one graph launch
+    if (!c.prof_events && !c.no_while_graph && run_whole_graph(c, P, &st)) return st;
     // capture CHUNK stages into a CUDA graph and replay it until no job is active
     std::vector<cudaEvent_t> ev;
     if (c.prof_events) {

@@ -80,8 +80,10 @@ struct Ctx {
     int *h_nactive_dev = nullptr;  // its device alias
     // autotuned tiles: (family, n_max, J, G)
     std::vector<std::array<int64_t, 4>> tiles;
-    // profiling
+    // profiling (per-kernel events need the chunked graph: conditional bodies
+    // take no event nodes)
     bool prof_events = false;
+    bool no_while_graph = false;
     smc_profile prof{};
     std::map<smc_job, Request *> reqs;
     uint64_t next_id = 1;

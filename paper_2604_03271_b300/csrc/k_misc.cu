@@ -245,7 +245,9 @@ cudaError_t launch_gather(JobDev *jobs, const int *slots, int nslots, int64_t ma
 // jobs still active (for the host loop).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_stage_end(JobDev *jobs, const int *slots, int nslots,
-                                                    int *n_active, int *n_active_host)
+                                                    int *n_active, int *n_active_host, int use_cond,
+                                                    cudaGraphConditionalHandle cond, int *iter,
+                                                    int max_iter)
 {
     __shared__ int red[32];
     int cnt = 0;
@@ -276,13 +278,28 @@ __global__ void __launch_bounds__(1024) k_stage_end(JobDev *jobs, const int *slo
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         *n_active = t;
         if (n_active_host) *(volatile int *)n_active_host = t;
+        if (use_cond) {
+            // while-node condition of a whole-run graph: continue while any job
+            // is active, and never beyond max_iter stages (every stage retires
+            // or advances each job, so max_stages + 1 stages always suffice)
+            const int it = ++(*iter);
+            cudaGraphSetConditional(cond, (t > 0 && it < max_iter) ? 1u : 0u);
+        }
     }
 }
 
 cudaError_t launch_stage_end(JobDev *jobs, const int *slots, int nslots, int *n_active,
                              int *n_active_host, cudaStream_t s)
 {
-    k_stage_end<<<1, 1024, 0, s>>>(jobs, slots, nslots, n_active, n_active_host);
+    k_stage_end<<<1, 1024, 0, s>>>(jobs, slots, nslots, n_active, n_active_host, 0, 0ull, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_end_cond(JobDev *jobs, const int *slots, int nslots, int *n_active,
+                                  cudaGraphConditionalHandle cond, int *iter, int max_iter,
+                                  cudaStream_t s)
+{
+    k_stage_end<<<1, 1024, 0, s>>>(jobs, slots, nslots, n_active, nullptr, 1, cond, iter, max_iter);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,12 @@ cudaError_t launch_mh_plain(JobDev *jobs, const int *slots, int nslots, int max_
 cudaError_t launch_stage_end(JobDev *jobs, const int *slots, int nslots, int *n_active,
                              int *n_active_host, cudaStream_t s);
 
+// Same, as the last node of a whole-run graph: sets the while-node condition
+// (any job active and fewer than max_iter stages run, counted in *iter).
+cudaError_t launch_stage_end_cond(JobDev *jobs, const int *slots, int nslots, int *n_active,
+                                  cudaGraphConditionalHandle cond, int *iter, int max_iter,
+                                  cudaStream_t s);
+
 // Posterior summaries (peaks sorted by centre) and natural-value samples;
 // row a of mean/sd/samples belongs to slots[a].
 cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, double *mean,

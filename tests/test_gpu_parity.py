@@ -317,3 +317,17 @@ def test_xps_shaped_fp32_vs_fp64_statistical(ctx):
     diff = np.abs(lz32.mean(0) - lz64.mean(0))
     assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
     assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0))
+
+
+def test_whole_run_graph_equals_chunked_replay(ctx):
+    # without profiling events a run is one graph launch (conditional while
+    # node); with events it replays four-stage graphs: identical results
+    spec = W.xps_like(2, n=500, k_true=2, k_max=3)
+    opts = W.Options(particles=2048, sweeps=3, seed=6)
+    ctx.profile_reset(events=False)
+    a = ctx.run(spec, opts, keep_samples=False)
+    ctx.profile_reset(events=True)
+    b = ctx.run(spec, opts, keep_samples=False)
+    ctx.profile_reset(events=False)
+    np.testing.assert_array_equal(a["log_z"], b["log_z"])
+    np.testing.assert_array_equal(a["n_stages"], b["n_stages"])
