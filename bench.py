@@ -60,16 +60,25 @@ def workload(name: str, seed: int):
         return W.xrd_like(seed), W.Options(particles=65536, sweeps=20, seed=seed)
     if name == "gauss":
         return W.gaussian_small(seed), W.Options(particles=1024, sweeps=10, seed=seed)
+    if name.startswith("deconv"):
+        # App. C Gaussian deconvolution at the true K, the paper's sweeps per
+        # stage; particles from the paper's range (100 x {3 .. 10000})
+        K = int(name[6:])
+        T = {3: 100000, 10: 100000, 30: 30000}[K]
+        return (W.gaussian_deconvolution(K, seed),
+                W.Options(particles=T, sweeps=W.DECONV_SWEEPS[K], seed=seed))
     raise ValueError(name)
 
 
 def config_of(name: str, batch: int) -> dict:
     s, o = workload(name, 1)
     return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301",
-                         "mixed": "mixed-256"}[name],
+                         "mixed": "mixed-256", "deconv3": "deconv-gauss-K3-300",
+                         "deconv10": "deconv-gauss-K10-1000", "deconv30": "deconv-gauss-K30-3000"}[name],
             "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
             "sweeps": o.sweeps, "ess_target": o.ess_target, "spectra_per_step": batch,
-            "family": "pseudo-voigt" if s.family == W.PSEUDO_VOIGT else "gauss",
+            "family": {W.GAUSS: "gauss", W.LORENTZ: "lorentz", W.PSEUDO_VOIGT: "pseudo-voigt",
+                       W.GAUSS_PRECISION: "gauss-precision"}[s.family],
             "l2": "flushed between steps (256 MiB write)"}
 
 
@@ -191,7 +200,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed"])
+    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "deconv3", "deconv10", "deconv30"])
     ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=1, help="time the plain FP64 path on a sample")

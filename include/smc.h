@@ -16,6 +16,7 @@
  *   SMC_PSEUDO_VOIGT   g = A [eta exp(-ln2 (x-mu)^2/w^2)
  *                             + (1-eta) w^2/(w^2 + (x-mu)^2)]   w: shared HWHM,
  *                                                               eta: Gaussian fraction (Eq. (E1))
+ *   SMC_GAUSS_PRECISION g = A exp(-b/2 (x-mu)^2)               b: precision (App. C Eq. (C1))
  * and background b(x) = sum_j c_j T_j(t), T_j Chebyshev polynomials of the first
  * kind, t = (2x - (x_min + x_max)) / (x_max - x_min).
  * Components per job, in this order (the Metropolis sweep order): for each peak
@@ -46,8 +47,8 @@ extern "C" {
 #endif
 
 #define SMC_MAX_BG 8     /* background coefficients (polynomial degree <= 7) */
-#define SMC_MAX_DIM 64   /* components per job: p K + nbg <= 64               */
-#define SMC_MAX_K 16     /* peaks per job                                     */
+#define SMC_MAX_DIM 128  /* components per job: p K + nbg <= 128              */
+#define SMC_MAX_K 32     /* peaks per job                                     */
 
 typedef struct smc_ctx smc_ctx;
 typedef uint64_t smc_job;
@@ -64,7 +65,7 @@ enum smc_status {
     SMC_ENUMERIC = 8      /* every particle's energy is non-finite                 */
 };
 
-enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2 };
+enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2, SMC_GAUSS_PRECISION = 3 };
 enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3 };
 
 /* Prior kinds.  Sampling coordinates: log v for LOG_UNIFORM, v otherwise.

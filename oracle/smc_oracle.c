@@ -35,7 +35,7 @@
 #define ORC_EMAXSTAGES 5
 #define ORC_ENUMERIC 8
 
-enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2 };
+enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2, FAM_GAUSS_PREC = 3 };
 enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3 };
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
 
@@ -181,12 +181,14 @@ static double log_prior(orc_prior pr, double u)
 }
 
 /* Peak profiles with natural parameters.
- * Gaussian with standard deviation w (App. C Eq. (C1) with b = 1/w^2);
+ * Gaussian with precision b, A exp(-b (x - mu)^2 / 2) (App. C Eq. (C1));
+ * Gaussian with standard deviation w (Eq. (C1) with b = 1/w^2);
  * Lorentzian with HWHM w (the Lorentzian part of Eq. (E1));
  * pseudo-Voigt of Eq. (E1): eta * Gaussian + (1 - eta) * Lorentzian, shared HWHM. */
 double orc_peak(int family, double x, double A, double mu, double w, double eta)
 {
     double dx = x - mu;
+    if (family == FAM_GAUSS_PREC) return A * exp(-w * dx * dx / 2.0);
     if (family == FAM_GAUSS) return A * exp(-dx * dx / (2.0 * w * w));
     double lor = w * w / (w * w + dx * dx);
     if (family == FAM_LORENTZ) return A * lor;

@@ -30,6 +30,11 @@ static int bg_params(int bg, int deg)
 }
 int job_dim(int family, int K, int bg, int deg) { return peak_params(family) * K + bg_params(bg, deg); }
 
+// Gaussian peaks given by their precision run the Gaussian kernels with the
+// width component read as b (shape scale sqrt(b / (2 ln 2)) instead of
+// 1 / (w sqrt(2 ln 2))).
+int kernel_family(int family) { return family == SMC_GAUSS_PRECISION ? SMC_GAUSS : family; }
+
 // ---------------------------------------------------------------------------
 // Tile of the fused Metropolis kernel: J points per lane, G warps per chain,
 // 32 G J >= N.  Chosen to minimise padding, then the number of warps per chain.
@@ -103,7 +108,7 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     if (!rq.priors || !rq.opts || !rq.x || !rq.y || !rq.sigma) return SMC_EINVAL;
     const smc_options &o = *rq.opts;
     if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
-    if (rq.family < 0 || rq.family > 2 || rq.bg < 0 || rq.bg > 3) return SMC_EINVAL;
+    if (rq.family < 0 || rq.family > 3 || rq.bg < 0 || rq.bg > 3) return SMC_EINVAL;
     if (rq.bg == SMC_BG_POLY && (rq.bg_degree < 0 || rq.bg_degree >= SMC_MAX_BG)) return SMC_EINVAL;
     if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
     if (job_dim(rq.family, rq.k_max, rq.bg, rq.bg_degree) > SMC_MAX_DIM) return SMC_EINVAL;
@@ -144,10 +149,11 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
             }
     }
     if (!r->fp64) {
-        r->tile = choose_tile(r->family, r->n);
+        const int kf = kernel_family(r->family);
+        r->tile = choose_tile(kf, r->n);
         for (const auto &t : c.tiles)
-            if (t[0] == r->family && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
-                mh_tile_supported(r->family, (int)t[2], (int)t[3])) {
+            if (t[0] == kf && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
+                mh_tile_supported(kf, (int)t[2], (int)t[3])) {
                 r->tile = {(int)t[2], (int)t[3]};
                 break;
             }
@@ -380,7 +386,8 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.is64 = r.sd.is64;
         jb.n = r.n;
         jb.n_pad = r.n_pad;
-        jb.family = r.family;
+        jb.family = kernel_family(r.family);
+        jb.wprec = r.family == SMC_GAUSS_PRECISION ? 1 : 0;
         jb.K = K;
         jb.p = r.p;
         jb.nbg = r.nbg;

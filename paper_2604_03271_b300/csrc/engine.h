@@ -104,6 +104,7 @@ void free_request_device(Ctx &c, Request &r);
 size_t request_bytes(const Request &r);
 Tile choose_tile(int family, int n);
 int job_dim(int family, int K, int bg, int bg_degree);
+int kernel_family(int family);
 
 // run every job of the given requests to completion (batched FP32 path; plain
 // FP64 requests run one job at a time) and collect their results

@@ -126,10 +126,14 @@ __device__ __forceinline__ float group_energy(GroupCtx<G> &g, const float *w, co
     return S - Cc;
 }
 
+// Inverse scale of the shape argument t = (x - mu) sc: Gaussian with standard
+// deviation w -> 1 / (w sqrt(2 ln 2)); Gaussian with precision b (wprec = 1)
+// -> sqrt(b / (2 ln 2)); Lorentzian / pseudo-Voigt HWHM w -> 1 / w.
 template <int FAM>
-__device__ __forceinline__ float sc2_of(float w)
+__device__ __forceinline__ float sc2_of(float w, int wprec)
 {
-    return (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / w : 1.0f / w;
+    if (FAM == FAM_GAUSS) return wprec ? sqrtf(w) * SMC_INV_SQRT_2LN2 : SMC_INV_SQRT_2LN2 / w;
+    return 1.0f / w;
 }
 
 // Per-warp copy of the chain's component state (every warp of a group keeps
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
     __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
     __shared__ WarpComp comp_sh[NT / 32];
-    __shared__ PropTable prop_sh[NT / 32][2];
+    __shared__ PropTable prop_sh[NT / 32 / G][2];  // one double-buffered table per chain
     GroupCtx<G> g;
     g.lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
 
         const JobDev &jb = jobs[slot];
         const int K = jb.K, d = jb.d, nbg = jb.nbg, S = jb.S, T = jb.T, n = jb.sweeps;
-        const int wf = jb.waste_free;
+        const int wf = jb.waste_free, wprec = jb.wprec;
         const float beta = (float)jb.beta;
         const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
         const unsigned long long seed = jb.seed;
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
             const int j0 = k * P;
             const float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
             const float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
-            const float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
+            const float sc = sc2_of<FAM>(wd, wprec);
 #pragma unroll
             for (int jj = 0; jj < J; ++jj) {
                 float a0, a1 = 0.0f;
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
                 const int j0 = k * P;
                 float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
                 float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
-                float sc = (FAM == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / wd : 1.0f / wd;
+                float sc = sc2_of<FAM>(wd, wprec);
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
                     float l = 0.0f;
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
                     } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
                         const float mu2 = (c == 1) ? v : mu;
-                        const float sc2 = (c == 2) ? sc2_of<FAM>(v) : sc;
+                        const float sc2 = (c == 2) ? sc2_of<FAM>(v, wprec) : sc;
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             float l = 0.0f;
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<
                                 mu = v;
                             } else {
                                 wd = v;
-                                sc = sc2_of<FAM>(v);
+                                sc = sc2_of<FAM>(v, wprec);
                             }
                         }
                         if (lane == 0) {

@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(256) k_energy_f32(JobDev *jobs, const int *slo
     // natural parameters of this particle, widths turned into inverse scales
     for (int j = lane; j < d; j += 32) {
         float v = natural_f(jb.pri[j], jb.th[(size_t)j * jb.T + i]);
-        if (j < p * K && j % p == 2) v = (jb.family == FAM_GAUSS) ? SMC_INV_SQRT_2LN2 / v : 1.0f / v;
+        if (j < p * K && j % p == 2)
+            v = (jb.family != FAM_GAUSS) ? 1.0f / v
+                                         : (jb.wprec ? sqrtf(v) * SMC_INV_SQRT_2LN2 : SMC_INV_SQRT_2LN2 / v);
         P[j] = v;
     }
     __syncwarp();

@@ -4,11 +4,13 @@
 #pragma once
 #include "smc_device.cuh"
 
-__device__ __forceinline__ double peak_eval_d(int fam, double x, double A, double mu, double w,
-                                              double eta)
+// Gaussian: w is the standard deviation, or the precision b when wprec = 1
+// (App. C Eq. (C1)); Lorentzian / pseudo-Voigt: w is the HWHM.
+__device__ __forceinline__ double peak_eval_d(int fam, int wprec, double x, double A, double mu,
+                                              double w, double eta)
 {
     const double dx = x - mu;
-    if (fam == FAM_GAUSS) return A * exp(-dx * dx / (2.0 * w * w));
+    if (fam == FAM_GAUSS) return wprec ? A * exp(-0.5 * w * dx * dx) : A * exp(-dx * dx / (2.0 * w * w));
     const double lor = w * w / (w * w + dx * dx);
     if (fam == FAM_LORENTZ) return A * lor;
     const double sg = w / sqrt(2.0 * 0.69314718055994530942);
@@ -23,7 +25,7 @@ __device__ __forceinline__ double energy_plain(const JobDev &jb, const double *n
         double f = 0.0;
         for (int k = 0; k < jb.K; ++k) {
             const double *q = nat + jb.p * k;
-            f += peak_eval_d(jb.family, x, q[0], q[1], q[2], jb.p == 4 ? q[3] : 0.0);
+            f += peak_eval_d(jb.family, jb.wprec, x, q[0], q[1], q[2], jb.p == 4 ? q[3] : 0.0);
         }
         if (jb.nbg > 0) {
             const double t = x * jb.t_scale + jb.t_off;

@@ -14,8 +14,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#define SMC_DMAX 64
-#define SMC_KMAX 16
+#define SMC_DMAX 128
+#define SMC_KMAX 32
 
 enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2 };
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
@@ -41,8 +41,8 @@ struct JobDev {
     int n, n_pad;
     double x_ref;          // centring offset of centre coordinates
     double t_scale, t_off; // Chebyshev coordinate t = x * t_scale + t_off (raw x)
-    // model
-    int family, K, p, nbg, d;
+    // model (family: kernel family; wprec: Gaussian width given as precision b)
+    int family, K, p, nbg, d, wprec;
     // tile of the Metropolis kernel (points per lane J, warps per chain G)
     int J, G;
     // particles

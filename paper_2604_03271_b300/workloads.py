@@ -14,6 +14,7 @@ paper are not available; these seeded generators stand in for them.
 
 Parameter conventions (shared by the C ABI):
   family 0 GAUSS   : A exp(-(x-mu)^2 / (2 w^2)),        w = standard deviation
+  family 3 GAUSS_PRECISION : A exp(-b (x-mu)^2 / 2),    b = precision (App. C Eq. (C1))
   family 1 LORENTZ : A g^2 / (g^2 + (x-mu)^2),           g = HWHM
   family 2 PV      : A [eta 2^(-(x-mu)^2/s^2) + (1-eta) s^2/(s^2+(x-mu)^2)],
                      s = shared HWHM, eta = Gaussian fraction (Eq. (E1))
@@ -27,7 +28,7 @@ from typing import List, Optional
 
 import numpy as np
 
-GAUSS, LORENTZ, PSEUDO_VOIGT = 0, 1, 2
+GAUSS, LORENTZ, PSEUDO_VOIGT, GAUSS_PRECISION = 0, 1, 2, 3
 BG_NONE, BG_CONST, BG_LINEAR, BG_POLY = 0, 1, 2, 3
 UNIFORM, LOG_UNIFORM, NORMAL, GAMMA, FIXED = 0, 1, 2, 3, 4
 
@@ -119,6 +120,62 @@ def data_bg_priors(y: np.ndarray, nbg: int) -> List[Prior]:
 # ----------------------------------------------------------------------------
 # configurations
 # ----------------------------------------------------------------------------
+
+# App. C: the paper's Gaussian spectral-deconvolution data.  Grid and noise per
+# K (Table "experimental conditions"), the printed true (A_k, mu_k, b_k) per K
+# (Tables of true parameter values) and the sweeps per stage (Sec. III A 2).
+DECONV_GRID = {3: (300, 3.0, 0.1), 10: (1000, 10.0, 0.1), 30: (3000, 30.0, 0.05)}
+DECONV_SWEEPS = {3: 10, 10: 10, 30: 100}
+DECONV_TRUTH = {
+    3: [(0.587, 1.210, 95.689), (1.522, 1.455, 146.837), (1.183, 1.703, 164.469)],
+    10: [(1.049, 0.558, 114.335), (1.215, 2.082, 194.467), (1.103, 2.804, 152.185),
+         (1.045, 3.549, 141.466), (0.924, 4.678, 126.456), (1.146, 5.633, 177.423),
+         (0.938, 7.098, 145.615), (1.392, 7.418, 156.843), (1.464, 8.625, 101.879),
+         (0.883, 9.158, 161.764)],
+    30: [(0.576, 0.486, 105.313), (1.280, 1.065, 130.885), (0.938, 2.378, 159.259),
+         (1.223, 2.814, 123.512), (1.478, 4.815, 196.497), (1.038, 5.375, 194.505),
+         (1.001, 6.277, 184.840), (0.572, 7.822, 147.232), (0.768, 8.005, 184.148),
+         (1.000, 9.661, 113.111), (1.179, 9.881, 130.873), (1.304, 11.301, 146.300),
+         (0.881, 12.139, 174.185), (0.566, 13.939, 148.583), (0.788, 15.030, 113.688),
+         (1.410, 15.401, 134.354), (0.713, 16.752, 132.443), (0.952, 17.446, 130.042),
+         (1.431, 18.670, 116.550), (0.525, 19.274, 141.490), (1.101, 19.987, 144.812),
+         (1.450, 20.959, 177.490), (0.730, 22.615, 179.639), (1.048, 24.174, 152.239),
+         (1.409, 24.581, 146.063), (0.633, 25.343, 177.821), (1.023, 27.074, 188.729),
+         (1.250, 27.571, 167.492), (1.169, 28.530, 180.048), (0.968, 29.576, 193.911)],
+}
+
+
+def deconv_priors(K: int) -> Priors:
+    """App. C prior table: A ~ Ga(5, 5), b ~ Ga(5, 0.04) (shape, rate); the
+    centre ~ N(1.5, variance 0.2) at K = 3, U over the x range otherwise."""
+    L = DECONV_GRID[K][1]
+    centre = Prior(NORMAL, 1.5, math.sqrt(0.2)) if K == 3 else Prior(UNIFORM, 0.0, L)
+    return Priors(amp=Prior(GAMMA, 5.0, 5.0), centre=centre, width=Prior(GAMMA, 5.0, 0.04))
+
+
+def gaussian_deconvolution(K: int = 10, seed: int = 0, k_min: Optional[int] = None,
+                           k_max: Optional[int] = None, n: Optional[int] = None) -> Spectrum:
+    """The paper's Gaussian-peak deconvolution spectrum with K true peaks
+    (K in 3, 10, 30), precision-parameterised, on N equally spaced points of
+    [0, L] with known noise sd; the noise is drawn from `seed` (the paper's
+    noise draws are not given).  Candidate range defaults to K alone.  `n`
+    overrides the point count (same x range) for small test cases."""
+    N, L, sd = DECONV_GRID[K]
+    N = n or N
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0.0, L, N)
+    f = np.zeros_like(x)
+    for A, mu, b in DECONV_TRUTH[K]:
+        f += _synth_gauss(x, A, mu, 1.0 / math.sqrt(b))
+    y = f + rng.normal(0.0, sd, size=x.shape)
+    t = DECONV_TRUTH[K]
+    return Spectrum(x, y, np.full_like(x, sd), GAUSS_PRECISION, K if k_min is None else k_min,
+                    K if k_max is None else k_max, BG_NONE, 0,
+                    deconv_priors(K),
+                    truth={"K": K, "A": [a for a, _, _ in t], "mu": [m for _, m, _ in t],
+                           "b": [b for _, _, b in t]},
+                    name=f"deconv-K{K}-{N}")
+
 
 def gaussian_small(seed: int = 1) -> Spectrum:
     """301-point, two-Gaussian spectrum on [0, 10], noise sd 0.05, K in 1..3.

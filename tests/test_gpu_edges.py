@@ -65,10 +65,10 @@ def test_background_only_k0_replay(ctx):
     np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7)
 
 
-def test_maximum_dimension_k16_pv(ctx):
-    # d = 4 * 16 = 64 components, the largest job: FP64 replay of two stages
-    spec = W.xps_like(5, n=64, k_true=3, k_max=16)
-    spec.k_min = 16
+def test_maximum_dimension_k32_pv(ctx):
+    # d = 4 * 32 = 128 components, the largest job: FP64 replay of two stages
+    spec = W.xps_like(5, n=64, k_true=3, k_max=32)
+    spec.k_min = 32
     spec.bg, spec.priors.bg = W.BG_NONE, []
     opts = W.Options(particles=32, sweeps=1, seed=3, max_stages=2)
     ref = oracle.run(spec, opts)
@@ -78,9 +78,13 @@ def test_maximum_dimension_k16_pv(ctx):
     assert r32["job_status"][0] == 5 and np.isfinite(r32["log_z"][0])
 
 
-def test_dimension_above_64_rejected(ctx):
+def test_dimension_above_128_rejected(ctx):
     from paper_2604_03271_b300 import api
-    spec = W.xps_like(5, n=64, k_true=3, k_max=16)  # 4 * 16 + 2 = 66 components
+    spec = W.xps_like(5, n=64, k_true=3, k_max=32)  # 4 * 32 + 2 = 130 components
+    with pytest.raises(api.SmcError) as e:
+        ctx.run(spec, W.Options(particles=32, sweeps=1))
+    assert e.value.status == api.SMC_EINVAL
+    spec = W.gaussian_deconvolution(30, seed=1, k_min=33, k_max=33)  # 99 components, K > 32
     with pytest.raises(api.SmcError) as e:
         ctx.run(spec, W.Options(particles=32, sweeps=1))
     assert e.value.status == api.SMC_EINVAL

@@ -15,7 +15,7 @@ import oracle
 from conftest import load_golden
 from paper_2604_03271_b300 import workloads as W
 
-GAUSS, LOR, PV = 0, 1, 2
+GAUSS, LOR, PV, GPREC = 0, 1, 2, 3
 
 
 # --------------------------------------------------------------------------
@@ -62,6 +62,22 @@ def test_gauss_lorentz_half_heights():
     assert oracle.peak(LOR, mu, A, mu, w) == pytest.approx(A, rel=1e-15)
 
 
+def test_precision_gaussian_height_half_height_area():
+    # Eq. (C1): A exp(-b/2 (x - mu)^2); half height at |x - mu| = sqrt(2 ln 2 / b),
+    # area A sqrt(2 pi / b), and the standard-deviation form at w = b^(-1/2)
+    A, mu, b = 1.3, 1.455, 146.837
+    assert oracle.peak(GPREC, mu, A, mu, b) == pytest.approx(A, rel=1e-15)
+    hw = math.sqrt(2 * math.log(2) / b)
+    for x in (mu - hw, mu + hw):
+        assert oracle.peak(GPREC, x, A, mu, b) == pytest.approx(A / 2, rel=1e-13)
+    val, _ = integrate.quad(lambda x: oracle.peak(GPREC, x, A, mu, b), -np.inf, np.inf,
+                            points=None, limit=400, epsabs=1e-14, epsrel=1e-12)
+    assert val == pytest.approx(A * math.sqrt(2 * math.pi / b), rel=1e-9)
+    for x in (0.9, 1.4, 2.0):
+        assert oracle.peak(GPREC, x, A, mu, b) == pytest.approx(
+            oracle.peak(GAUSS, x, A, mu, 1.0 / math.sqrt(b)), rel=1e-13)
+
+
 @pytest.mark.parametrize("fam,eta,area", [
     (GAUSS, 0.0, lambda A, w, eta: A * w * math.sqrt(2 * math.pi)),
     (LOR, 0.0, lambda A, w, eta: A * math.pi * w),
@@ -102,6 +118,8 @@ def _mp_energy(fam, K, nbg, nat, x, y, s):
             d2 = (X - mu) ** 2
             if fam == GAUSS:
                 f += A * mpmath.e ** (-d2 / (2 * w * w))
+            elif fam == GPREC:
+                f += A * mpmath.e ** (-w * d2 / 2)
             else:
                 lor = w * w / (w * w + d2)
                 if fam == LOR:
@@ -117,7 +135,7 @@ def _mp_energy(fam, K, nbg, nat, x, y, s):
     return float(tot)
 
 
-@pytest.mark.parametrize("fam", [GAUSS, LOR, PV])
+@pytest.mark.parametrize("fam", [GAUSS, LOR, PV, GPREC])
 def test_energy_brute_force_high_precision(fam):
     rng = np.random.default_rng(11 + fam)
     N, K, nbg = 8, 2, 2
@@ -360,6 +378,26 @@ def test_evidence_k1_quadrature_free_centre():
     lmax = lg.max()
     Z, _ = integrate.quad(lambda m: 0.5 * math.exp(lz_lin(m) - lmax), 0, 2, limit=500,
                           points=[float(grid[np.argmax(lg)])], epsabs=0, epsrel=1e-10)
+    exact = math.log(Z) + lmax
+    vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"]
+            for s in range(1, 6)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
+
+
+def test_evidence_k1_quadrature_gamma_precision():
+    # the App. C parameterisation: A and mu fixed, precision b ~ Gamma(4, 0.25)
+    # (shape, rate; mean 16): Z = int Ga(b) L(b) db by adaptive quadrature
+    spec = W.tiny_single_peak(6)
+    spec.family = W.GAUSS_PRECISION
+    A, mu = 1.2, 0.9
+    spec.comp_priors = [W.Prior(W.FIXED, A), W.Prior(W.FIXED, mu), W.Prior(W.GAMMA, 4.0, 0.25)]
+    ll = lambda b: _log_lik_gauss(spec.y, spec.sigma, A * np.exp(-b * (spec.x - mu) ** 2 / 2))
+    grid = np.linspace(0.5, 80, 800)
+    lmax = max(ll(b) for b in grid)
+    Z, _ = integrate.quad(lambda b: stats.gamma(4.0, scale=4.0).pdf(b) * math.exp(ll(b) - lmax),
+                          0, 120, limit=400, points=[float(grid[np.argmax([ll(b) for b in grid])])],
+                          epsabs=0, epsrel=1e-11)
     exact = math.log(Z) + lmax
     vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"]
             for s in range(1, 6)]
