@@ -320,9 +320,9 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 energies (Kahan), f64 tempering/logZ",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 energies, Metropolis and ESS-search weights (Kahan); f64 evidence, beta and moment totals",
             "data": "synthetic", "config": config_of(args.workload, B), "impl": "ours",
-            "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())) + 5 * prof["jobs"],
+            "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())) + 6 * args.steps * B,
             "clocks": clk, "roofline": roofline,
             "particle_point_evals_per_s": prof["point_evals"] / (total_ms / 1000.0) * world,
             "kernel_ms_share": {k: v / tot for k, v in shares.items()},

@@ -135,7 +135,11 @@ typedef struct {
     double latency_ms;            /* submit (or run start) to completion, host clock   */
 } smc_result_view;
 
-/* Create / destroy a context bound to one device. */
+/* Create / destroy a context bound to one device.  A batched run is one CUDA
+ * graph launch (a conditional while node over the tempering stages); with the
+ * environment variable SMC_GRAPH_CHUNKED=1 at creation the context replays
+ * four-stage graphs from the host instead (same results; for kernel profilers,
+ * which cannot replay kernels inside conditional graphs). */
 int smc_create(smc_ctx **out, const smc_create_opts *opts);
 int smc_destroy(smc_ctx *ctx);
 

@@ -2,6 +2,7 @@
 // include/smc_kernels.h, and the serving loop.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "../../include/smc.h"
@@ -166,6 +167,9 @@ int smc_create(smc_ctx **out, const smc_create_opts *opts)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c.budget = (opts && opts->mem_budget_bytes) ? opts->mem_budget_bytes : (size_t)(0.8 * fr);
+    // SMC_GRAPH_CHUNKED=1: replay four-stage graphs instead of one graph with a
+    // conditional while node (kernel profilers cannot replay kernels of the latter)
+    if (const char *g = getenv("SMC_GRAPH_CHUNKED")) c.no_while_graph = g[0] == '1';
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -571,7 +575,7 @@ int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double
     if (c.free_slots.empty()) return SMC_ENOMEM;
     const size_t e = precision ? 8 : 4;
     char *a = nullptr;
-    const size_t bytes = ((T * e + 255) & ~size_t(255)) + 16 * T + 1024;
+    const size_t bytes = ((T * e + 255) & ~size_t(255)) + 16 * T + 1024 + 8 * RW_SPLIT_MAX;
     CKS(cudaMalloc((void **)&a, bytes));
     JobDev jb{};
     jb.T = jb.S = (int)T;
@@ -590,6 +594,7 @@ int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double
     jb.acc = (unsigned long long *)(tail + 192);
     jb.prop = (unsigned long long *)(tail + 256);
     jb.pri = (const PriorDev *)(tail + 320);
+    jb.rwpart = (double *)(tail + 1024);
     jb.d = 0;
     jb.beta = beta;
     jb.rho = rho;
@@ -607,7 +612,7 @@ int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double
     }
     if (st == SMC_OK) st = cuda_status(cudaMemcpy(c.d_jobs + sl, &jb, sizeof(JobDev), cudaMemcpyHostToDevice));
     if (st == SMC_OK) st = cuda_status(cudaMemcpy(c.d_lists, &sl, 4, cudaMemcpyHostToDevice));
-    if (st == SMC_OK) st = cuda_status(launch_reweight(c.d_jobs, c.d_lists, 1, precision != 0, c.stream));
+    if (st == SMC_OK) st = cuda_status(launch_reweight(c.d_jobs, c.d_lists, 1, precision != 0, T, c.stream));
     if (st == SMC_OK) st = cuda_status(cudaStreamSynchronize(c.stream));
     JobDev o{};
     if (st == SMC_OK) st = cuda_status(cudaMemcpy(&o, c.d_jobs + sl, sizeof(JobDev), cudaMemcpyDeviceToHost));

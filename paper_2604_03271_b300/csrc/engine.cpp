@@ -188,7 +188,7 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 // Device memory of a request: one arena for the spectrum and results, one per job.
 // ---------------------------------------------------------------------------
 struct SpecLayout {
-    size_t raw, x64, y64, is64, xc, wt, y, ts, scal, slots, off, pk, mean, sd, samples, total;
+    size_t raw, x64, y64, is64, xc, wt, y, ts, scal, slots, off, pk, mean, sd, fpart, fcnt, samples, total;
 };
 
 static SpecLayout spec_layout(const Request &r, int64_t T_out)
@@ -211,6 +211,8 @@ static SpecLayout spec_layout(const Request &r, int64_t T_out)
     L.pk = o;   o += al(nK * 8);
     L.mean = o; o += al(nK * dmax * 8);
     L.sd = o;   o += al(nK * dmax * 8);
+    L.fpart = o; o += al(nK * (size_t)finalize_split(T_out) * 2 * dmax * 8);
+    L.fcnt = o; o += al(nK * 4);
     L.samples = o;
     if (r.opts.keep_samples) o += al(nK * (size_t)T_out * dmax * 4);
     L.total = o;
@@ -218,7 +220,7 @@ static SpecLayout spec_layout(const Request &r, int64_t T_out)
 }
 
 struct JobLayout {
-    size_t th, E, ths, Es, w64, q, anc, lam, step, stepf, acc, prop, pri, total;
+    size_t th, E, ths, Es, w64, rwpart, q, anc, lam, step, stepf, acc, prop, pri, total;
 };
 
 static JobLayout job_layout(int d, int64_t T, int64_t S, bool fp64)
@@ -231,6 +233,7 @@ static JobLayout job_layout(int d, int64_t T, int64_t S, bool fp64)
     L.ths = o;  o += al(dd * S * e);
     L.Es = o;   o += al(S * e);
     L.w64 = o;  o += al(T * 8);
+    L.rwpart = o; o += al((size_t)rw_split(T) * (1 + 2 * dd) * 8);
     L.q = o;    o += al(T * 8);
     L.anc = o;  o += al(S * 4);
     L.lam = o;  o += al(dd * 8);
@@ -411,6 +414,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
             jb.Es = (float *)(ja + JL.Es);
         }
         jb.w64 = (double *)(ja + JL.w64);
+        jb.rwpart = (double *)(ja + JL.rwpart);
         jb.q = (unsigned long long *)(ja + JL.q);
         jb.anc = (int *)(ja + JL.anc);
         jb.lam = (double *)(ja + JL.lam);
@@ -457,6 +461,7 @@ struct Plan {
     std::vector<size_t> boff;
     std::vector<int> grids;
     int64_t max_elems = 0;
+    int64_t max_T = 0;
     int max_stages = 1;
 };
 
@@ -470,6 +475,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
             P.all.push_back(sl);
             const JobDev &jb = c.h_jobs[sl];
             P.max_elems = std::max<int64_t>(P.max_elems, (int64_t)jb.S * (jb.d + 1));
+            P.max_T = std::max<int64_t>(P.max_T, jb.T);
             P.max_stages = std::max(P.max_stages, jb.max_stages);
             Bucket *b = nullptr;
             for (Bucket &x : P.buckets)
@@ -513,7 +519,7 @@ static cudaError_t iteration(Ctx &c, const Plan &P, cudaEvent_t *ev, int k)
         return ev ? cudaEventRecordWithFlags(ev[i], c.stream, cudaEventRecordExternal) : cudaSuccess;
     };
     if ((e = mark(0)) != cudaSuccess) return e;
-    if ((e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream)) != cudaSuccess) return e;
+    if ((e = launch_reweight(c.d_jobs, c.d_lists, nall, false, P.max_T, c.stream)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_resample(c.d_jobs, c.d_lists, nall, c.stream)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
@@ -568,7 +574,7 @@ static bool run_whole_graph(Ctx &c, const Plan &P, int *status)
                                           cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             break;
         const int nall = (int)P.all.size();
-        cudaError_t e = launch_reweight(c.d_jobs, c.d_lists, nall, false, c.stream);
+        cudaError_t e = launch_reweight(c.d_jobs, c.d_lists, nall, false, P.max_T, c.stream);
         if (e == cudaSuccess) e = launch_resample(c.d_jobs, c.d_lists, nall, c.stream);
         if (e == cudaSuccess) e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream);
         for (size_t b = 0; b < P.buckets.size() && e == cudaSuccess; ++b)
@@ -656,7 +662,8 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
                         ms = 0.0f;
                     }
                     c.prof.ms[q] += ms;
-                    c.prof.launches[q] += (q == 3) ? (int64_t)P.buckets.size() : 1;
+                    // the tempering class is three kernels for FP32 jobs
+                    c.prof.launches[q] += (q == 3) ? (int64_t)P.buckets.size() : (q == 0 ? 3 : 1);
                 }
             }
             if (prev_active > 0) c.prof.stages += 1;
@@ -681,7 +688,7 @@ static int run_fp64(Ctx &c, Request &r)
         const JobDev &jb = c.h_jobs[sl];
         const int64_t elems = (int64_t)jb.S * (jb.d + 1);
         for (int it = 0; it < jb.max_stages + 2; ++it) {
-            CK(launch_reweight(c.d_jobs, list, 1, true, c.stream));
+            CK(launch_reweight(c.d_jobs, list, 1, true, jb.T, c.stream));
             CK(launch_resample(c.d_jobs, list, 1, c.stream));
             CK(launch_gather(c.d_jobs, list, 1, elems, true, c.stream));
             CK(launch_mh_plain(c.d_jobs, list, 1, jb.S, c.stream));
@@ -720,8 +727,10 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
         const int dmax = std::max(1, job_dim(r->family, r->k_max, r->bg, r->bg_degree));
         const int *dslots = (const int *)(sa + SL.slots);
         float *samples = r->opts.keep_samples ? (float *)(sa + SL.samples) : nullptr;
-        CK(launch_finalize(c.d_jobs, dslots, nK, (double *)(sa + SL.mean), (double *)(sa + SL.sd),
-                           samples, dmax, (int64_t)T * dmax, c.stream));
+        CK(cudaMemsetAsync(sa + SL.fcnt, 0, 4 * nK, c.stream));
+        CK(launch_finalize(c.d_jobs, dslots, nK, dmax, r->k_max, T, (double *)(sa + SL.mean),
+                           (double *)(sa + SL.sd), samples, dmax, (int64_t)T * dmax,
+                           (double *)(sa + SL.fpart), (int *)(sa + SL.fcnt), c.stream));
         CK(launch_posterior(c.d_jobs, dslots, (const int *)(sa + SL.off), 1, (double *)(sa + SL.pk),
                             c.stream));
         r->dim_max = dmax;

@@ -1,5 +1,6 @@
 // k_misc.cu -- prior draws, full energies, particle copy, stage bookkeeping,
 // posterior summaries.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -310,101 +311,138 @@ cudaError_t launch_stage_end_cond(JobDev *jobs, const int *slots, int nslots, in
 // sample's peaks are ordered by centre (peaks are exchangeable in Eq. (1)),
 // then mean and population SD per component in FP64; optional FP32 copy of the
 // natural values as samples [T][dim_stride] (unsorted).
+//
+// A job's particles are split over `split` CTAs.  Each thread keeps its FP64
+// sums of (v - c) and (v - c)^2 per sorted position in shared memory
+// ([position][thread], so the dynamic position index costs no local memory),
+// c being the sorted natural values of particle 0 (a shift against
+// cancellation).  A CTA writes its per-position totals (threads summed in
+// order) to part[job][split]; the last CTA of the job to finish (counted with
+// an atomic after a fence, no waiting) adds the parts in split order and
+// writes mean = c + S1/T and sd = sqrt(S2/T - (S1/T)^2).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_natural(const JobDev &jb, int i, double *v)
+__device__ __forceinline__ double natural_at(const JobDev &jb, int j, int i)
 {
-    for (int j = 0; j < jb.d; ++j) {
-        const double u =
-            jb.fp64 ? jb.th64[(size_t)j * jb.T + i] : (double)jb.th[(size_t)j * jb.T + i];
-        double x = natural_d(jb.pri[j], u);
-        if (jb.pri[j].is_centre) x += jb.x_ref;
-        v[j] = x;
-    }
+    const double u = jb.fp64 ? jb.th64[(size_t)j * jb.T + i] : (double)jb.th[(size_t)j * jb.T + i];
+    double x = natural_d(jb.pri[j], u);
+    if (jb.pri[j].is_centre) x += jb.x_ref;
+    return x;
 }
 
-__device__ __forceinline__ void sort_peaks(const JobDev &jb, const double *v, int *perm)
+// sorted position of peak k: peaks with a smaller centre, ties by index (the
+// order of a stable sort); cen[k * ld] holds the centres
+__device__ __forceinline__ int peak_rank(const float *cen, int ld, int K, int k)
 {
-    for (int k = 0; k < jb.K; ++k) perm[k] = k;
-    for (int k = 1; k < jb.K; ++k) {
-        const int pk = perm[k];
-        const double key = v[pk * jb.p + 1];
-        int m = k - 1;
-        while (m >= 0 && v[perm[m] * jb.p + 1] > key) {
-            perm[m + 1] = perm[m];
-            --m;
+    const float ck = cen[k * ld];
+    int r = 0;
+    for (int m = 0; m < K; ++m) {
+        const float cm = cen[m * ld];
+        r += (cm < ck) || (cm == ck && m < k);
+    }
+    return r;
+}
+
+int finalize_split(int64_t T) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, (T + 1023) / 1024)); }
+
+static int fin_threads(int d) { return d <= 48 ? 128 : 64; }
+
+static size_t fin_smem(int d, int K, int nt)
+{
+    return (size_t)nt * (16 * (size_t)d + 4 * (size_t)std::max(K, 1)) + 8 * (size_t)d + 16;
+}
+
+__global__ void k_finalize(JobDev *jobs, const int *slots, int split, double *mean, double *sd,
+                           float *samples, int dstride, long long sstride, double *part,
+                           int *counters)
+{
+    extern __shared__ __align__(16) unsigned char fin_sh[];
+    const int a = blockIdx.x / split, sp = blockIdx.x - a * split;
+    const JobDev &jb = jobs[slots[a]];
+    const int T = jb.T, d = jb.d, K = jb.K, p = jb.p, NT = blockDim.x, tid = threadIdx.x;
+    double *acc1 = (double *)fin_sh;                 // [d][NT]
+    double *acc2 = acc1 + (size_t)d * NT;            // [d][NT]
+    double *shift = acc2 + (size_t)d * NT;           // [d]
+    float *cen = (float *)(shift + d);               // [K][NT]
+    __shared__ int is_last;
+
+    if (tid == 0) {  // shift: particle 0, sorted
+        for (int k = 0; k < K; ++k) cen[k * NT] = (float)natural_at(jb, k * p + 1, 0);
+        for (int k = 0; k < K; ++k) {
+            const int r = peak_rank(cen, NT, K, k);
+            for (int c = 0; c < p; ++c) shift[r * p + c] = natural_at(jb, k * p + c, 0);
         }
-        perm[m + 1] = pk;
+        for (int j = p * K; j < d; ++j) shift[j] = natural_at(jb, j, 0);
     }
-}
-
-__device__ __forceinline__ double sorted_value(const JobDev &jb, const double *v, const int *perm,
-                                               int j)
-{
-    if (j < jb.p * jb.K) return v[perm[j / jb.p] * jb.p + j % jb.p];
-    return v[j];
-}
-
-__device__ double block_sum_d(double x, double *red)
-{
-    x = warp_sum_d(x);
+    for (int j = 0; j < d; ++j) acc1[j * NT + tid] = acc2[j * NT + tid] = 0.0;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    return t;
-}
 
-__global__ void __launch_bounds__(256) k_finalize(JobDev *jobs, const int *slots, double *mean,
-                                                  double *sd, float *samples, int dstride,
-                                                  long long sstride)
-{
-    __shared__ double red[8];
-    __shared__ double mu[SMC_DMAX];
-    const JobDev &jb = jobs[slots[blockIdx.x]];
-    const int T = jb.T, d = jb.d;
-    double v[SMC_DMAX], acc[SMC_DMAX];
-    int perm[SMC_KMAX];
-    for (int j = 0; j < d; ++j) acc[j] = 0.0;
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        load_natural(jb, i, v);
-        if (samples) {
-            float *row = samples + blockIdx.x * sstride + (long long)i * dstride;
-            for (int j = 0; j < d; ++j) row[j] = (float)v[j];
+    const int lo = (int)((long long)T * sp / split), hi = (int)((long long)T * (sp + 1) / split);
+    for (int i = lo + tid; i < hi; i += NT) {
+        for (int k = 0; k < K; ++k) cen[k * NT + tid] = (float)natural_at(jb, k * p + 1, i);
+        float *row = samples ? samples + a * sstride + (long long)i * dstride : nullptr;
+        for (int k = 0; k < K; ++k) {
+            const int r = peak_rank(cen + tid, NT, K, k);
+            for (int c = 0; c < p; ++c) {
+                const int j = k * p + c, q = r * p + c;
+                const double v = natural_at(jb, j, i);
+                if (row) row[j] = (float)v;
+                const double x = v - shift[q];
+                acc1[q * NT + tid] += x;
+                acc2[q * NT + tid] += x * x;
+            }
         }
-        sort_peaks(jb, v, perm);
-        for (int j = 0; j < d; ++j) acc[j] += sorted_value(jb, v, perm, j);
-    }
-    for (int j = 0; j < d; ++j) {
-        const double t = block_sum_d(acc[j], red);
-        if (threadIdx.x == 0) mu[j] = t / T;
+        for (int j = p * K; j < d; ++j) {
+            const double v = natural_at(jb, j, i);
+            if (row) row[j] = (float)v;
+            const double x = v - shift[j];
+            acc1[j * NT + tid] += x;
+            acc2[j * NT + tid] += x * x;
+        }
     }
     __syncthreads();
-    for (int j = 0; j < d; ++j) acc[j] = 0.0;
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        load_natural(jb, i, v);
-        sort_peaks(jb, v, perm);
-        for (int j = 0; j < d; ++j) {
-            const double t = sorted_value(jb, v, perm, j) - mu[j];
-            acc[j] += t * t;
+    double *mypart = part + ((size_t)a * split + sp) * 2 * dstride;
+    for (int j = tid; j < d; j += NT) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int t = 0; t < NT; ++t) {
+            s1 += acc1[j * NT + t];
+            s2 += acc2[j * NT + t];
         }
+        mypart[j] = s1;
+        mypart[dstride + j] = s2;
     }
-    for (int j = 0; j < d; ++j) {
-        const double t = block_sum_d(acc[j], red);
-        if (threadIdx.x == 0) {
-            mean[(size_t)blockIdx.x * dstride + j] = mu[j];
-            sd[(size_t)blockIdx.x * dstride + j] = sqrt(t / T);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(&counters[a], 1) == split - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const double *jp = part + (size_t)a * split * 2 * dstride;
+    for (int j = tid; j < d; j += NT) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int t = 0; t < split; ++t) {
+            s1 += __ldcg(&jp[(size_t)t * 2 * dstride + j]);
+            s2 += __ldcg(&jp[(size_t)t * 2 * dstride + dstride + j]);
         }
+        const double m1 = s1 / T;
+        mean[(size_t)a * dstride + j] = shift[j] + m1;
+        sd[(size_t)a * dstride + j] = sqrt(fmax(s2 / T - m1 * m1, 0.0));
     }
+    if (tid == 0) counters[a] = 0;
 }
 
-cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, double *mean,
-                            double *sd, float *samples, int dim_stride, int64_t sample_stride,
-                            cudaStream_t s)
+cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, int d_max, int k_max, int64_t T,
+                            double *mean, double *sd, float *samples, int dim_stride,
+                            int64_t sample_stride, double *part, int *counters, cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
-    k_finalize<<<nslots, 256, 0, s>>>(jobs, slots, mean, sd, samples, dim_stride,
-                                      (long long)sample_stride);
+    const int nt = fin_threads(d_max), split = finalize_split(T);
+    const size_t smem = fin_smem(d_max, k_max, nt);
+    // per device and cheap: set on every (eager, uncaptured) launch
+    cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fin_smem(SMC_DMAX, SMC_KMAX, 64));
+    if (e != cudaSuccess) return e;
+    k_finalize<<<nslots * split, nt, smem, s>>>(jobs, slots, split, mean, sd, samples, dim_stride,
+                                               (long long)sample_stride, part, counters);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ struct StaticScratch {
     int slot;
     int pad_[63];
     double w64[SMC_STATIC_MAX_PARTICLES];
+    double rwpart[RW_SPLIT_MAX];  // one partial sum per weights CTA (no components)
 };
 
 static __device__ __align__(256) StaticScratch g_scratch;
@@ -80,6 +81,7 @@ extern "C" int smc_k_reweight_static(const void *E_dev, int64_t T, double beta, 
     else
         jb.E = (float *)E_dev;
     jb.w64 = sc->w64;
+    jb.rwpart = sc->rwpart;
     jb.q = (unsigned long long *)q_dev;
     jb.d = 0;
     jb.beta = beta;
@@ -90,7 +92,7 @@ extern "C" int smc_k_reweight_static(const void *E_dev, int64_t T, double beta, 
     const int zero = 0;
     cudaError_t e = cudaMemcpyAsync(&sc->job, &jb, sizeof(JobDev), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&sc->slot, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_reweight(&sc->job, &sc->slot, 1, precision != 0, s);
+    if (e == cudaSuccess) e = launch_reweight(&sc->job, &sc->slot, 1, precision != 0, T, s);
     JobDev o{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&o, &sc->job, sizeof(JobDev), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -4,11 +4,13 @@
 // (Eq. (10)); the next inverse temperature is found by bisection on the
 // effective sample size ESS = (sum w)^2 / sum w^2 so that ESS >= rho T; the
 // evidence gains log((1/T) sum_i exp(-delta E_i)) (Eq. (11)).  All of it is
-// FP64.  One thread-block cluster works on one job: each CTA owns a slice of
-// the particles and the per-iteration sums are exchanged through distributed
-// shared memory in a fixed order, so the result does not depend on which
-// other jobs share the launch.  The same pass produces the weighted mean and
-// SD of every component (step sizes of the Metropolis kernel, Sec. II B 4).
+// FP64.  This file holds the kernel for jobs with FP64 energies (the plain
+// path, which replays the FP64 oracle); FP32-energy jobs take the kernels of
+// k_temper32.cu.  One thread-block cluster works on one job: each CTA owns a
+// slice of the particles and the per-iteration sums are exchanged through
+// distributed shared memory in a fixed order, so the result does not depend on
+// which other jobs share the launch.  The same pass produces the weighted mean
+// and SD of every component (step sizes of the Metropolis kernel, Sec. II B 4).
 //
 // Resampling: systematic, on the integer weights q_i = floor(w_i 2^40).  For
 // each particle i the kernel writes the range of output slots m whose point
@@ -19,6 +21,7 @@
 #include <cmath>
 
 #include "kernels.h"
+#include "temper.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -28,14 +31,20 @@ constexpr int RW_THREADS = 512;
 constexpr int RW_WARPS = RW_THREADS / 32;
 constexpr int RW_CL = 8;  // CTAs per job (portable cluster size)
 
+constexpr int RW_GATHER = 16;  // values per cluster_sum (nv * RW_CL <= RW_THREADS)
+static_assert(RW_GATHER * RW_CL <= RW_THREADS, "cluster_sum gather size");
+
 struct RwShared {
     double red[SMC_DMAX][RW_WARPS];
     double xch[2][SMC_DMAX];
     double mean[SMC_DMAX];
+    double gat[RW_GATHER][RW_CL];
 };
 
-// Cluster-wide sum of per-thread values v[0..nv), nv <= SMC_DMAX; every thread
-// of every CTA receives the identical totals (fixed summation order).
+// Cluster-wide sum of per-thread values v[0..nv), nv <= RW_GATHER; every
+// thread of every CTA receives the identical totals (fixed summation order).
+// The nv x RW_CL remote reads are issued by as many threads at once (one
+// distributed-shared-memory round trip), then summed from local shared memory.
 __device__ void cluster_sum(cg::cluster_group &cl, RwShared &sh, int &par, const double *v, int nv,
                             double *out)
 {
@@ -51,9 +60,15 @@ __device__ void cluster_sum(cg::cluster_group &cl, RwShared &sh, int &par, const
         sh.xch[par][threadIdx.x] = t;
     }
     cl.sync();
+    if ((int)threadIdx.x < nv * RW_CL) {
+        const int k = threadIdx.x / RW_CL, r = threadIdx.x - k * RW_CL;
+        sh.gat[k][r] = *cl.map_shared_rank(&sh.xch[par][k], r);
+    }
+    __syncthreads();
     for (int k = 0; k < nv; ++k) {
         double t = 0.0;
-        for (int r = 0; r < RW_CL; ++r) t += *cl.map_shared_rank(&sh.xch[par][k], r);
+#pragma unroll
+        for (int r = 0; r < RW_CL; ++r) t += sh.gat[k][r];
         out[k] = t;
     }
     par ^= 1;
@@ -92,14 +107,15 @@ __device__ double cluster_min(cg::cluster_group &cl, RwShared &sh, int &par, dou
         sh.xch[par][0] = t;
     }
     cl.sync();
-    double t = *cl.map_shared_rank(&sh.xch[par][0], 0);
-    for (int r = 1; r < RW_CL; ++r) t = fmin(t, *cl.map_shared_rank(&sh.xch[par][0], r));
+    if ((int)threadIdx.x < RW_CL) sh.gat[0][threadIdx.x] = *cl.map_shared_rank(&sh.xch[par][0], threadIdx.x);
+    __syncthreads();
+    double t = sh.gat[0][0];
+    for (int r = 1; r < RW_CL; ++r) t = fmin(t, sh.gat[0][r]);
     par ^= 1;
     return t;
 }
 
-template <typename P>
-__device__ double ess_frac(cg::cluster_group &cl, RwShared &sh, int &par, const P *E, int lo,
+__device__ double ess_frac(cg::cluster_group &cl, RwShared &sh, int &par, const double *E, int lo,
                            int hi, int T, double emin, double delta)
 {
     double v[2] = {0.0, 0.0};
@@ -115,9 +131,8 @@ __device__ double ess_frac(cg::cluster_group &cl, RwShared &sh, int &par, const 
     return s[0] * s[0] / ((double)T * s[1]);
 }
 
-template <typename P>
 __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
-    k_reweight(JobDev *jobs, const int *slots)
+    k_reweight64(JobDev *jobs, const int *slots)
 {
     __shared__ RwShared sh;
     cg::cluster_group cl = cg::this_cluster();
@@ -126,8 +141,8 @@ __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
     // every CTA of the cluster reads the same state before the first sync
     if (jb.state != JOB_ACTIVE || jb.status != 0) return;
     const int T = jb.T, d = jb.d;
-    const P *E = (const P *)(jb.fp64 ? (const void *)jb.E64 : (const void *)jb.E);
-    const P *th = (const P *)(jb.fp64 ? (const void *)jb.th64 : (const void *)jb.th);
+    const double *E = jb.E64;
+    const double *th = jb.th64;
     double *w64 = jb.w64;
     const int lo = (int)((long long)T * rank / RW_CL);
     const int hi = (int)((long long)T * (rank + 1) / RW_CL);
@@ -151,14 +166,14 @@ __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
     const double room = 1.0 - beta;
     double delta;
     int final_step = 0, iters = 0;
-    if (ess_frac<P>(cl, sh, par, E, lo, hi, T, emin, room) >= rho) {
+    if (ess_frac(cl, sh, par, E, lo, hi, T, emin, room) >= rho) {
         delta = room;
         final_step = 1;
     } else {
         double a = 0.0, b = room;
         while (iters < 200 && b - a > 1e-7 * b) {
             const double mid = 0.5 * (a + b);
-            if (ess_frac<P>(cl, sh, par, E, lo, hi, T, emin, mid) >= rho)
+            if (ess_frac(cl, sh, par, E, lo, hi, T, emin, mid) >= rho)
                 a = mid;
             else
                 b = mid;
@@ -208,28 +223,7 @@ __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
     // -- job scalars (rank 0): step sizes from the previous stage's acceptance,
     //    evidence increment, new temperature
     if (rank == 0) {
-        for (int j = (int)threadIdx.x; j < d; j += RW_THREADS) {
-            if (jb.pri[j].kind == PR_FIXED) {
-                jb.step[j] = 0.0;
-                jb.stepf[j] = 0.0f;
-            } else {
-                double sd = sqrt(var[j] / sw);
-                const double floor_sd = 1e-9 * (1.0 + fabs(sh.mean[j]));
-                if (sd < floor_sd) sd = floor_sd;
-                double lam = jb.lam[j];
-                if (jb.stage >= 1) {
-                    const unsigned long long pr = jb.prop[j];
-                    const double rate = pr ? (double)jb.acc[j] / (double)pr : 0.44;
-                    lam *= exp(rate - 0.44);
-                    lam = fmin(fmax(lam, 0.01), 10.0);
-                    jb.lam[j] = lam;
-                }
-                jb.step[j] = lam * sd;
-                jb.stepf[j] = (float)(lam * sd);
-            }
-            jb.acc[j] = 0ull;
-            jb.prop[j] = 0ull;
-        }
+        for (int j = (int)threadIdx.x; j < d; j += RW_THREADS) update_step(jb, j, sh.mean[j], var[j] / sw);
         if (threadIdx.x == 0) {
             jb.logz += -delta * emin + log(sw / (double)T);
             jb.beta = final_step ? 1.0 : beta + delta;
@@ -242,14 +236,12 @@ __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
     cl.sync();  // keep this CTA's shared memory alive for remote readers
 }
 
-cudaError_t launch_reweight(JobDev *jobs, const int *slots, int nslots, bool fp64,
+cudaError_t launch_reweight(JobDev *jobs, const int *slots, int nslots, bool fp64, int64_t t_max,
                             cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
-    if (fp64)
-        k_reweight<double><<<nslots * RW_CL, RW_THREADS, 0, s>>>(jobs, slots);
-    else
-        k_reweight<float><<<nslots * RW_CL, RW_THREADS, 0, s>>>(jobs, slots);
+    if (!fp64) return launch_temper32(jobs, slots, nslots, t_max, s);
+    k_reweight64<<<nslots * RW_CL, RW_THREADS, 0, s>>>(jobs, slots);
     return cudaGetLastError();
 }
 
@@ -258,14 +250,17 @@ cudaError_t launch_reweight(JobDev *jobs, const int *slots, int nslots, bool fp6
 // ---------------------------------------------------------------------------
 typedef unsigned __int128 u128;
 
-// smallest m in [0, M] with m Q + r >= M c
+// smallest m in [0, M] with m Q + r >= M c: an FP32 estimate of
+// M c / Q - r / Q (off by a few slots at most for M <= 2^24; FP64 division
+// would dominate this kernel on B300), corrected exactly in 128-bit integers.
+// inv_q = 1 / Q in FP32.
 __device__ __forceinline__ long long first_slot(unsigned long long c, unsigned long long Q,
-                                                unsigned long long r, long long M)
+                                                unsigned long long r, long long M, float inv_q)
 {
     const u128 target = (u128)(unsigned long long)M * c;
     if (target <= (u128)r) return 0;
-    double est = ceil(((double)M * (double)c - (double)r) / (double)Q);
-    long long m = est < 0.0 ? 0 : (est > (double)M ? M : (long long)est);
+    const float est = ceilf(fmaf((float)M, (float)c * inv_q, -(float)r * inv_q));
+    long long m = !(est >= 0.0f) ? 0 : (est > (float)M ? M : (long long)est);
     while (m > 0 && (u128)(unsigned long long)(m - 1) * Q + r >= target) --m;
     while (m < M && (u128)(unsigned long long)m * Q + r < target) ++m;
     return m;
@@ -304,10 +299,11 @@ __device__ __forceinline__ void resample_block(const unsigned long long *q, int 
     const unsigned long long Q = wsum[31];
     unsigned long long C = x - loc + (warp > 0 ? wsum[warp - 1] : 0ull);
     const unsigned long long r = (unsigned long long)(((u128)u32 * Q) >> 32);
-    long long mprev = first_slot(C, Q, r, M);
+    const float inv_q = 1.0f / (float)Q;
+    long long mprev = first_slot(C, Q, r, M, inv_q);
     for (int i = i0; i < i1; ++i) {
         C += q[i];
-        const long long mnext = first_slot(C, Q, r, M);
+        const long long mnext = first_slot(C, Q, r, M, inv_q);
         for (long long m = mprev; m < mnext; ++m) anc[m] = i;
         mprev = mnext;
     }

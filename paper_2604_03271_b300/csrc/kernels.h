@@ -24,9 +24,13 @@ cudaError_t launch_energy(JobDev *jobs, const int *slots, int nslots, int max_T,
                           cudaStream_t s);
 
 // Tempering step of every active listed job: ESS bisection, log Z increment,
-// step sizes, quantised weights (a thread-block cluster per job).
-cudaError_t launch_reweight(JobDev *jobs, const int *slots, int nslots, bool fp64,
+// step sizes, quantised weights.  Tempering step of every job in slots (FP64 jobs: one cluster kernel; FP32
+// jobs: search, weights and finish kernels).  t_max: largest T of the jobs.
+constexpr int RW_SPLIT_MAX = 64;
+int rw_split(int64_t T);  // CTAs per FP32 job in the weights kernel
+cudaError_t launch_reweight(JobDev *jobs, const int *slots, int nslots, bool fp64, int64_t t_max,
                             cudaStream_t s);
+cudaError_t launch_temper32(JobDev *jobs, const int *slots, int nslots, int64_t t_max, cudaStream_t s);
 
 // Systematic resampling of given integer weights (one CTA).
 cudaError_t launch_resample_raw(const unsigned long long *q, int T, int M, uint32_t u32, int *anc,
@@ -60,9 +64,13 @@ cudaError_t launch_stage_end_cond(JobDev *jobs, const int *slots, int nslots, in
                                   cudaStream_t s);
 
 // Posterior summaries (peaks sorted by centre) and natural-value samples;
-// row a of mean/sd/samples belongs to slots[a].
-cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, double *mean,
-                            double *sd, float *samples, int dim_stride, int64_t sample_stride,
-                            cudaStream_t s);
+// row a of mean/sd/samples belongs to slots[a].  Every job has T particles and
+// at most d_max components / k_max peaks.  part: nslots * finalize_split(T) *
+// 2 * dim_stride doubles of scratch; counters: nslots ints, zero on entry
+// (left zero on exit).
+int finalize_split(int64_t T);
+cudaError_t launch_finalize(JobDev *jobs, const int *slots, int nslots, int d_max, int k_max, int64_t T,
+                            double *mean, double *sd, float *samples, int dim_stride,
+                            int64_t sample_stride, double *part, int *counters, cudaStream_t s);
 
 }  // namespace smc

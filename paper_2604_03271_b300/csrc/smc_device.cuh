@@ -49,7 +49,8 @@ struct JobDev {
     int T, S, sweeps, waste_free, fp64;
     float *th, *E, *ths, *Es;
     double *th64, *E64, *ths64, *Es64;
-    double *w64;
+    double *w64;           // weights (FP32 jobs: FP32 weights in the first half)
+    double *rwpart;        // FP32 jobs: rw_split(T) rows of 1 + 2 d tempering partial sums
     unsigned long long *q;
     int *anc;
     double *lam, *step;
@@ -57,7 +58,7 @@ struct JobDev {
     unsigned long long *acc, *prop;
     const PriorDev *pri;
     // tempering state
-    double beta, logz, lognorm, rho, delta;
+    double beta, logz, lognorm, rho, delta, emin;
     int stage, max_stages, status, state, final_step, bisect_iters;
     int next_chain;  // dynamic work counter of the Metropolis kernel
     unsigned tag;

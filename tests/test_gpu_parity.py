@@ -128,12 +128,27 @@ def test_reweight_fp64_matches_oracle(ctx, T, scale, beta):
         assert 0.5 <= g <= 0.5 * (1 + 1e-6)
 
 
-def test_reweight_fp32_energies(ctx):
-    rng = np.random.default_rng(3)
-    E = (rng.gamma(2.0, 200.0, 8192) + 1000.0).astype(np.float32).astype(np.float64)
-    d, lz, fin, q = ctx.reweight(E, 0.0, 0.5, precision=0)
-    d_or, fin_or, _ = oracle.choose_delta(E - E.min(), 0.0, 0.5)
-    assert fin == fin_or and d == pytest.approx(d_or, rel=1e-12)
+@pytest.mark.parametrize("T,scale,beta", [(8192, 200.0, 0.0), (100000, 3e3, 0.01), (4097, 50.0, 0.3),
+                                           (257, 1e-4, 0.9)])
+def test_reweight_fp32_energies(ctx, T, scale, beta):
+    # With FP32 energies the increment search weighs in FP32 (relative error
+    # ~2^-22, below that of the FP32 energies themselves): delta agrees with the
+    # FP64 bisection to its stopping width (1e-7) plus that error, and the ESS at
+    # the chosen delta is rho T to 1e-5.  The evidence increment and the
+    # quantised weights are FP64 at the chosen delta.
+    rng = np.random.default_rng(T + 1)
+    E = (rng.gamma(2.0, scale, T) + 1000.0).astype(np.float32).astype(np.float64)
+    d, lz, fin, q = ctx.reweight(E, beta, 0.5, precision=0)
+    e = E - E.min()
+    d_or, fin_or, _ = oracle.choose_delta(e, beta, 0.5)
+    assert fin == fin_or
+    assert d == pytest.approx(d_or, rel=2e-6)
+    if not fin:
+        assert abs(oracle.ess_frac(e, d) - 0.5) <= 1e-5
+    w = np.exp(-d * e)
+    assert lz == pytest.approx(-d * E.min() + math.log(w.mean()), rel=1e-12, abs=1e-12)
+    diff = np.abs(q.astype(np.int64) - oracle.quantise(w).astype(np.int64))
+    assert diff.max() <= 1
 
 
 # --------------------------------------------------------------------------
