@@ -230,6 +230,8 @@ def main():
     ctx = api.Context(local, stream=stream.cuda_stream)
     from paper_2604_03271_b300 import autotune
     n_tiles = autotune.load(ctx)  # tuned Metropolis tiles, if a table is present
+    # SFU throughput of this device (roofline denominator), before any timing
+    mufu = {"ex2": ctx.mufu_rate(0, stream.cuda_stream), "rcp": ctx.mufu_rate(1, stream.cuda_stream)}
     B = args.batch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -297,7 +299,12 @@ def main():
     mh_n = max(1, prof["launches"]["metropolis"])
     sfu_per_launch = prof["sfu_ops"] / mh_n
     achieved = sfu_per_launch / (mh_ms / mh_n / 1000.0) / 1e9 if mh_ms > 0 else 0.0
-    peak = SM_COUNT * SFU_PER_SM_CLK * 2032e6 / 1e9
+    # denominator: the SFU rate measured on this device for the workload's mix
+    # of EX2 and RCP (time-weighted harmonic combination of the two rates)
+    rx, rr = mufu["ex2"]["ops_per_s"], mufu["rcp"]["ops_per_s"]
+    n_ex2, n_rcp = prof["ex2_ops"], prof["rcp_ops"]
+    peak = ((n_ex2 + n_rcp) / (n_ex2 / rx + n_rcp / rr) if n_ex2 + n_rcp > 0 else rx) / 1e9
+    nominal = SM_COUNT * SFU_PER_SM_CLK * 2032e6 / 1e9
     import hashlib
     src = open(os.path.join(ROOT, "paper_2604_03271_b300", "csrc", "k_mh_impl.cuh"), "rb").read()
     same_kernel = hashlib.sha1(src).hexdigest()[:12] == MH_TRAFFIC["sha1"]
@@ -305,7 +312,13 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_mh (fused Metropolis)", "avg_launch_ms": mh_ms / mh_n,
-                "peak_note": "148 SMs x 16 SFU/clk x 2032 MHz (nominal max clock)"}
+                "peak_note": ("measured EX2 %.1f / RCP %.1f results per clock per SM at %.0f MHz "
+                              "(smc_k_mufu_rate), mixed %.0f%% EX2; a 16/clk/SM SFU x 148 x 2032 MHz "
+                              "would be %.0f Gop/s (frac %.3f)"
+                              % (mufu["ex2"]["lanes_per_clk_sm"], mufu["rcp"]["lanes_per_clk_sm"],
+                                 mufu["ex2"]["sm_mhz"], 100.0 * n_ex2 / max(n_ex2 + n_rcp, 1.0), nominal,
+                                 achieved / nominal)),
+                "peak_measured": {k: v for k, v in mufu.items()}}
     shares = {k: prof["ms"][k] for k in prof["ms"]}
     tot = sum(shares.values()) or 1.0
     gather_gbs = prof["gather_bytes"] / (prof["ms"]["gather"] / 1000.0) / 1e9 if prof["ms"]["gather"] else None

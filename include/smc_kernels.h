@@ -97,6 +97,8 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
  *                prior-draw energies), the "particle-point evaluations";
  *   sfu_ops      SFU operations (EX2, RCP) the centre/width proposals need:
  *                N per Gaussian or Lorentzian evaluation, 2 N per pseudo-Voigt;
+ *   ex2_ops / rcp_ops  the same split by operation (Gaussian: EX2,
+ *                Lorentzian: RCP, pseudo-Voigt: one of each per point);
  *   gather_bytes bytes the particle copy must move (read + write), per stage;
  *   resample_bytes bytes the resampler must move (q read, ancestors written);
  *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied. */
@@ -106,10 +108,23 @@ typedef struct {
     double point_evals, sfu_ops, gather_bytes, resample_bytes;
     double h2d_bytes, d2h_bytes;
     int64_t stages, jobs;
+    double ex2_ops, rcp_ops;
 } smc_profile;
 
 int smc_profile_reset(smc_ctx *ctx, int32_t enable_events);
 int smc_profile_read(smc_ctx *ctx, smc_profile *out);
+
+/* Measured throughput of one SFU (MUFU) operation on the current device:
+ * op 0 = EX2 (ex2.approx.ftz.f32), op 1 = RCP (rcp.approx.ftz.f32), the two
+ * transcendentals of the peak shapes.  Runs a dependency-free stream of the
+ * operation on every SM (twelve launches, about 0.25 s, on cuda_stream; the
+ * best of the last four counts) and returns results per second over the whole
+ * device, the SM clock the blocks saw (clock64 cycles over globaltimer
+ * nanoseconds, MHz) and results per clock per SM at that clock.  The paper
+ * has no counterpart: it is the denominator of the Metropolis kernel's
+ * roofline.  Allocates and frees its own small buffers. */
+int smc_k_mufu_rate(int32_t op, double *ops_per_s, double *lanes_per_clk_sm, double *sm_mhz,
+                    void *cuda_stream);
 
 #ifdef __cplusplus
 }

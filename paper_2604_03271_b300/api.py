@@ -58,7 +58,8 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("point_evals", C.c_double),
                 ("sfu_ops", C.c_double), ("gather_bytes", C.c_double), ("resample_bytes", C.c_double),
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
-                ("stages", C.c_int64), ("jobs", C.c_int64)]
+                ("stages", C.c_int64), ("jobs", C.c_int64),
+                ("ex2_ops", C.c_double), ("rcp_ops", C.c_double)]
 
 
 KERNEL_CLASSES = ("reweight", "resample", "gather", "metropolis", "stage_end")
@@ -108,7 +109,8 @@ def lib():
     L.smc_set_tile.restype = C.c_int
     L.smc_profile_reset.argtypes = [vp, i32]
     L.smc_profile_read.argtypes = [vp, P(Profile)]
-    for f in ("smc_profile_reset", "smc_profile_read", "smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_poll",
+    L.smc_k_mufu_rate.argtypes = [i32, P(dbl), P(dbl), P(dbl), vp]
+    for f in ("smc_k_mufu_rate", "smc_profile_reset", "smc_profile_read", "smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_poll",
               "smc_wait", "smc_result", "smc_release", "smc_k_philox", "smc_k_energy",
               "smc_k_prior", "smc_k_reweight", "smc_k_resample", "smc_k_mh_stage"):
         getattr(L, f).restype = C.c_int
@@ -287,7 +289,16 @@ class Context:
                 "point_evals": p.point_evals, "sfu_ops": p.sfu_ops,
                 "gather_bytes": p.gather_bytes, "resample_bytes": p.resample_bytes,
                 "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes,
-                "stages": p.stages, "jobs": p.jobs}
+                "stages": p.stages, "jobs": p.jobs, "ex2_ops": p.ex2_ops, "rcp_ops": p.rcp_ops}
+
+    def mufu_rate(self, op: int, stream=None) -> dict:
+        """Measured SFU throughput of EX2 (op 0) or RCP (op 1) on this
+        context's device: results per second, the SM clock seen (MHz) and
+        results per clock per SM at that clock."""
+        rate, per_clk, mhz = C.c_double(), C.c_double(), C.c_double()
+        _check(self._L.smc_k_mufu_rate(op, C.byref(rate), C.byref(per_clk), C.byref(mhz), stream),
+               "smc_k_mufu_rate")
+        return {"ops_per_s": rate.value, "lanes_per_clk_sm": per_clk.value, "sm_mhz": mhz.value}
 
     # -- step-level entry points (include/smc_kernels.h) -------------------
     def philox(self, seed: int, ctr: np.ndarray) -> np.ndarray:

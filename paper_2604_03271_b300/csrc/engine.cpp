@@ -41,13 +41,13 @@ int kernel_family(int family) { return family == SMC_GAUSS_PRECISION ? SMC_GAUSS
 // ---------------------------------------------------------------------------
 Tile choose_tile(int family, int n)
 {
-    // measured on B300 (XPS-shaped N = 1001): PV fastest at J = 8 (127
-    // registers, 16 warps/SM), Gaussian / Lorentzian at J = 16 (~160
-    // registers, 12 warps/SM); other J only when they pad much less
-    static const int Js_pv[] = {8, 4, 12, 16};
-    static const int Js_gl[] = {16, 8, 12, 4, 24, 32};
-    const int *Js = family == SMC_PSEUDO_VOIGT ? Js_pv : Js_gl;
-    const int nJ = family == SMC_PSEUDO_VOIGT ? 4 : 6;
+    // measured on B300 (XPS-, XRD- and App. C-shaped grids): J = 8 (64
+    // registers, 32 warps/SM) while four warps per chain cover the grid,
+    // J = 16 (128 registers) beyond; other J only when they pad much less
+    static const int Js_small[] = {8, 16, 12, 4, 24, 32};
+    static const int Js_large[] = {16, 8, 12, 4, 24, 32};
+    const int *Js = n <= 32 * 4 * 8 ? Js_small : Js_large;
+    const int nJ = 6;  // unsupported (family, J, G) are skipped below
     Tile best{0, 0};
     double best_cost = -1.0;
     for (int a = 0; a < nJ; ++a)
@@ -764,6 +764,12 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             const double esz = jd.fp64 ? 8.0 : 4.0;
             c.prof.point_evals += (double)jd.point_evals + (double)jd.T * jd.n;
             c.prof.sfu_ops += (double)jd.sfu_ops;
+            if (jd.family == SMC_GAUSS) c.prof.ex2_ops += (double)jd.sfu_ops;
+            else if (jd.family == SMC_LORENTZ) c.prof.rcp_ops += (double)jd.sfu_ops;
+            else {
+                c.prof.ex2_ops += 0.5 * (double)jd.sfu_ops;
+                c.prof.rcp_ops += 0.5 * (double)jd.sfu_ops;
+            }
             c.prof.gather_bytes += (double)jd.stage * ((double)jd.S * (jd.d + 1) * 2.0 * esz + 4.0 * jd.S);
             c.prof.resample_bytes += (double)jd.stage * (8.0 * jd.T + 4.0 * jd.S);
             c.prof.jobs += 1;

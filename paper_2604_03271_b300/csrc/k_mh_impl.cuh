@@ -166,10 +166,6 @@ __device__ __forceinline__ float cheb(int q, float t)
     return b;
 }
 
-// Register budget per tile: blocks of NT threads, at least MINB of them
-// resident per SM (J <= 8: 128 registers; J = 12, and J = 16 without the
-// Lorentzian+Gaussian pair of PV: 170; otherwise up to 255), chosen so that
-// no tile spills.
 // Threads per block of a tile: four one-, two- or four-warp chains per block,
 // one chain per block beyond that.
 template <int G>
@@ -177,15 +173,25 @@ struct MhThreads {
     static constexpr int NT = G <= 4 ? 128 : 32 * G;
 };
 
-template <int FAM, int J, int NT>
+// Register budget per tile, as resident blocks per SM (the __launch_bounds__
+// minimum).  Measured on B300 (Metropolis time of XPS-, XRD- and App. C-shaped
+// runs and of the tuning spectra): a four-warp chain per 128-thread block runs
+// best at 64 registers for J <= 8 (32 warps per SM, despite a few spilled
+// values) and at 128 for J <= 16; blocks holding several one- or two-warp
+// chains keep 128 / 170 registers (their extra per-chain state spills
+// otherwise); 256- and 512-thread blocks at 64 (J <= 8) or 128 registers.
+template <int FAM, int J, int G>
 struct MhBounds {
-    static constexpr int MINB = (NT == 128)   ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2))
-                                : (NT == 256) ? (J <= 8 ? 2 : 1)
-                                              : 1;
+    static constexpr int NT = MhThreads<G>::NT;
+    static constexpr int MINB =
+        (G == 4)      ? (J <= 8 ? 8 : (J <= 16 ? 4 : 2))
+        : (NT == 128) ? (J <= 8 ? 4 : (J <= 12 || (J <= 16 && FAM != FAM_PV) ? 3 : 2))
+        : (NT == 256) ? (J <= 8 ? 4 : 2)
+                      : 2;
 };
 
 template <int FAM, int J, int G>
-__global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, MhThreads<G>::NT>::MINB))
+__global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
     k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots, int nslots)
 {
     constexpr int NT = MhThreads<G>::NT;

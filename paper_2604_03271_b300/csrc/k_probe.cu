@@ -1,0 +1,120 @@
+// k_probe.cu -- throughput of the two SFU (MUFU) operations the Metropolis
+// kernel is built on, EX2 and RCP, measured on the device it runs on.  It is
+// the denominator of the kernel's roofline: a bound that the hardware, not a
+// data sheet, sets.  Every thread runs eight independent chains
+// v <- 2^(-v) (values stay in (0.5, 1]) or v <- 1 / (1 + v) (in (0.5, 1)), so
+// the SFU pipe, not latency, limits the rate.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/smc.h"
+#include "../../include/smc_kernels.h"
+#include "kernels.h"
+
+namespace smc {
+
+constexpr int PR_THREADS = 256;
+constexpr int PR_CHAINS = 8;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// cycles[2 b], cycles[2 b + 1]: SM clock cycles and nanoseconds of block b
+template <int OP>
+__global__ void __launch_bounds__(PR_THREADS) k_mufu(int iters, float *out, long long *cycles)
+{
+    float v[PR_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PR_CHAINS; ++k) v[k] = 0.5f + 0.01f * (threadIdx.x & 7) + 0.001f * k;
+    const long long c0 = clock64();
+    const unsigned long long n0 = global_ns();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < PR_CHAINS; ++k) v[k] = OP == 0 ? ex2_approx(-v[k]) : rcp_approx(1.0f + v[k]);
+    }
+    const long long c1 = clock64();
+    const unsigned long long n1 = global_ns();
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PR_CHAINS; ++k) s += v[k];
+    out[(size_t)blockIdx.x * PR_THREADS + threadIdx.x] = s;
+    if (threadIdx.x == 0) {
+        cycles[2 * blockIdx.x] = c1 - c0;
+        cycles[2 * blockIdx.x + 1] = (long long)(n1 - n0);
+    }
+}
+
+}  // namespace smc
+
+using namespace smc;
+
+extern "C" int smc_k_mufu_rate(int32_t op, double *ops_per_s, double *lanes_per_clk_sm, double *sm_mhz,
+                               void *cuda_stream)
+{
+    if ((op != 0 && op != 1) || !ops_per_s || !lanes_per_clk_sm || !sm_mhz) return SMC_EINVAL;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SMC_ECUDA;
+    cudaError_t e = op == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mufu<0>, PR_THREADS, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mufu<1>, PR_THREADS, 0);
+    if (e != cudaSuccess || per_sm < 1) return SMC_ECUDA;
+    const int grid = sms * per_sm, iters = 1 << 16;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float *out = nullptr;
+    long long *cyc = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int st = SMC_OK;
+    if (cudaMalloc((void **)&out, sizeof(float) * grid * PR_THREADS) != cudaSuccess ||
+        cudaMalloc((void **)&cyc, 2 * sizeof(long long) * grid) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+        cudaEventCreate(&b) != cudaSuccess) {
+        st = SMC_ENOMEM;
+    } else {
+        // launches of ~20 ms each: the first ones bring the SM clock up from
+        // idle, the best of the last four is kept
+        float best = 0.0f;
+        for (int rep = 0; rep < 12 && st == SMC_OK; ++rep) {
+            cudaEventRecord(a, s);
+            if (op == 0)
+                k_mufu<0><<<grid, PR_THREADS, 0, s>>>(iters, out, cyc);
+            else
+                k_mufu<1><<<grid, PR_THREADS, 0, s>>>(iters, out, cyc);
+            cudaEventRecord(b, s);
+            float ms = 0.0f;
+            if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                st = SMC_ECUDA;
+                break;
+            }
+            if (rep >= 8 && (best == 0.0f || ms < best)) best = ms;
+        }
+        if (st == SMC_OK) {
+            std::vector<long long> h(2 * grid);
+            if (cudaMemcpy(h.data(), cyc, 2 * sizeof(long long) * grid, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                st = SMC_ECUDA;
+            } else {
+                // SM clock of the last launch from each block's cycles / nanoseconds
+                double cyc_sum = 0.0, ns_sum = 0.0;
+                for (int i = 0; i < grid; ++i) {
+                    cyc_sum += (double)h[2 * i];
+                    ns_sum += (double)h[2 * i + 1];
+                }
+                const double ops = (double)grid * PR_THREADS * PR_CHAINS * iters;
+                const double hz = ns_sum > 0.0 ? cyc_sum / ns_sum * 1e9 : 0.0;
+                *ops_per_s = ops / (best * 1e-3);
+                *sm_mhz = hz / 1e6;
+                *lanes_per_clk_sm = hz > 0.0 ? *ops_per_s / ((double)sms * hz) : 0.0;
+            }
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(out);
+    cudaFree(cyc);
+    return st;
+}

@@ -154,3 +154,14 @@ def test_full_size_xrd_g16_tile_energies(ctx):
                     for v in smp[idx]])
     e32 = ctx.energy(spec, 6, opts, smp[idx], precision=0)
     assert np.all(np.abs(e32 - e64) <= 2e-5 * (e64 + spec.n))
+
+
+def test_mufu_probe_rates_are_plausible(ctx):
+    # roofline denominator: EX2 / RCP results per clock per SM between 8 and
+    # 64 (the SFU lanes of an SM), at an SM clock between 0.5 and 2.1 GHz, and
+    # per-second rate = per-clock rate x 148 SMs x that clock
+    for op in (0, 1):
+        r = ctx.mufu_rate(op)
+        assert 8.0 <= r["lanes_per_clk_sm"] <= 64.0, r
+        assert 500.0 <= r["sm_mhz"] <= 2100.0, r
+        assert r["ops_per_s"] == pytest.approx(r["lanes_per_clk_sm"] * 148 * r["sm_mhz"] * 1e6, rel=1e-9)
