@@ -38,10 +38,11 @@ from paper_2604_03271_b300.sharding import max_over_ranks, shard_seeds  # noqa: 
 
 METRIC = "spectra/s (all candidate K per spectrum, |dlogZ|<=0.05 vs FP64)"
 SM_COUNT = 148
-# DRAM bytes per k_mh launch from the ncu capture summarised in
-# profiles/k_mh_xps-pv-1001.md, valid only for the kernel source (k_mh_impl.cuh)
-# it was taken on
-MH_TRAFFIC = {"sha1": "f4d2c9a50f69", "bytes": 6.41e6 + 256, "workload": "xps"}
+# DRAM bytes (read + write) of one k_mh launch from the ncu capture summarised
+# in profiles/k_mh_xps-pv-1001.md (one spectrum per step), valid only for the
+# kernel source (k_mh_impl.cuh) it was taken on; scaled by the spectra a launch
+# processes (the particle state of each spectrum's jobs is its own)
+MH_TRAFFIC = {"sha1": "82a8414cd80e", "bytes_per_spectrum": 6.374e6 + 0.392e6, "workload": "xps"}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
@@ -308,7 +309,8 @@ def main():
     import hashlib
     src = open(os.path.join(ROOT, "paper_2604_03271_b300", "csrc", "k_mh_impl.cuh"), "rb").read()
     same_kernel = hashlib.sha1(src).hexdigest()[:12] == MH_TRAFFIC["sha1"]
-    traffic = MH_TRAFFIC["bytes"] if same_kernel and args.workload == MH_TRAFFIC["workload"] else None
+    traffic = (MH_TRAFFIC["bytes_per_spectrum"] * B
+               if same_kernel and args.workload == MH_TRAFFIC["workload"] else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_mh (fused Metropolis)", "avg_launch_ms": mh_ms / mh_n,

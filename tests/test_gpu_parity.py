@@ -131,24 +131,51 @@ def test_reweight_fp64_matches_oracle(ctx, T, scale, beta):
 @pytest.mark.parametrize("T,scale,beta", [(8192, 200.0, 0.0), (100000, 3e3, 0.01), (4097, 50.0, 0.3),
                                            (257, 1e-4, 0.9)])
 def test_reweight_fp32_energies(ctx, T, scale, beta):
-    # With FP32 energies the increment search weighs in FP32 (relative error
-    # ~2^-22, below that of the FP32 energies themselves): delta agrees with the
-    # FP64 bisection to its stopping width (1e-7) plus that error, and the ESS at
-    # the chosen delta is rho T to 1e-5.  The evidence increment and the
-    # quantised weights are FP64 at the chosen delta.
+    # FP32 energies: the search screens midpoints with FP32 weights and takes
+    # every decision within 1e-5 of rho in FP64, so delta is the FP64
+    # bisection's; evidence increment and quantised weights are FP64 at it
     rng = np.random.default_rng(T + 1)
     E = (rng.gamma(2.0, scale, T) + 1000.0).astype(np.float32).astype(np.float64)
     d, lz, fin, q = ctx.reweight(E, beta, 0.5, precision=0)
     e = E - E.min()
     d_or, fin_or, _ = oracle.choose_delta(e, beta, 0.5)
     assert fin == fin_or
-    assert d == pytest.approx(d_or, rel=2e-6)
+    assert d == pytest.approx(d_or, rel=1e-12)
     if not fin:
-        assert abs(oracle.ess_frac(e, d) - 0.5) <= 1e-5
-    w = np.exp(-d * e)
-    assert lz == pytest.approx(-d * E.min() + math.log(w.mean()), rel=1e-12, abs=1e-12)
+        assert 0.5 <= oracle.ess_frac(e, d) <= 0.5 * (1 + 1e-6)
+    w = np.exp(-d_or * e)
+    assert lz == pytest.approx(-d_or * E.min() + math.log(w.mean()), rel=1e-12, abs=1e-12)
     diff = np.abs(q.astype(np.int64) - oracle.quantise(w).astype(np.int64))
-    assert diff.max() <= 1
+    assert diff.max() <= 1 and np.mean(diff > 0) < 1e-3
+
+
+@pytest.mark.parametrize("T,k,c", [(4096, 2048, -math.log(3e-6)), (1000000, 499997, 30.0)])
+def test_reweight_fp32_whole_step_check_near_rho(ctx, T, k, c):
+    # k particles at E0, the rest at E0 + c: ESS/T at the whole remaining step
+    # is within 1e-5 of rho (above it in the first case, below in the second),
+    # so the FP32 screen cannot decide and the check runs in FP64.  Near the
+    # root of the second case ESS/T is so flat (1e-11 per 1e-7 of delta) that
+    # the order of an FP64 sum over 10^6 weights decides the last halvings, so
+    # delta is checked against the exact root of the closed form
+    # ESS/T = (k + (T-k) q)^2 / (T (k + (T-k) q^2)), q = exp(-c delta):
+    # the bisection's final bracket [delta, delta (1 + 1e-7)] must hold it.
+    import mpmath
+    E = np.full(T, 1000.0)
+    E[k:] += c
+    E = E.astype(np.float32).astype(np.float64)
+    cc = float(E[-1] - E[0])
+    d, lz, fin, q = ctx.reweight(E, 0.0, 0.5, precision=0)
+    d_or, fin_or, _ = oracle.choose_delta(E - E.min(), 0.0, 0.5)
+    assert abs(oracle.ess_frac(E - E.min(), 1.0) - 0.5) < 1e-5
+    assert fin == fin_or
+    if fin:
+        assert d == d_or == 1.0
+    else:
+        mpmath.mp.dps = 40
+        f = lambda x: ((k + (T - k) * mpmath.e ** (-cc * x)) ** 2
+                       / (T * (k + (T - k) * mpmath.e ** (-2 * cc * x))) - mpmath.mpf("0.5"))
+        root = float(mpmath.findroot(f, d_or))
+        assert d <= root <= d * (1 + 1.0e-7 + 1e-12)
 
 
 # --------------------------------------------------------------------------
