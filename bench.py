@@ -189,7 +189,8 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 7.6e11, "xrd": 1.0e13, "gauss": 8.0e8}
+UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12,
+                      "deconv3": 3.6e10, "deconv10": 8.2e11, "deconv30": 4.8e13}
 
 
 # ---------------------------------------------------------------------------

@@ -7,7 +7,10 @@
 // A component-wise random-walk proposal (Sec. II B 4) therefore costs one pass
 // over the lane's points and one group reduction:
 //   dE = 1/2 sum_i w_i D_i (D_i - 2 r_i),   D_i = g'_i - g_i (change of the peak)
-// which is E(theta') - E(theta) of the Gaussian energy (App. C Eq. (C2)).
+// which is E(theta') - E(theta) of the Gaussian energy (App. C Eq. (C2)).  The
+// lanes keep h_i = w_i / 2 and R_i = -w_i r_i instead of w_i and r_i, so a point
+// costs two FMAs, dE = sum_i D_i (h_i D_i + R_i), and an accepted change D
+// updates R_i += 2 h_i D_i.
 // Within a peak's block of components the unit-amplitude shapes of the peak
 // (the Gaussian and Lorentzian parts) are cached per point, so amplitude and
 // mixing-ratio proposals need no transcendental at all and centre / width
@@ -101,7 +104,8 @@ __device__ __forceinline__ float group_energy(GroupCtx<G> &g, const float *w, co
     float s = 0.0f, c = 0.0f;
 #pragma unroll
     for (int jj = 0; jj < J; ++jj) {
-        const float term = 0.5f * w[jj] * r[jj] * r[jj];
+        // w holds h = w/2 and r holds R = -w r: 1/2 w r^2 = R^2 / (4 h)
+        const float term = w[jj] > 0.0f ? r[jj] * r[jj] / (4.0f * w[jj]) : 0.0f;
         const float yk = term - c;
         const float tk = s + yk;
         c = (tk - s) - yk;
@@ -148,9 +152,8 @@ struct WarpComp {
 // read by all of its warps (double-buffered by sweep parity: the group
 // barrier after each table write keeps every warp within one sweep).
 struct PropTable {
+    float2 tv[SMC_DMAX];  // (thr, vn): accept iff thr < -beta dE (INFINITY: not proposed), natural value
     float un[SMC_DMAX];   // proposal, sampling coordinate
-    float vn[SMC_DMAX];   // proposal, natural
-    float thr[SMC_DMAX];  // accept iff thr < -beta dE (INFINITY: not proposed)
 };
 
 // Chebyshev T_q(t) by the three-term recurrence
@@ -312,6 +315,14 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
             }
         }
 
+        // weighted form of the residual: h = w / 2, R = -w r, so that
+        // dE = 1/2 sum w D (D - 2 r) = sum D (h D + R) and, on acceptance,
+        // r -> r - D is R -> R + 2 h D
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            r[jj] = -w[jj] * r[jj];
+            w[jj] = 0.5f * w[jj];
+        }
         unsigned n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
         for (int sw = 0; sw < n; ++sw) {
             // ---- this sweep's proposals: lane j of the first warp draws component j
@@ -331,9 +342,8 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                         v = pr.kind == PR_LOG_UNIFORM ? expf(u) : u;
                     }
                 }
-                tb.thr[j] = thr;
+                tb.tv[j] = make_float2(thr, v);
                 tb.un[j] = u;
-                tb.vn[j] = v;
             }
             group_sync(g);
 
@@ -352,8 +362,9 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                 float tq[P], vq[P];
 #pragma unroll
                 for (int c = 0; c < P; ++c) {
-                    tq[c] = tb.thr[j0 + c];
-                    vq[c] = tb.vn[j0 + c];
+                    const float2 q2 = tb.tv[j0 + c];
+                    tq[c] = q2.x;
+                    vq[c] = q2.y;
                 }
 #pragma unroll
                 for (int c = 0; c < P; ++c) {
@@ -369,22 +380,20 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             const float D = dA * (FAM == FAM_PV ? S1[jj] : S0[jj]);
-                            const float wd2 = w[jj] * D;
                             if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
                             else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
+                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
                         }
                     } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
                         const float dd = A * (v - eta);
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
                             const float D = dd * S0[jj];
-                            const float wd2 = w[jj] * D;
                             if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
                             else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
+                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
                         }
                     } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
@@ -396,26 +405,25 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                             shape<FAM>(x[jj], mu2, sc2, N0[jj], l);
                             if (FAM == FAM_PV) N1[jj] = fmaf(eta, N0[jj], l);
                             const float D = A * (FAM == FAM_PV ? N1[jj] - S1[jj] : N0[jj] - S0[jj]);
-                            const float wd2 = w[jj] * D;
                             if (jj & 1)
-                                p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
                             else
-                                p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
+                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
                         }
                     }
-                    const float dE = 0.5f * group_sum(g, p0 + p1);
+                    const float dE = group_sum(g, p0 + p1);
                     if (tj < -beta * dE) {
                         if (c == 0) {
                             const float dA = v - A;
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(-dA, FAM == FAM_PV ? S1[jj] : S0[jj], r[jj]);
+                            for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(w[jj], (dA + dA) * (FAM == FAM_PV ? S1[jj] : S0[jj]), r[jj]);
                             A = v;
                         } else if (c == 3) {
                             const float de = v - eta;
                             const float dd = A * de;
 #pragma unroll
                             for (int jj = 0; jj < J; ++jj) {
-                                r[jj] = fmaf(-dd, S0[jj], r[jj]);
+                                r[jj] = fmaf(w[jj], (dd + dd) * S0[jj], r[jj]);
                                 S1[jj] = fmaf(de, S0[jj], S1[jj]);
                             }
                             eta = v;
@@ -423,10 +431,10 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
 #pragma unroll
                             for (int jj = 0; jj < J; ++jj) {
                                 if (FAM == FAM_PV) {
-                                    r[jj] = fmaf(-A, N1[jj] - S1[jj], r[jj]);
+                                    r[jj] = fmaf(w[jj], (A + A) * (N1[jj] - S1[jj]), r[jj]);
                                     S1[jj] = N1[jj];
                                 } else {
-                                    r[jj] = fmaf(-A, N0[jj] - S0[jj], r[jj]);
+                                    r[jj] = fmaf(w[jj], (A + A) * (N0[jj] - S0[jj]), r[jj]);
                                 }
                                 S0[jj] = N0[jj];
                             }
@@ -471,25 +479,25 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                         S1[jj] = N0[jj];
                     }
                 }
-                const float tj = tb.thr[j];
+                const float2 q2 = tb.tv[j];
+                const float tj = q2.x;
                 if (tj == INFINITY) continue;
-                const float v = tb.vn[j];
+                const float v = q2.y;
                 const float dc = v - cs.nat[j];
                 ++n_eval;
                 float p0 = 0.0f, p1 = 0.0f;
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj) {
                     const float D = dc * N0[jj];
-                    const float wd2 = w[jj] * D;
                     if (jj & 1)
-                        p1 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p1);
+                        p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
                     else
-                        p0 = fmaf(wd2, fmaf(-2.0f, r[jj], D), p0);
+                        p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
                 }
-                const float dE = 0.5f * group_sum(g, p0 + p1);
+                const float dE = group_sum(g, p0 + p1);
                 if (tj < -beta * dE) {
 #pragma unroll
-                    for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(-dc, N0[jj], r[jj]);
+                    for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(w[jj], (dc + dc) * N0[jj], r[jj]);
                     if (lane == 0) {
                         cs.th[j] = tb.un[j];
                         cs.nat[j] = v;
