@@ -51,7 +51,8 @@ class Job(C.Structure):
                 ("comp_priors", C.POINTER(Prior)), ("n_comp_priors", C.c_int32),
                 ("particles", C.c_int64), ("ess_target", C.c_double),
                 ("sweeps", C.c_int32), ("waste_free", C.c_int32),
-                ("seed", C.c_uint64), ("max_stages", C.c_int32)]
+                ("seed", C.c_uint64), ("max_stages", C.c_int32),
+                ("noise", C.c_int32), ("noise_par", C.c_double * 3)]
 
 
 class Out(C.Structure):
@@ -75,6 +76,9 @@ def lib():
         _lib.orc_model_at.restype = d
         _lib.orc_energy_nat.argtypes = [i32, i32, i32, P(d), P(d), P(d), P(d), i64]
         _lib.orc_energy_nat.restype = d
+        _lib.orc_model_vec.argtypes = [i32, i32, i32, i32, P(d), P(d), i64, P(d)]
+        _lib.orc_energy_model.argtypes = [i32, i32, i32, i32, i32, P(d), P(d), P(d), P(d), P(d), i64]
+        _lib.orc_energy_model.restype = d
         _lib.orc_dim.argtypes = [i32, i32, i32, i32]
         _lib.orc_dim.restype = i32
         _lib.orc_prior_draw.argtypes = [Prior, C.c_uint64, u32, u32, u32]
@@ -135,6 +139,22 @@ def energy_natural(family: int, K: int, nbg: int, nat, x, y, sigma) -> float:
     return lib().orc_energy_nat(family, K, nbg, _dp(nat), _dp(x), _dp(y), _dp(sigma), x.shape[0])
 
 
+def model_vec(family: int, K: int, bg: int, bg_degree: int, nat, x) -> np.ndarray:
+    """Forward model at every grid point (any background, Shirley included)."""
+    nat, x = _f64(nat), _f64(x)
+    f = np.zeros(x.shape[0])
+    lib().orc_model_vec(family, K, bg, bg_degree, _dp(nat), _dp(x), x.shape[0], _dp(f))
+    return f
+
+
+def energy_spec(spec, K: int, nat) -> float:
+    """Energy of natural parameters for the spectrum's background and noise model."""
+    nat, x, y, sg = _f64(nat), _f64(spec.x), _f64(spec.y), _f64(spec.sigma)
+    par = (C.c_double * 3)(*getattr(spec, "noise_par", (0.0, 0.0, 0.0)))
+    return lib().orc_energy_model(spec.family, K, spec.bg, spec.bg_degree, getattr(spec, "noise", 0), par,
+                                  _dp(nat), _dp(x), _dp(y), _dp(sg), x.shape[0])
+
+
 def prior_draw(kind: int, p1: float, p2: float, seed: int, comp: int, particle: int, tag: int) -> float:
     return lib().orc_prior_draw(Prior(kind, p1, p2), seed, comp, particle, tag)
 
@@ -193,6 +213,9 @@ class _JobHolder:
         j.particles, j.ess_target = opts.particles, opts.ess_target
         j.sweeps, j.waste_free = opts.sweeps, opts.waste_free
         j.seed, j.max_stages = opts.seed, opts.max_stages
+        j.noise = getattr(spec, "noise", 0)
+        for i, v in enumerate(getattr(spec, "noise_par", (0.0, 0.0, 0.0))):
+            j.noise_par[i] = v
         self.job = j
         self.d = dim(spec.family, K, spec.bg, spec.bg_degree)
 

@@ -13,6 +13,15 @@
  *   - likelihood: Gaussian with known per-point sigma_i; the energy is
  *     E = 1/2 sum ((y_i - f_i)/sigma_i)^2 and the reported log Z adds the
  *     normaliser -sum log(sqrt(2 pi) sigma_i)          (App. C, Eq. (C2));
+ *     or, for the XPS model (App. E), a variance that follows the model,
+ *     sigma_i^2 = s0^2 f_i + s1^2 f_i^2 + s2^2, with
+ *     E = sum [1/2 ln(2 pi sigma_i^2) + 1/2 (y_i - f_i)^2 / sigma_i^2]
+ *     (the 1/N factor and the missing 1/2 of the printed formula read as
+ *     garbles of the Gaussian negative log-likelihood);
+ *   - Shirley background (App. E): B_i = a + (b - a) C_i / C_N with C_i the
+ *     integral of the peak signal from the first grid point to x_i by the
+ *     right-end rectangle rule, C_i = sum_{1 < j <= i} P_j |x_j - x_{j-1}|,
+ *     so B = a at the first point and b at the last (B = a if C_N = 0);
  *   - tempering: next beta by bisection on the effective sample size;
  *   - resampling: systematic, on integer-quantised weights (exact);
  *   - step sizes: lambda_j * weighted population SD, lambda_j adapted from
@@ -36,7 +45,8 @@
 #define ORC_ENUMERIC 8
 
 enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2, FAM_GAUSS_PREC = 3 };
-enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3 };
+enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3, BG_SHIRLEY = 4 };
+enum { NOISE_KNOWN = 0, NOISE_MODEL = 1 };
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
 
 typedef struct {
@@ -56,6 +66,8 @@ typedef struct {
     int32_t sweeps, waste_free;
     uint64_t seed;
     int32_t max_stages;
+    int32_t noise;        /* NOISE_KNOWN: sigma[]; NOISE_MODEL: noise_par */
+    double noise_par[3];  /* s0, s1, s2 of sigma_i^2 = s0^2 f + s1^2 f^2 + s2^2 */
 } orc_job;
 
 typedef struct {
@@ -129,6 +141,7 @@ static int bg_params(int kind, int degree)
     case BG_NONE: return 0;
     case BG_CONST: return 1;
     case BG_LINEAR: return 2;
+    case BG_SHIRLEY: return 2;
     default: return degree + 1;
     }
 }
@@ -255,6 +268,60 @@ double orc_energy_nat(int family, int K, int nbg, const double *nat, const doubl
     return e;
 }
 
+/* Forward model at every grid point, f[i] (Eq. (1); App. E for the Shirley
+ * background, whose value at x_i integrates the peak signal up to x_i). */
+void orc_model_vec(int family, int K, int bg_kind, int bg_degree, const double *nat,
+                   const double *x, int64_t n, double *f)
+{
+    int p = peak_params(family), nbg = bg_params(bg_kind, bg_degree);
+    if (bg_kind != BG_SHIRLEY) {
+        double xmin, xmax;
+        range_of(x, n, &xmin, &xmax);
+        for (int64_t i = 0; i < n; ++i) f[i] = orc_model_at(family, K, nbg, nat, x[i], xmin, xmax);
+        return;
+    }
+    /* peaks only, then the Shirley background from their running integral */
+    for (int64_t i = 0; i < n; ++i) f[i] = orc_model_at(family, K, 0, nat, x[i], 0.0, 1.0);
+    double a = nat[p * K], b = nat[p * K + 1], total = 0.0;
+    for (int64_t i = 1; i < n; ++i) total += f[i] * fabs(x[i] - x[i - 1]);
+    double run = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (i > 0) run += f[i] * fabs(x[i] - x[i - 1]);
+        double shirley = total > 0.0 ? a + (b - a) * run / total : a;
+        f[i] += shirley;
+    }
+}
+
+/* Energy of the natural parameters for either likelihood (see the header):
+ * noise = NOISE_KNOWN: 1/2 sum ((y - f)/sigma)^2 (normaliser not included);
+ * noise = NOISE_MODEL: sum [1/2 ln(2 pi s^2) + 1/2 (y - f)^2 / s^2],
+ * s^2 = par0^2 f + par1^2 f^2 + par2^2 (+inf where s^2 <= 0). */
+double orc_energy_model(int family, int K, int bg_kind, int bg_degree, int noise,
+                        const double *noise_par, const double *nat, const double *x,
+                        const double *y, const double *sigma, int64_t n)
+{
+    double *f = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!f) return NAN;
+    orc_model_vec(family, K, bg_kind, bg_degree, nat, x, n, f);
+    double e = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = y[i] - f[i];
+        if (noise == NOISE_KNOWN) {
+            e += 0.5 * (r / sigma[i]) * (r / sigma[i]);
+        } else {
+            double s0 = noise_par[0], s1 = noise_par[1], s2 = noise_par[2];
+            double v = s0 * s0 * f[i] + s1 * s1 * f[i] * f[i] + s2 * s2;
+            if (!(v > 0.0)) {
+                e = INFINITY;
+                break;
+            }
+            e += 0.5 * log(2.0 * M_PI * v) + 0.5 * r * r / v;
+        }
+    }
+    free(f);
+    return e;
+}
+
 typedef struct {
     const orc_job *job;
     int d, p, nbg;
@@ -267,6 +334,9 @@ static double energy_u(ctx_t *c, const double *u)
 {
     for (int j = 0; j < c->d; ++j) c->nat[j] = to_natural(c->pri[j], u[j]);
     const orc_job *job = c->job;
+    if (job->bg_kind == BG_SHIRLEY || job->noise == NOISE_MODEL)
+        return orc_energy_model(job->family, job->K, job->bg_kind, job->bg_degree, job->noise,
+                                job->noise_par, c->nat, job->x, job->y, job->sigma, job->n);
     double e = 0.0;
     for (int64_t i = 0; i < job->n; ++i) {
         double r = (job->y[i] - orc_model_at(job->family, job->K, c->nbg, c->nat, job->x[i],
@@ -546,10 +616,12 @@ static int validate(const orc_job *job, int d)
     if (job->n < 2 || job->K < 0 || job->particles < 2 || job->sweeps < 1) return ORC_EINVAL;
     if (!(job->ess_target > 0.0 && job->ess_target < 1.0)) return ORC_EINVAL;
     if (job->n_comp_priors > 0 && job->n_comp_priors != d) return ORC_EINVAL;
-    for (int64_t i = 0; i < job->n; ++i)
-        if (!(job->sigma[i] > 0.0) || !isfinite(job->sigma[i]) || !isfinite(job->y[i]) ||
-            !isfinite(job->x[i]))
+    if (job->noise != NOISE_KNOWN && job->noise != NOISE_MODEL) return ORC_EINVAL;
+    for (int64_t i = 0; i < job->n; ++i) {
+        if (!isfinite(job->y[i]) || !isfinite(job->x[i])) return ORC_EINVAL;
+        if (job->noise == NOISE_KNOWN && (!(job->sigma[i] > 0.0) || !isfinite(job->sigma[i])))
             return ORC_EINVAL;
+    }
     return ORC_OK;
 }
 
@@ -592,9 +664,11 @@ int orc_run_job(const orc_job *job, orc_out *out)
     }
     for (int j = 0; j < d; ++j) lam[j] = 2.38;
 
-    /* normaliser of the Gaussian likelihood (reading of App. C, Eq. (C2)) */
+    /* normaliser of the known-sigma Gaussian likelihood (reading of App. C,
+     * Eq. (C2)); the model-variance energy carries its own log terms */
     double lognorm = 0.0;
-    for (int64_t i = 0; i < job->n; ++i) lognorm -= log(sqrt(2.0 * M_PI) * job->sigma[i]);
+    if (job->noise == NOISE_KNOWN)
+        for (int64_t i = 0; i < job->n; ++i) lognorm -= log(sqrt(2.0 * M_PI) * job->sigma[i]);
 
     /* stage 0: prior draws, beta_0 = 0 (Eq. (9)) */
     for (int64_t i = 0; i < Tc; ++i) {

@@ -18,7 +18,9 @@ Parameter conventions (shared by the C ABI):
   family 1 LORENTZ : A g^2 / (g^2 + (x-mu)^2),           g = HWHM
   family 2 PV      : A [eta 2^(-(x-mu)^2/s^2) + (1-eta) s^2/(s^2+(x-mu)^2)],
                      s = shared HWHM, eta = Gaussian fraction (Eq. (E1))
-  background       : sum_j c_j T_j(t), T_j Chebyshev, t = x scaled to [-1, 1]
+  background       : sum_j c_j T_j(t), T_j Chebyshev, t = x scaled to [-1, 1],
+                     or Shirley a + (b - a) C(x)/C(x_last) (App. E), C the running
+                     integral of the peak signal from the first point
 """
 from __future__ import annotations
 
@@ -29,7 +31,8 @@ from typing import List, Optional
 import numpy as np
 
 GAUSS, LORENTZ, PSEUDO_VOIGT, GAUSS_PRECISION = 0, 1, 2, 3
-BG_NONE, BG_CONST, BG_LINEAR, BG_POLY = 0, 1, 2, 3
+BG_NONE, BG_CONST, BG_LINEAR, BG_POLY, BG_SHIRLEY = 0, 1, 2, 3, 4
+NOISE_KNOWN, NOISE_MODEL = 0, 1
 UNIFORM, LOG_UNIFORM, NORMAL, GAMMA, FIXED = 0, 1, 2, 3, 4
 
 
@@ -76,6 +79,10 @@ class Spectrum:
     # Optional per-component priors (one per component, in component order);
     # only meaningful when k_min == k_max.  Overrides the shared priors.
     comp_priors: Optional[List[Prior]] = None
+    # likelihood: NOISE_KNOWN (sigma per point) or NOISE_MODEL (variance
+    # s0^2 f + s1^2 f^2 + s2^2 of the model value f, App. E; sigma unused)
+    noise: int = 0
+    noise_par: tuple = (0.0, 0.0, 0.0)
 
     @property
     def n(self) -> int:
@@ -101,7 +108,7 @@ def _synth_cheb(x, coeffs):
 
 
 def bg_count(bg: int, bg_degree: int) -> int:
-    return {BG_NONE: 0, BG_CONST: 1, BG_LINEAR: 2}.get(bg, bg_degree + 1)
+    return {BG_NONE: 0, BG_CONST: 1, BG_LINEAR: 2, BG_SHIRLEY: 2}.get(bg, bg_degree + 1)
 
 
 def data_bg_priors(y: np.ndarray, nbg: int) -> List[Prior]:
@@ -232,6 +239,53 @@ def xps_like(seed: int = 1, n: int = 1001, k_true: int = 4, k_max: int = 6,
                     truth={"K": k_true, "A": amp.tolist(), "mu": mus,
                            "hwhm": (0.5 * fwhm).tolist(), "eta": eta.tolist()},
                     name=f"xps-{n}")
+
+
+def _synth_shirley(x, peaks, a, b):
+    """Shirley background a + (b - a) C(x)/C(x_last), C the running integral of
+    the peak signal from the first point (right-end rectangle rule)."""
+    inc = np.zeros_like(x)
+    inc[1:] = peaks[1:] * np.abs(np.diff(x))
+    c = np.cumsum(inc)
+    return a + (b - a) * c / c[-1] if c[-1] > 0 else np.full_like(x, a)
+
+
+def xps_shirley(seed: int = 1, n: int = 840, k_true: int = 7, k_min: int = 5, k_max: int = 8,
+                scale: float = 3.0e4) -> Spectrum:
+    """XPS spectrum of the App. E kind: a Ni 2p-like core level on 840 points of
+    binding energy 845-887 eV (the paper's measured grid), pseudo-Voigt peaks on
+    a Shirley background, noise of variance f + (0.01 f)^2 (App. E with
+    sigma_0 = 1, sigma_1 = 0.01, sigma_2 = 0), and the paper's data-derived
+    uniform priors (App. E prior table).  Peaks: two spin-orbit groups 17.3 eV
+    apart (main line, a second chemical state +2.7 eV, a satellite +6 eV) and
+    one weak feature between them; HWHM 0.6-2.0 eV, eta ~ U[0.4, 0.9], amplitudes
+    S 10^U[-0.8, 0]; Shirley start 0.3 S, end 0.9 S.  The measured spectrum is
+    not available; this stands in for it."""
+    rng = np.random.default_rng(seed)
+    x = np.linspace(845.0, 887.0, n)
+    base = [852.6, 855.3, 858.6, 869.9, 872.6, 875.9, 864.5][:k_true]
+    mus = [m + rng.uniform(-0.3, 0.3) for m in base]
+    hwhm = rng.uniform(0.6, 2.0, len(mus))
+    eta = rng.uniform(0.4, 0.9, len(mus))
+    amp = scale * 10.0 ** rng.uniform(-0.8, 0.0, len(mus))
+    peaks = np.zeros_like(x)
+    for k in range(len(mus)):
+        peaks += _synth_pv(x, amp[k], mus[k], hwhm[k], eta[k])
+    f = peaks + _synth_shirley(x, peaks, 0.3 * scale, 0.9 * scale)
+    s0, s1, s2 = 1.0, 0.01, 0.0
+    var = s0 ** 2 * f + s1 ** 2 * f ** 2 + s2 ** 2
+    y = f + np.sqrt(var) * rng.normal(size=x.shape)
+    ymin, ymax = float(y.min()), float(y.max())
+    pri = Priors(amp=Prior(UNIFORM, max(0.0, 0.3 * ymin), 1.05 * ymax),
+                 centre=Prior(UNIFORM, float(x.min()), float(x.max())),
+                 width=Prior(UNIFORM, 0.1, 15.0),
+                 eta=Prior(UNIFORM, 0.0, 1.0),
+                 bg=[Prior(UNIFORM, 0.95 * float(y[0]), 1.01 * float(y[0])),
+                     Prior(UNIFORM, 0.95 * float(y[-1]), 1.01 * float(y[-1]))])
+    return Spectrum(x, y, np.ones_like(x), PSEUDO_VOIGT, k_min, k_max, BG_SHIRLEY, 0, pri,
+                    truth={"K": len(mus), "A": amp.tolist(), "mu": mus, "hwhm": hwhm.tolist(),
+                           "eta": eta.tolist(), "a": 0.3 * scale, "b": 0.9 * scale},
+                    name=f"xps-shirley-{n}", noise=NOISE_MODEL, noise_par=(s0, s1, s2))
 
 
 def xrd_like(seed: int = 1, n: int = 4096, k_true: int = 10, k_max: int = 12) -> Spectrum:

@@ -297,6 +297,32 @@ def test_full_run_fp32_matches_oracle_gaussian(ctx):
     assert np.all(np.argmax(lz32, axis=1) == 1) and np.all(np.argmax(lz64, axis=1) == 1)
 
 
+def test_posterior_means_within_two_standard_errors(ctx):
+    # posterior means of the selected model (K = 2, peaks sorted by centre):
+    # the FP32 batched path against the oracle's estimator, each averaged over
+    # 16 seeds, |difference| <= 2 standard errors of the difference (from the
+    # spread over seeds).  The oracle's replicates come from the FP64 path,
+    # which is checked here to give the oracle's own summaries on two seeds.
+    spec = W.gaussian_small(3)
+    spec.k_min = spec.k_max = 2
+    m32, m64 = [], []
+    for s in range(1, 17):
+        o = W.Options(particles=1024, sweeps=10, seed=s)
+        m32.append(ctx.run(spec, o, keep_samples=False)["post_mean"][0])
+        m64.append(ctx.run(spec, W.Options(particles=1024, sweeps=10, seed=s, energy_fp64=1),
+                           keep_samples=False)["post_mean"][0])
+    for s in (1, 2):
+        ref = oracle.run(spec, W.Options(particles=1024, sweeps=10, seed=s))
+        np.testing.assert_allclose(m64[s - 1], ref["post_mean"][0], rtol=1e-6, atol=1e-9)
+    m32, m64 = np.array(m32), np.array(m64)
+    se = np.sqrt(m32.var(axis=0, ddof=1) / 16 + m64.var(axis=0, ddof=1) / 16)
+    diff = np.abs(m32.mean(0) - m64.mean(0))
+    assert np.all(diff <= 2 * se + 1e-12), (diff, se)
+    # and both estimate the truth (A, mu, sd) of the two peaks
+    truth = np.array([1.0, 3.5, 0.5, 0.6, 6.0, 0.8])
+    assert np.all(np.abs(m32.mean(0) - truth) < 0.1 * np.maximum(truth, 1.0))
+
+
 def test_full_run_waste_free(ctx):
     spec = W.gaussian_small(2)
     opts = W.Options(particles=600, sweeps=6, seed=3, waste_free=1)

@@ -9,7 +9,7 @@ import math
 import mpmath
 import numpy as np
 import pytest
-from scipy import integrate, stats
+from scipy import integrate, special, stats
 
 import oracle
 from conftest import load_golden
@@ -434,3 +434,107 @@ def test_waste_free_particle_count():
     r = oracle.run_job(spec, 1, W.Options(particles=100, sweeps=7, waste_free=1, seed=2))
     assert r["status"] == 0
     assert r["samples"].shape[0] == 15 * 7
+
+
+# --------------------------------------------------------------------------
+# XPS model of App. E: Shirley background, variance that follows the model
+# --------------------------------------------------------------------------
+
+def test_shirley_background_endpoints_and_gaussian_closed_form():
+    # one Gaussian peak on a fine grid: the background is a at the first point,
+    # b at the last, and in between a + (b - a) times the normalised running
+    # integral of the peak, which for a Gaussian is a difference of erf values
+    x = np.linspace(0.0, 10.0, 20001)
+    A, mu, w, a, b = 2.0, 4.3, 0.7, 1.5, 3.25
+    f = oracle.model_vec(GAUSS, 1, W.BG_SHIRLEY, 0, [A, mu, w, a, b], x)
+    peak = A * np.exp(-0.5 * ((x - mu) / w) ** 2)
+    bg = f - peak
+    assert bg[0] == pytest.approx(a, rel=1e-15) and bg[-1] == pytest.approx(b, rel=1e-15)
+    Phi = lambda z: 0.5 * (1.0 + special.erf(z / math.sqrt(2.0)))
+    frac = (Phi((x - mu) / w) - Phi((x[0] - mu) / w)) / (Phi((x[-1] - mu) / w) - Phi((x[0] - mu) / w))
+    np.testing.assert_allclose(bg, a + (b - a) * frac, atol=2e-3 * (b - a))
+    assert np.all(np.diff(bg) >= 0.0)
+    # no peak signal: the background is the start value
+    f0 = oracle.model_vec(GAUSS, 0, W.BG_SHIRLEY, 0, [a, b], x)
+    np.testing.assert_array_equal(f0, np.full_like(x, a))
+
+
+def _mp_energy_model(K, nat, x, y, s0, s1, s2):
+    """1/2 ln(2 pi v) + 1/2 (y - f)^2 / v summed, v = s0^2 f + s1^2 f^2 + s2^2,
+    f = PV peaks (Eq. (E1)) + Shirley background, in 50-digit arithmetic."""
+    mpmath.mp.dps = 50
+    X = [mpmath.mpf(float(v)) for v in x]
+    P = []
+    for xi in X:
+        t = mpmath.mpf(0)
+        for k in range(K):
+            A, mu, g, eta = [mpmath.mpf(float(v)) for v in nat[4 * k:4 * k + 4]]
+            d2 = (xi - mu) ** 2
+            t += A * (eta * mpmath.e ** (-mpmath.log(2) * d2 / (g * g)) + (1 - eta) * g * g / (g * g + d2))
+        P.append(t)
+    a, b = mpmath.mpf(float(nat[4 * K])), mpmath.mpf(float(nat[4 * K + 1]))
+    inc = [mpmath.mpf(0)] + [P[i] * abs(X[i] - X[i - 1]) for i in range(1, len(X))]
+    tot = sum(inc)
+    run, e = mpmath.mpf(0), mpmath.mpf(0)
+    for i in range(len(X)):
+        run += inc[i]
+        f = P[i] + a + (b - a) * run / tot
+        v = mpmath.mpf(s0) ** 2 * f + mpmath.mpf(s1) ** 2 * f * f + mpmath.mpf(s2) ** 2
+        e += mpmath.log(2 * mpmath.pi * v) / 2 + (mpmath.mpf(float(y[i])) - f) ** 2 / (2 * v)
+    return float(e)
+
+
+def test_energy_model_variance_brute_force():
+    rng = np.random.default_rng(21)
+    x = np.sort(rng.uniform(845.0, 860.0, 11))
+    nat = [3000.0, 850.0, 1.2, 0.6, 1200.0, 854.5, 0.8, 0.3, 800.0, 1100.0]
+    f = oracle.model_vec(PV, 2, W.BG_SHIRLEY, 0, nat, x)
+    y = f + rng.normal(0.0, 30.0, x.shape)
+    spec = W.Spectrum(x, y, np.ones_like(x), PV, 2, 2, W.BG_SHIRLEY, 0,
+                      W.Priors(amp=W.Prior(W.UNIFORM, 0, 1), centre=W.Prior(W.UNIFORM, 0, 1),
+                               width=W.Prior(W.UNIFORM, 0, 1)), truth={},
+                      noise=W.NOISE_MODEL, noise_par=(1.0, 0.01, 0.5))
+    e = oracle.energy_spec(spec, 2, nat)
+    assert e == pytest.approx(_mp_energy_model(2, nat, x, y, 1.0, 0.01, 0.5), rel=1e-13)
+
+
+def test_constant_model_variance_reduces_to_known_sigma():
+    # variance (0, 0, s): the energy is the known-sigma energy plus N/2 ln(2 pi s^2),
+    # and log Z (which carries the normaliser in the known-sigma case) is equal
+    spec = W.tiny_single_peak(7, n=31)
+    s = float(spec.sigma[0])
+    nat = [1.1, 0.95, 0.3]
+    e_known = oracle.energy_spec(spec, 1, nat)
+    spec_m = W.Spectrum(spec.x, spec.y, spec.sigma, spec.family, 1, 1, spec.bg, 0, spec.priors,
+                        truth={}, noise=W.NOISE_MODEL, noise_par=(0.0, 0.0, s))
+    e_model = oracle.energy_spec(spec_m, 1, nat)
+    assert e_model - e_known == pytest.approx(0.5 * spec.n * math.log(2 * math.pi * s * s), rel=1e-12)
+    o = W.Options(particles=400, sweeps=4, seed=3)
+    assert oracle.run_job(spec_m, 1, o)["log_z"] == pytest.approx(oracle.run_job(spec, 1, o)["log_z"], abs=1e-8)
+
+
+def test_evidence_k1_quadrature_model_variance_shirley():
+    # App. E likelihood, K = 1 pseudo-Voigt on a Shirley background with only the
+    # amplitude free (uniform prior): Z = int p(A) exp(-E(A)) dA by quadrature
+    x = np.linspace(850.0, 860.0, 41)
+    mu, g, eta, a, b = 855.0, 1.0, 0.5, 500.0, 900.0
+    truth = [2000.0, mu, g, eta, a, b]
+    f = oracle.model_vec(PV, 1, W.BG_SHIRLEY, 0, truth, x)
+    rng = np.random.default_rng(4)
+    y = f + np.sqrt(f + (0.01 * f) ** 2) * rng.normal(size=x.shape)
+    pri = W.Priors(amp=W.Prior(W.UNIFORM, 1000.0, 3000.0), centre=W.Prior(W.UNIFORM, 850, 860),
+                   width=W.Prior(W.UNIFORM, 0.1, 5.0))
+    spec = W.Spectrum(x, y, np.ones_like(x), PV, 1, 1, W.BG_SHIRLEY, 0, pri, truth={},
+                      noise=W.NOISE_MODEL, noise_par=(1.0, 0.01, 0.0))
+    spec.comp_priors = [W.Prior(W.UNIFORM, 1000.0, 3000.0), W.Prior(W.FIXED, mu), W.Prior(W.FIXED, g),
+                        W.Prior(W.FIXED, eta), W.Prior(W.FIXED, a), W.Prior(W.FIXED, b)]
+    E = lambda A: oracle.energy_spec(spec, 1, [A, mu, g, eta, a, b])
+    grid = np.linspace(1000.0, 3000.0, 2001)
+    emin = min(E(A) for A in grid)
+    Z, _ = integrate.quad(lambda A: math.exp(-(E(A) - emin)) / 2000.0, 1000.0, 3000.0,
+                          points=[float(grid[np.argmin([E(A) for A in grid])])], limit=400,
+                          epsabs=0, epsrel=1e-11)
+    exact = math.log(Z) - emin
+    vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"] for s in range(1, 6)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
