@@ -18,14 +18,25 @@
  *                                                               eta: Gaussian fraction (Eq. (E1))
  *   SMC_GAUSS_PRECISION g = A exp(-b/2 (x-mu)^2)               b: precision (App. C Eq. (C1))
  * and background b(x) = sum_j c_j T_j(t), T_j Chebyshev polynomials of the first
- * kind, t = (2x - (x_min + x_max)) / (x_max - x_min).
+ * kind, t = (2x - (x_min + x_max)) / (x_max - x_min), or the Shirley background
+ * of App. E (SMC_BG_SHIRLEY, components a, b):
+ *   B_i = a + (b - a) C_i / C_N,  C_i = sum_{1 < j <= i} P_j |x_j - x_{j-1}|,
+ * P the peak sum, points in data order: the running integral of the peak signal
+ * from the first point (right-end rectangle rule), B = a at the first point and
+ * b at the last (B = a if C_N = 0).
  * Components per job, in this order (the Metropolis sweep order): for each peak
  * (A, mu, w[, eta]), then c_0 .. c_{nbg-1}.  d = p K + nbg, p = 3 or 4.
  *
- * Likelihood: Gaussian with known per-point sigma_i.  Energy
- * E(theta) = 1/2 sum_i ((y_i - f_i)/sigma_i)^2; the returned log Z includes the
- * normaliser -sum_i log(sqrt(2 pi) sigma_i), so log Z is the log marginal
- * likelihood of Eq. (5) and F = -log Z.
+ * Likelihood (smc_request.noise): SMC_NOISE_KNOWN, Gaussian with known per-point
+ * sigma_i, energy E(theta) = 1/2 sum_i ((y_i - f_i)/sigma_i)^2, the returned
+ * log Z including the normaliser -sum_i log(sqrt(2 pi) sigma_i); or
+ * SMC_NOISE_MODEL (App. E), variance following the model value,
+ *   sigma_i^2 = s0^2 f_i + s1^2 f_i^2 + s2^2   (noise_par = {s0, s1, s2}),
+ * E = sum_i [1/2 ln(2 pi sigma_i^2) + 1/2 (y_i - f_i)^2 / sigma_i^2] (+inf where
+ * sigma_i^2 <= 0), sigma unused.  Either way log Z is the log marginal likelihood
+ * of Eq. (5) and F = -log Z.  The Shirley background and the model variance run
+ * in the coupled-grid Metropolis kernel and are combined with no Chebyshev
+ * background.
  *
  * Errors: every call returns an int status (SMC_OK = 0 or an SMC_E* code).
  * On error nothing is allocated on the caller's behalf and output arguments
@@ -66,7 +77,8 @@ enum smc_status {
 };
 
 enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2, SMC_GAUSS_PRECISION = 3 };
-enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3 };
+enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3, SMC_BG_SHIRLEY = 4 };
+enum smc_noise { SMC_NOISE_KNOWN = 0, SMC_NOISE_MODEL = 1 };
 
 /* Prior kinds.  Sampling coordinates: log v for LOG_UNIFORM, v otherwise.
  *   SMC_UNIFORM      p1 = lower, p2 = upper
@@ -110,12 +122,14 @@ typedef struct {
 
 /* One spectrum and its candidate range, for smc_run_batch / smc_submit. */
 typedef struct {
-    const double *x, *y, *sigma;  /* n points each (host, or device if flagged)  */
-    int64_t n;
+    const double *x, *y, *sigma;  /* n points each (host, or device if flagged);  */
+    int64_t n;                    /* sigma may be NULL with SMC_NOISE_MODEL       */
     int32_t k_min, k_max;
     int32_t family, bg, bg_degree;
     const smc_priors *priors;
     const smc_options *opts;
+    int32_t noise;                /* smc_noise (SMC_NOISE_KNOWN = 0)              */
+    double noise_par[3];          /* s0, s1, s2 of SMC_NOISE_MODEL                */
 } smc_request;
 
 /* Result of one spectrum: arrays indexed by K - k_min.  Views are owned by the

@@ -51,7 +51,8 @@ class Request(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("sigma", C.c_void_p), ("n", C.c_int64),
                 ("k_min", C.c_int32), ("k_max", C.c_int32), ("family", C.c_int32),
                 ("bg", C.c_int32), ("bg_degree", C.c_int32),
-                ("priors", C.POINTER(Priors)), ("opts", C.POINTER(Options))]
+                ("priors", C.POINTER(Priors)), ("opts", C.POINTER(Options)),
+                ("noise", C.c_int32), ("noise_par", C.c_double * 3)]
 
 
 class Profile(C.Structure):
@@ -166,7 +167,9 @@ class _Marshalled:
             self.dev = device_arrays  # keep torch tensors alive
             xp, yp, sp = [int(t.data_ptr()) for t in device_arrays]
         self.req = Request(xp, yp, sp, spec.n, spec.k_min, spec.k_max, spec.family, spec.bg,
-                           spec.bg_degree, C.pointer(self.pri), C.pointer(self.opts))
+                           spec.bg_degree, C.pointer(self.pri), C.pointer(self.opts),
+                           int(getattr(spec, "noise", 0)),
+                           (C.c_double * 3)(*getattr(spec, "noise_par", (0.0, 0.0, 0.0))))
 
 
 def _dim(family: int, K: int, bg: int, bg_degree: int) -> int:

@@ -25,6 +25,7 @@ static int bg_params(int bg, int deg)
     case SMC_BG_NONE: return 0;
     case SMC_BG_CONST: return 1;
     case SMC_BG_LINEAR: return 2;
+    case SMC_BG_SHIRLEY: return 2;
     default: return deg + 1;
     }
 }
@@ -41,6 +42,20 @@ int kernel_family(int family) { return family == SMC_GAUSS_PRECISION ? SMC_GAUSS
 // ---------------------------------------------------------------------------
 Tile choose_tile(int family, int n)
 {
+    if (family & MH_COUPLED) {  // coupled-grid kernel: J = 8 or 4, least padding
+        Tile best{0, 0};
+        long best_pad = -1;
+        for (int J : {8, 4})
+            for (int G : {1, 2, 4, 8, 16}) {
+                if (!mh_tile_supported(family, J, G) || 32L * G * J < n) continue;
+                if (best_pad < 0 || 32L * G * J < best_pad) {
+                    best = {J, G};
+                    best_pad = 32L * G * J;
+                }
+                break;
+            }
+        return best;
+    }
     // measured on B300 (XPS-, XRD- and App. C-shaped grids): J = 8 (64
     // registers, 32 warps/SM) while four warps per chain cover the grid,
     // J = 16 (128 registers) beyond; other J only when they pad much less
@@ -105,10 +120,17 @@ static int comp_role(const Request &r, int K, int j)
 
 int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 {
-    if (!rq.priors || !rq.opts || !rq.x || !rq.y || !rq.sigma) return SMC_EINVAL;
+    if (!rq.priors || !rq.opts || !rq.x || !rq.y) return SMC_EINVAL;
+    if (rq.noise != SMC_NOISE_KNOWN && rq.noise != SMC_NOISE_MODEL) return SMC_EINVAL;
+    if (rq.noise == SMC_NOISE_KNOWN && !rq.sigma) return SMC_EINVAL;
+    if (rq.noise == SMC_NOISE_MODEL)
+        for (int q = 0; q < 3; ++q)
+            if (!std::isfinite(rq.noise_par[q])) return SMC_EINVAL;
     const smc_options &o = *rq.opts;
     if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
-    if (rq.family < 0 || rq.family > 3 || rq.bg < 0 || rq.bg > 3) return SMC_EINVAL;
+    if (rq.family < 0 || rq.family > 3 || rq.bg < 0 || rq.bg > 4) return SMC_EINVAL;
+    const bool full = rq.bg == SMC_BG_SHIRLEY || rq.noise == SMC_NOISE_MODEL;
+    if (full && rq.bg != SMC_BG_NONE && rq.bg != SMC_BG_SHIRLEY) return SMC_EINVAL;
     if (rq.bg == SMC_BG_POLY && (rq.bg_degree < 0 || rq.bg_degree >= SMC_MAX_BG)) return SMC_EINVAL;
     if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
     if (job_dim(rq.family, rq.k_max, rq.bg, rq.bg_degree) > SMC_MAX_DIM) return SMC_EINVAL;
@@ -127,6 +149,9 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     r->nbg = bg_params(rq.bg, rq.bg_degree);
     r->p = peak_params(rq.family);
     r->n = (int)rq.n;
+    r->noise = rq.noise;
+    for (int q = 0; q < 3; ++q) r->noise_par[q] = rq.noise == SMC_NOISE_MODEL ? rq.noise_par[q] : 0.0;
+    r->full = full;
     r->opts = o;
     r->pri = *rq.priors;
     r->fp64 = o.energy_fp64 != 0;
@@ -149,7 +174,7 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
             }
     }
     if (!r->fp64) {
-        const int kf = kernel_family(r->family);
+        const int kf = kernel_family(r->family) | (full ? MH_COUPLED : 0);
         r->tile = choose_tile(kf, r->n);
         for (const auto &t : c.tiles)
             if (t[0] == kf && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
@@ -165,17 +190,18 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     } else {
         r->n_pad = r->n;
     }
+    const bool known = rq.noise == SMC_NOISE_KNOWN;
     if (on_device) {
         r->dx = rq.x;
         r->dy = rq.y;
-        r->ds = rq.sigma;
+        r->ds = known ? rq.sigma : nullptr;
     } else {
         r->hx.assign(rq.x, rq.x + rq.n);
         r->hy.assign(rq.y, rq.y + rq.n);
-        r->hs.assign(rq.sigma, rq.sigma + rq.n);
+        if (known) r->hs.assign(rq.sigma, rq.sigma + rq.n);
         for (int i = 0; i < r->n; ++i)
-            if (!std::isfinite(r->hx[i]) || !std::isfinite(r->hy[i]) || !std::isfinite(r->hs[i]) ||
-                !(r->hs[i] > 0.0)) {
+            if (!std::isfinite(r->hx[i]) || !std::isfinite(r->hy[i]) ||
+                (known && (!std::isfinite(r->hs[i]) || !(r->hs[i] > 0.0)))) {
                 delete r;
                 return SMC_EINVAL;
             }
@@ -346,13 +372,15 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         double *raw = (double *)(sa + SL.raw);
         CK(cudaMemcpyAsync(raw, r.hx.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
         CK(cudaMemcpyAsync(raw + r.n, r.hy.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
-        CK(cudaMemcpyAsync(raw + 2 * r.n, r.hs.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
-        c.prof.h2d_bytes += 24.0 * r.n;
+        if (!r.hs.empty())
+            CK(cudaMemcpyAsync(raw + 2 * r.n, r.hs.data(), r.n * 8, cudaMemcpyHostToDevice, c.stream));
+        c.prof.h2d_bytes += (r.hs.empty() ? 16.0 : 24.0) * r.n;
         ix = raw;
         iy = raw + r.n;
-        is = raw + 2 * r.n;
+        is = r.hs.empty() ? nullptr : raw + 2 * r.n;
     }
-    CK(launch_spec_prep(ix, iy, is, r.n, r.n_pad, r.fp64 ? 0 : 1, r.sd, c.stream));
+    CK(launch_spec_prep(ix, iy, is, r.n, r.n_pad, r.fp64 ? 0 : 1, r.noise,
+                        r.bg == SMC_BG_SHIRLEY ? 1 : 0, r.sd, c.stream));
 
     std::vector<int> slots;
     for (int K = r.k_min; K <= r.k_max; ++K) {
@@ -391,6 +419,15 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.n_pad = r.n_pad;
         jb.family = kernel_family(r.family);
         jb.wprec = r.family == SMC_GAUSS_PRECISION ? 1 : 0;
+        jb.bg_kind = r.bg;
+        jb.noise = r.noise;
+        jb.full = r.full ? 1 : 0;
+        jb.nd0 = r.noise_par[0] * r.noise_par[0];
+        jb.nd1 = r.noise_par[1] * r.noise_par[1];
+        jb.nd2 = r.noise_par[2] * r.noise_par[2];
+        jb.nv0 = (float)jb.nd0;
+        jb.nv1 = (float)jb.nd1;
+        jb.nv2 = (float)jb.nd2;
         jb.K = K;
         jb.p = r.p;
         jb.nbg = r.nbg;
@@ -478,10 +515,11 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
             P.max_T = std::max<int64_t>(P.max_T, jb.T);
             P.max_stages = std::max(P.max_stages, jb.max_stages);
             Bucket *b = nullptr;
+            const int kfam = jb.family | (jb.full ? MH_COUPLED : 0);
             for (Bucket &x : P.buckets)
-                if (x.family == jb.family && x.J == jb.J && x.G == jb.G) b = &x;
+                if (x.family == kfam && x.J == jb.J && x.G == jb.G) b = &x;
             if (!b) {
-                P.buckets.push_back({jb.family, jb.J, jb.G, {}});
+                P.buckets.push_back({kfam, jb.J, jb.G, {}});
                 b = &P.buckets.back();
             }
             b->slots.push_back(sl);

@@ -38,6 +38,9 @@ struct Request {
     smc_job id = 0;
     int k_min = 0, k_max = 0, family = 0, bg = 0, bg_degree = 0, nbg = 0, p = 3;
     int n = 0;
+    int noise = 0;                 // SMC_NOISE_*
+    double noise_par[3] = {0, 0, 0};
+    bool full = false;             // coupled-grid Metropolis kernel
     smc_options opts{};
     smc_priors pri{};
     std::vector<smc_prior> comp;

@@ -1,5 +1,6 @@
-// k_mh.cu -- tile dispatch and launch of the fused FP32 Metropolis kernel
-// (kernel in k_mh_impl.cuh, instantiated per family in k_mh_{gauss,lor,pv}.cu).
+// k_mh.cu -- tile dispatch and launch of the fused FP32 Metropolis kernels
+// (k_mh_impl.cuh, instantiated per family in k_mh_{gauss,lor,pv}.cu; the
+// coupled-grid kernel of k_mh_full.cuh in k_mh_full_{gauss,lor,pv}.cu).
 #include "kernels.h"
 
 namespace smc {
@@ -8,13 +9,23 @@ typedef void (*mh_fn)(JobDev *, const int *, int);
 mh_fn mh_pick_gauss(int J, int G);
 mh_fn mh_pick_lor(int J, int G);
 mh_fn mh_pick_pv(int J, int G);
+mh_fn mhf_pick_gauss(int J, int G);
+mh_fn mhf_pick_lor(int J, int G);
+mh_fn mhf_pick_pv(int J, int G);
 
 static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 
+// family: FAM_* of the peaks, plus MH_COUPLED for the coupled-grid kernel
 static mh_fn pick(int family, int J, int G)
 {
-    if (family == FAM_GAUSS) return mh_pick_gauss(J, G);
-    if (family == FAM_LORENTZ) return mh_pick_lor(J, G);
+    const int fam = family & (MH_COUPLED - 1);
+    if (family & MH_COUPLED) {
+        if (fam == FAM_GAUSS) return mhf_pick_gauss(J, G);
+        if (fam == FAM_LORENTZ) return mhf_pick_lor(J, G);
+        return mhf_pick_pv(J, G);
+    }
+    if (fam == FAM_GAUSS) return mh_pick_gauss(J, G);
+    if (fam == FAM_LORENTZ) return mh_pick_lor(J, G);
     return mh_pick_pv(J, G);
 }
 

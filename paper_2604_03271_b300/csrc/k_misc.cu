@@ -146,6 +146,67 @@ __device__ __forceinline__ float energy_warp(const JobDev &jb, const float *P)
     return s + c;
 }
 
+// Coupled-grid likelihoods (Shirley background, model variance): a lane owns a
+// contiguous run of grid points; the running integral of the peak signal is a
+// lane-local sum plus a warp scan; peaks are evaluated twice (total, then the
+// running pass) instead of stored.
+template <int FAM>
+__device__ __forceinline__ float energy_warp_full(const JobDev &jb, const float *P)
+{
+    const int lane = threadIdx.x & 31;
+    const int K = jb.K, p = jb.p, n = jb.n;
+    const bool shir = jb.bg_kind == BGK_SHIRLEY, model = jb.noise == NZ_MODEL;
+    const int ch = (n + 31) / 32, lo = min(n, lane * ch), hi = min(n, lo + ch);
+    auto peaks = [&](int pt) {
+        const float x = jb.xc[pt];
+        float f = 0.0f;
+        for (int k = 0; k < K; ++k)
+            f += peak_eval<FAM>(x, P[k * p], P[k * p + 1], P[k * p + 2], FAM == FAM_PV ? P[k * p + 3] : 0.0f);
+        return f;
+    };
+    float a = 0.0f, b = 0.0f, start = 0.0f, iCN = 0.0f;
+    if (shir) {
+        a = P[p * K];
+        b = P[p * K + 1];
+        float part = 0.0f;
+        for (int pt = lo; pt < hi; ++pt) part = fmaf(jb.ts[pt], peaks(pt), part);
+        float sc = part;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float t = __shfl_up_sync(FULL_MASK, sc, o);
+            if (lane >= o) sc += t;
+        }
+        start = __shfl_up_sync(FULL_MASK, sc, 1);
+        if (lane == 0) start = 0.0f;
+        const float CN = __shfl_sync(FULL_MASK, sc, 31);
+        iCN = CN > 0.0f ? 1.0f / CN : 0.0f;
+    }
+    float s = 0.0f, c = 0.0f, run = start;
+    for (int pt = lo; pt < hi; ++pt) {
+        const float Pk = peaks(pt);
+        float f = Pk;
+        if (shir) {
+            run = fmaf(jb.ts[pt], Pk, run);
+            f += fmaf(b - a, run * iCN, a);
+        }
+        const float r = jb.y[pt] - f;
+        float term;
+        if (!model) {
+            term = 0.5f * jb.wt[pt] * r * r;
+        } else {
+            const float v = fmaf(fmaf(jb.nv1, f, jb.nv0), f, jb.nv2);
+            term = v > 0.0f ? fmaf(0.34657359027997264f, __log2f(v), 0.91893853320467274f) + 0.5f * r * r / v
+                            : INFINITY;
+        }
+        const float yk = term - c;
+        const float tk = s + yk;
+        c = (tk - s) - yk;
+        s = tk;
+    }
+    c = -c;
+    warp_sum2(s, c);
+    return s + c;
+}
+
 __global__ void __launch_bounds__(256) k_energy_f32(JobDev *jobs, const int *slots)
 {
     __shared__ float par[8][SMC_DMAX];
@@ -165,7 +226,14 @@ __global__ void __launch_bounds__(256) k_energy_f32(JobDev *jobs, const int *slo
     }
     __syncwarp();
     float e;
-    if (jb.family == FAM_GAUSS)
+    if (jb.full) {
+        if (jb.family == FAM_GAUSS)
+            e = energy_warp_full<FAM_GAUSS>(jb, P);
+        else if (jb.family == FAM_LORENTZ)
+            e = energy_warp_full<FAM_LORENTZ>(jb, P);
+        else
+            e = energy_warp_full<FAM_PV>(jb, P);
+    } else if (jb.family == FAM_GAUSS)
         e = energy_warp<FAM_GAUSS>(jb, P);
     else if (jb.family == FAM_LORENTZ)
         e = energy_warp<FAM_LORENTZ>(jb, P);

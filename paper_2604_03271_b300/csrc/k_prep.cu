@@ -18,7 +18,7 @@ namespace smc {
 
 __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const double *y,
                                                     const double *sg, int n, int n_pad,
-                                                    int centre, SpecDev sd)
+                                                    int centre, int noise, int shirley, SpecDev sd)
 {
     __shared__ double r0[32], r1[32], r2[32];
     __shared__ double s_lo, s_hi;
@@ -27,11 +27,15 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
     double lo = INFINITY, hi = -INFINITY, ln = 0.0;
     int bad = 0;
     for (int i = tid; i < n; i += blockDim.x) {
-        const double xi = x[i], yi = y[i], si = sg[i];
-        if (!isfinite(xi) || !isfinite(yi) || !isfinite(si) || !(si > 0.0)) bad = 1;
+        const double xi = x[i], yi = y[i];
+        if (!isfinite(xi) || !isfinite(yi)) bad = 1;
+        if (noise == NZ_KNOWN) {
+            const double si = sg[i];
+            if (!isfinite(si) || !(si > 0.0)) bad = 1;
+            ln -= log(sqrt(2.0 * 3.141592653589793) * si);
+        }
         lo = fmin(lo, xi);
         hi = fmax(hi, xi);
-        ln -= log(sqrt(2.0 * 3.141592653589793) * si);
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = fmin(lo, __shfl_xor_sync(FULL_MASK, lo, o));
@@ -70,12 +74,13 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
         if (i < n) {
             const double xi = x[i];
             sd.xc[i] = (float)(xi - xref);
-            sd.wt[i] = (float)(1.0 / (sg[i] * sg[i]));
+            sd.wt[i] = noise == NZ_KNOWN ? (float)(1.0 / (sg[i] * sg[i])) : 1.0f;
             sd.y[i] = (float)y[i];
-            sd.ts[i] = (float)((2.0 * xi - (xmin + xmax)) / (xmax - xmin));
+            sd.ts[i] = shirley ? (i > 0 ? (float)fabs(xi - x[i - 1]) : 0.0f)
+                               : (float)((2.0 * xi - (xmin + xmax)) / (xmax - xmin));
             sd.x64[i] = xi;
             sd.y64[i] = y[i];
-            sd.is64[i] = 1.0 / sg[i];
+            sd.is64[i] = noise == NZ_KNOWN ? 1.0 / sg[i] : 1.0;
         } else {
             sd.xc[i] = 0.0f;
             sd.wt[i] = 0.0f;
@@ -86,9 +91,9 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
 }
 
 cudaError_t launch_spec_prep(const double *x, const double *y, const double *sg, int n, int n_pad,
-                             int centre, const SpecDev &sd, cudaStream_t s)
+                             int centre, int noise, int shirley, const SpecDev &sd, cudaStream_t s)
 {
-    k_spec_prep<<<1, 1024, 0, s>>>(x, y, sg, n, n_pad, centre, sd);
+    k_spec_prep<<<1, 1024, 0, s>>>(x, y, sg, n, n_pad, centre, noise, shirley, sd);
     return cudaGetLastError();
 }
 

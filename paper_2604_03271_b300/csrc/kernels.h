@@ -43,6 +43,9 @@ cudaError_t launch_gather(JobDev *jobs, const int *slots, int nslots, int64_t ma
 
 // Fused FP32 Metropolis stage of one bucket (family, points per lane J, warps
 // per chain G, all listed jobs sharing them); grid 0 = one wave of resident CTAs.
+// family = FAM_* of the peaks, | MH_COUPLED for the coupled-grid kernel (Shirley
+// background and/or model variance).
+constexpr int MH_COUPLED = 16;
 cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
                       int grid, cudaStream_t s);
 bool mh_tile_supported(int family, int J, int G);

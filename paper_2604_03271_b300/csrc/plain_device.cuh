@@ -17,8 +17,56 @@ __device__ __forceinline__ double peak_eval_d(int fam, int wprec, double x, doub
     return A * (eta * exp(-dx * dx / (2.0 * sg * sg)) + (1.0 - eta) * lor);
 }
 
+// sum of the K peaks at x (natural parameters)
+__device__ __forceinline__ double peaks_at_d(const JobDev &jb, const double *nat, double x)
+{
+    double f = 0.0;
+    for (int k = 0; k < jb.K; ++k) {
+        const double *q = nat + jb.p * k;
+        f += peak_eval_d(jb.family, jb.wprec, x, q[0], q[1], q[2], jb.p == 4 ? q[3] : 0.0);
+    }
+    return f;
+}
+
+// Coupled-grid likelihoods (App. E): Shirley background B_i = a + (b - a)
+// C_i / C_N with C_i = sum_{1 < j <= i} P_j |x_j - x_{j-1}| (B = a if C_N = 0),
+// and the known-sigma or the model-variance energy
+// sum [1/2 ln(2 pi v) + 1/2 (y - f)^2 / v], v = nd0 f + nd1 f^2 + nd2.
+__device__ __forceinline__ double energy_plain_full(const JobDev &jb, const double *nat)
+{
+    const bool shir = jb.bg_kind == BGK_SHIRLEY, model = jb.noise == NZ_MODEL;
+    double a = 0.0, b = 0.0, total = 0.0;
+    if (shir) {
+        a = nat[jb.p * jb.K];
+        b = nat[jb.p * jb.K + 1];
+        for (int pt = 1; pt < jb.n; ++pt)
+            total += peaks_at_d(jb, nat, jb.x64[pt]) * fabs(jb.x64[pt] - jb.x64[pt - 1]);
+    }
+    double e = 0.0, run = 0.0;
+    for (int pt = 0; pt < jb.n; ++pt) {
+        const double x = jb.x64[pt];
+        const double P = peaks_at_d(jb, nat, x);
+        double f = P;
+        if (shir) {
+            if (pt > 0) run += P * fabs(x - jb.x64[pt - 1]);
+            f += total > 0.0 ? a + (b - a) * run / total : a;
+        }
+        const double r = jb.y64[pt] - f;
+        if (!model) {
+            const double rs = r * jb.is64[pt];
+            e += 0.5 * rs * rs;
+        } else {
+            const double v = jb.nd0 * f + jb.nd1 * f * f + jb.nd2;
+            if (!(v > 0.0)) return INFINITY;
+            e += 0.5 * log(2.0 * 3.141592653589793 * v) + 0.5 * r * r / v;
+        }
+    }
+    return e;
+}
+
 __device__ __forceinline__ double energy_plain(const JobDev &jb, const double *nat)
 {
+    if (jb.full) return energy_plain_full(jb, nat);
     double e = 0.0;
     for (int pt = 0; pt < jb.n; ++pt) {
         const double x = jb.x64[pt];

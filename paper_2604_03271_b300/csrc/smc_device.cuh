@@ -20,6 +20,8 @@
 enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2 };
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
 enum { JOB_FREE = 0, JOB_ACTIVE = 1, JOB_DONE = 2 };
+enum { BGK_SHIRLEY = 4 };                 // smc_bg value of the Shirley background
+enum { NZ_KNOWN = 0, NZ_MODEL = 1 };      // smc_noise values
 
 // Prior of one component in sampling coordinates.
 //   support [lo, hi] (UNIFORM, LOG_UNIFORM), u > 0 (GAMMA), all (NORMAL)
@@ -41,8 +43,13 @@ struct JobDev {
     int n, n_pad;
     double x_ref;          // centring offset of centre coordinates
     double t_scale, t_off; // Chebyshev coordinate t = x * t_scale + t_off (raw x)
-    // model (family: kernel family; wprec: Gaussian width given as precision b)
+    // model (family: kernel family; wprec: Gaussian width given as precision b;
+    // bg_kind: SMC_BG_*; noise: SMC_NOISE_*, variance nv0 f + nv1 f^2 + nv2 with
+    // nv = squares of noise_par (FP32 and FP64 copies); full: coupled-grid kernel)
     int family, K, p, nbg, d, wprec;
+    int bg_kind, noise, full;
+    float nv0, nv1, nv2;
+    double nd0, nd1, nd2;
     // tile of the Metropolis kernel (points per lane J, warps per chain G)
     int J, G;
     // particles

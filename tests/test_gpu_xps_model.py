@@ -1,0 +1,128 @@
+"""The App. E XPS likelihood on the GPU: Shirley background (the running
+integral of the peak signal) and the variance that follows the model,
+v = s0^2 f + s1^2 f^2 + s2^2, E = sum [1/2 ln(2 pi v) + 1/2 (y - f)^2 / v];
+also each of the two alone (Shirley with known sigma, model variance without
+background).  They run in the coupled-grid Metropolis kernel (k_mh_full.cuh)
+and in the coupled branches of the energy kernels.
+
+Against the FP64 oracle on the same seeded inputs: FP64 energies relative
+1e-12, FP64 Metropolis replays (accept counts equal, states to 1e-9), FP64 full
+runs (log Z to 1e-7); FP32 energies within 2e-5 (|E| + N), FP32 runs as an
+estimator over seeds (max(0.05, 3 SE))."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_03271_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_03271_b300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _variants(n=840, seed=1, K=7):
+    full = W.xps_shirley(seed, n=n, k_min=K, k_max=K)
+    # Shirley with known sigma (the noise sd of the truth)
+    t = full.truth
+    nat = [v for k in range(len(t["mu"])) for v in (t["A"][k], t["mu"][k], t["hwhm"][k], t["eta"][k])]
+    f = oracle.model_vec(W.PSEUDO_VOIGT, len(t["mu"]), W.BG_SHIRLEY, 0, nat + [t["a"], t["b"]], full.x)
+    known = W.Spectrum(full.x, full.y, np.sqrt(f + (0.01 * f) ** 2), W.PSEUDO_VOIGT, K, K, W.BG_SHIRLEY,
+                       0, full.priors, truth=t, name="shirley-known")
+    # model variance, no background
+    nobg = W.Spectrum(full.x, full.y - np.linspace(full.y[0], full.y[-1], n) * 0.9, full.sigma,
+                      W.PSEUDO_VOIGT, K, K, W.BG_NONE, 0,
+                      W.Priors(amp=full.priors.amp, centre=full.priors.centre, width=full.priors.width),
+                      truth={}, name="model-nobg", noise=W.NOISE_MODEL, noise_par=(1.0, 0.01, 2.0))
+    return [full, known, nobg]
+
+
+@pytest.mark.parametrize("which", range(3))
+def test_energies_fp64_and_fp32(ctx, which):
+    spec = _variants()[which]
+    K = spec.k_min
+    opts = W.Options(particles=256, seed=5)
+    u, E_or = oracle.init_particles(spec, K, opts, 256)
+    nat64, E64 = ctx.prior(spec, K, opts, 256, precision=1)
+    np.testing.assert_allclose(nat64, u, rtol=1e-12, atol=1e-9)
+    fin = np.isfinite(E_or)
+    assert np.array_equal(fin, np.isfinite(E64))
+    np.testing.assert_allclose(E64[fin], E_or[fin], rtol=1e-12)
+    E32 = ctx.energy(spec, K, opts, u, precision=0)
+    assert np.all(np.abs(E32[fin] - E_or[fin]) <= 2e-5 * (np.abs(E_or[fin]) + spec.n))
+    # at the truth: energies of order N/2 + sum 1/2 ln(2 pi v)
+    if which == 0:
+        t = spec.truth
+        nat = [v for k in range(7) for v in (t["A"][k], t["mu"][k], t["hwhm"][k], t["eta"][k])] + [t["a"], t["b"]]
+        e_or = oracle.energy_spec(spec, 7, nat)
+        e_gpu = ctx.energy(spec, 7, opts, np.array([nat]), precision=1)[0]
+        assert e_gpu == pytest.approx(e_or, rel=1e-12)
+        e32 = ctx.energy(spec, 7, opts, np.array([nat]), precision=0)[0]
+        assert abs(e32 - e_or) <= 2e-5 * (abs(e_or) + spec.n)
+
+
+@pytest.mark.parametrize("which,beta", [(0, 1e-3), (1, 1e-2), (2, 0.05)])
+def test_mh_stage_replay_and_tracking(ctx, which, beta):
+    spec = _variants(n=300, seed=2, K=2)[which]
+    K = 2
+    opts = W.Options(particles=64, sweeps=3, seed=9)
+    u, E = oracle.init_particles(spec, K, opts, 64)
+    ok = np.isfinite(E)
+    u, E = u[ok][:48], E[ok][:48]
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, beta, 4)
+    nat_g, E_g, acc_g, prop_g = ctx.mh_stage(spec, K, opts, u, E, step, beta, 4, precision=1)
+    np.testing.assert_array_equal(prop_g, prop_or)
+    np.testing.assert_array_equal(acc_g, acc_or)
+    np.testing.assert_allclose(nat_g, u_or, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(E_g, E_or, rtol=1e-9)
+    # FP32 coupled kernel on the same streams
+    nat32, E32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u, E, step, beta, 4, precision=0)
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+def test_full_run_fp64_replays_oracle(ctx):
+    spec = W.xps_shirley(3, n=160, k_true=2, k_min=1, k_max=2)
+    opts = W.Options(particles=96, sweeps=3, seed=2)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=96, sweeps=3, seed=2, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7, rtol=0)
+    np.testing.assert_array_equal(r["n_stages"], [j["n_stages"] for j in ref["jobs"]])
+
+
+def test_fp32_estimator_and_selection(ctx):
+    # three true peaks (two lines and a satellite) on a Shirley background,
+    # model variance; K = 2..4: FP32 batched vs the FP64 path over seeds
+    spec = W.xps_shirley(4, n=400, k_true=3, k_min=2, k_max=4)
+    lz32, lz64 = [], []
+    for s in range(1, 9):
+        lz32.append(ctx.run(spec, W.Options(particles=1024, sweeps=6, seed=s), keep_samples=False)["log_z"])
+        lz64.append(ctx.run(spec, W.Options(particles=1024, sweeps=6, seed=s, energy_fp64=1),
+                            keep_samples=False)["log_z"])
+    lz32, lz64 = np.array(lz32), np.array(lz64)
+    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 8)
+    diff = np.abs(lz32.mean(0) - lz64.mean(0))
+    assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
+    assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0)) == 1
+
+
+def test_full_size_sampled_energies(ctx):
+    """The App. E-shaped spectrum (840 points, K = 7, T = 16384, 20 sweeps):
+    two stages of the FP32 coupled kernel, sampled final energies vs the oracle."""
+    spec = W.xps_shirley(1, k_min=7, k_max=7)
+    opts = W.Options(particles=16384, sweeps=20, seed=3, max_stages=2)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["job_status"][0] == 5 and np.isfinite(r["log_z"][0])
+    smp = r["samples"][0].astype(np.float64)
+    idx = np.random.default_rng(3).choice(16384, 32, replace=False)
+    e64 = np.array([oracle.energy_spec(spec, 7, v) for v in smp[idx]])
+    e32 = ctx.energy(spec, 7, opts, smp[idx], precision=0)
+    assert np.all(np.abs(e32 - e64) <= 2e-5 * (np.abs(e64) + spec.n))
