@@ -100,7 +100,9 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
  *   sfu_ops      SFU operations (EX2, RCP) the centre/width proposals need:
  *                N per Gaussian or Lorentzian evaluation, 2 N per pseudo-Voigt;
  *   ex2_ops / rcp_ops  the same split by operation (Gaussian: EX2,
- *                Lorentzian: RCP, pseudo-Voigt: one of each per point);
+ *                Lorentzian: RCP, pseudo-Voigt: one of each per point), plus,
+ *                with the model variance, one RCP and one LG2 (lg2_ops) per
+ *                point of every evaluated proposal (not part of sfu_ops);
  *   gather_bytes bytes the particle copy must move (read + write), per stage;
  *   resample_bytes bytes the resampler must move (q read, ancestors written);
  *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied. */
@@ -110,7 +112,7 @@ typedef struct {
     double point_evals, sfu_ops, gather_bytes, resample_bytes;
     double h2d_bytes, d2h_bytes;
     int64_t stages, jobs;
-    double ex2_ops, rcp_ops;
+    double ex2_ops, rcp_ops, lg2_ops;
 } smc_profile;
 
 int smc_profile_reset(smc_ctx *ctx, int32_t enable_events);
@@ -118,7 +120,8 @@ int smc_profile_read(smc_ctx *ctx, smc_profile *out);
 
 /* Measured throughput of one SFU (MUFU) operation on the current device:
  * op 0 = EX2 (ex2.approx.ftz.f32), op 1 = RCP (rcp.approx.ftz.f32), the two
- * transcendentals of the peak shapes.  Runs a dependency-free stream of the
+ * transcendentals of the peak shapes, op 2 = LG2 (lg2.approx.ftz.f32, the
+ * model variance's logarithm).  Runs a dependency-free stream of the
  * operation on every SM (twelve launches, about 0.25 s, on cuda_stream; the
  * best of the last four counts) and returns results per second over the whole
  * device, the SM clock the blocks saw (clock64 cycles over globaltimer

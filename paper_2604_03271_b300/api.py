@@ -60,7 +60,7 @@ class Profile(C.Structure):
                 ("sfu_ops", C.c_double), ("gather_bytes", C.c_double), ("resample_bytes", C.c_double),
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
                 ("stages", C.c_int64), ("jobs", C.c_int64),
-                ("ex2_ops", C.c_double), ("rcp_ops", C.c_double)]
+                ("ex2_ops", C.c_double), ("rcp_ops", C.c_double), ("lg2_ops", C.c_double)]
 
 
 KERNEL_CLASSES = ("reweight", "resample", "gather", "metropolis", "stage_end")
@@ -292,10 +292,11 @@ class Context:
                 "point_evals": p.point_evals, "sfu_ops": p.sfu_ops,
                 "gather_bytes": p.gather_bytes, "resample_bytes": p.resample_bytes,
                 "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes,
-                "stages": p.stages, "jobs": p.jobs, "ex2_ops": p.ex2_ops, "rcp_ops": p.rcp_ops}
+                "stages": p.stages, "jobs": p.jobs, "ex2_ops": p.ex2_ops, "rcp_ops": p.rcp_ops,
+                "lg2_ops": p.lg2_ops}
 
     def mufu_rate(self, op: int, stream=None) -> dict:
-        """Measured SFU throughput of EX2 (op 0) or RCP (op 1) on this
+        """Measured SFU throughput of EX2 (op 0), RCP (op 1) or LG2 (op 2) on this
         context's device: results per second, the SM clock seen (MHz) and
         results per clock per SM at that clock."""
         rate, per_clk, mhz = C.c_double(), C.c_double(), C.c_double()

@@ -22,6 +22,8 @@ from . import workloads as W
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiles_b300.json")
 BUCKETS = (256, 512, 1024, 2048, 4096)
 J_SET = {W.PSEUDO_VOIGT: (4, 8, 12, 16), W.GAUSS: (4, 8, 12, 16, 24, 32), W.LORENTZ: (4, 8, 12, 16, 24, 32)}
+COUPLED = 16  # family flag of the coupled-grid kernel (Shirley background, model variance)
+J_SET_COUPLED = (4, 8)
 G_SET = (1, 2, 4, 8, 16)
 
 
@@ -29,7 +31,7 @@ def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]
     """Admissible tiles for an n-point grid whose padding is within `slack` of
     the smallest one."""
     tiles = []
-    for J in J_SET[family]:
+    for J in (J_SET_COUPLED if family & COUPLED else J_SET[family]):
         for G in G_SET:
             if G == 16 and J > 8:
                 continue
@@ -43,6 +45,14 @@ def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]
 
 
 def tuning_spectrum(family: int, n: int) -> W.Spectrum:
+    if family & COUPLED:
+        s = W.xps_shirley(11, n=n, k_true=3, k_min=1, k_max=4)
+        fam = family & (COUPLED - 1)
+        if fam != W.PSEUDO_VOIGT:
+            s.family = fam
+            s.priors = W.Priors(amp=s.priors.amp, centre=s.priors.centre, width=s.priors.width,
+                                bg=s.priors.bg)
+        return s
     s = W.xps_like(11, n=n, k_true=3, k_max=4)
     if family != W.PSEUDO_VOIGT:
         s.family = family
@@ -51,7 +61,7 @@ def tuning_spectrum(family: int, n: int) -> W.Spectrum:
     return s
 
 
-def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ), buckets=BUCKETS,
+def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COUPLED), buckets=BUCKETS,
          particles: int = 8192, sweeps: int = 4, stages: int = 6, verbose: bool = True) -> List[Dict]:
     table = []
     for fam in families:

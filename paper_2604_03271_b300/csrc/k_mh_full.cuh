@@ -36,7 +36,7 @@ __device__ __forceinline__ float mhf_eterm(bool model, float f, float y, float w
     if (wt == 0.0f) return 0.0f;
     const float v = fmaf(fmaf(nv1, f, nv0), f, nv2);
     if (!(v > 0.0f)) return INFINITY;
-    return fmaf(MHF_HALF_LN2, __log2f(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
+    return fmaf(MHF_HALF_LN2, lg2_approx(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
 }
 
 // In place: v <- inclusive prefix sums of v over the group's grid (point order
@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhfBounds<J, G>::MINB))
                 atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
                 atomicAdd(&jobs[slot].sfu_ops,
                           (unsigned long long)n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
+                if (model) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
             }
         }
         __syncwarp();

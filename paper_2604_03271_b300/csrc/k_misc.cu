@@ -194,7 +194,7 @@ __device__ __forceinline__ float energy_warp_full(const JobDev &jb, const float 
             term = 0.5f * jb.wt[pt] * r * r;
         } else {
             const float v = fmaf(fmaf(jb.nv1, f, jb.nv0), f, jb.nv2);
-            term = v > 0.0f ? fmaf(0.34657359027997264f, __log2f(v), 0.91893853320467274f) + 0.5f * r * r / v
+            term = v > 0.0f ? fmaf(0.34657359027997264f, lg2_approx(v), 0.91893853320467274f) + 0.5f * r * r / v
                             : INFINITY;
         }
         const float yk = term - c;

@@ -2,8 +2,8 @@
 // kernel is built on, EX2 and RCP, measured on the device it runs on.  It is
 // the denominator of the kernel's roofline: a bound that the hardware, not a
 // data sheet, sets.  Every thread runs eight independent chains
-// v <- 2^(-v) (values stay in (0.5, 1]) or v <- 1 / (1 + v) (in (0.5, 1)), so
-// the SFU pipe, not latency, limits the rate.
+// v <- 2^(-v) (values stay in (0.5, 1]), v <- 1 / (1 + v) (in (0.5, 1)) or
+// v <- log2(3 + v) (in (1.5, 2.2)), so the SFU pipe, not latency, limits the rate.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(PR_THREADS) k_mufu(int iters, float *out, long
     const unsigned long long n0 = global_ns();
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int k = 0; k < PR_CHAINS; ++k) v[k] = OP == 0 ? ex2_approx(-v[k]) : rcp_approx(1.0f + v[k]);
+        for (int k = 0; k < PR_CHAINS; ++k)
+            v[k] = OP == 0 ? ex2_approx(-v[k]) : OP == 1 ? rcp_approx(1.0f + v[k]) : lg2_approx(3.0f + v[k]);
     }
     const long long c1 = clock64();
     const unsigned long long n1 = global_ns();
@@ -56,13 +57,12 @@ using namespace smc;
 extern "C" int smc_k_mufu_rate(int32_t op, double *ops_per_s, double *lanes_per_clk_sm, double *sm_mhz,
                                void *cuda_stream)
 {
-    if ((op != 0 && op != 1) || !ops_per_s || !lanes_per_clk_sm || !sm_mhz) return SMC_EINVAL;
+    if (op < 0 || op > 2 || !ops_per_s || !lanes_per_clk_sm || !sm_mhz) return SMC_EINVAL;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SMC_ECUDA;
-    cudaError_t e = op == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mufu<0>, PR_THREADS, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mufu<1>, PR_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mufu<0>, PR_THREADS, 0);
     if (e != cudaSuccess || per_sm < 1) return SMC_ECUDA;
     const int grid = sms * per_sm, iters = 1 << 16;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -82,8 +82,10 @@ extern "C" int smc_k_mufu_rate(int32_t op, double *ops_per_s, double *lanes_per_
             cudaEventRecord(a, s);
             if (op == 0)
                 k_mufu<0><<<grid, PR_THREADS, 0, s>>>(iters, out, cyc);
-            else
+            else if (op == 1)
                 k_mufu<1><<<grid, PR_THREADS, 0, s>>>(iters, out, cyc);
+            else
+                k_mufu<2><<<grid, PR_THREADS, 0, s>>>(iters, out, cyc);
             cudaEventRecord(b, s);
             float ms = 0.0f;
             if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||

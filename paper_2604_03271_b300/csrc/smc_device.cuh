@@ -73,7 +73,7 @@ struct JobDev {
     // cumulative algorithmic work of the Metropolis kernel: grid-point
     // evaluations of in-support proposals, and SFU operations of the
     // shape-changing (centre, width) proposals among them
-    unsigned long long point_evals, sfu_ops;
+    unsigned long long point_evals, sfu_ops, var_ops;  // var_ops: LG2 + RCP of the model variance
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +131,12 @@ __device__ __forceinline__ float rcp_approx(float a)
 {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float a)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
 }
 

@@ -160,7 +160,7 @@ def test_mufu_probe_rates_are_plausible(ctx):
     # roofline denominator: EX2 / RCP results per clock per SM between 8 and
     # 64 (the SFU lanes of an SM), at an SM clock between 0.5 and 2.1 GHz, and
     # per-second rate = per-clock rate x 148 SMs x that clock
-    for op in (0, 1):
+    for op in (0, 1, 2):
         r = ctx.mufu_rate(op)
         assert 8.0 <= r["lanes_per_clk_sm"] <= 64.0, r
         assert 500.0 <= r["sm_mhz"] <= 2100.0, r
