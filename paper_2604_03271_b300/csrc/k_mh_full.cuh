@@ -27,16 +27,16 @@ namespace smc {
 constexpr float MHF_HALF_LN_2PI = 0.91893853320467274f;  // 1/2 ln(2 pi)
 constexpr float MHF_HALF_LN2 = 0.34657359027997264f;     // 1/2 ln 2
 
-// energy term of one grid point (wt = 0: padding point, term 0)
+// energy term of one grid point (wt = 0: padding point, term 0); the model
+// variance's term is computed unconditionally and selected (no branch)
 __device__ __forceinline__ float mhf_eterm(bool model, float f, float y, float wt, float nv0,
                                            float nv1, float nv2)
 {
     const float r = y - f;
     if (!model) return 0.5f * wt * r * r;
-    if (wt == 0.0f) return 0.0f;
     const float v = fmaf(fmaf(nv1, f, nv0), f, nv2);
-    if (!(v > 0.0f)) return INFINITY;
-    return fmaf(MHF_HALF_LN2, lg2_approx(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
+    const float t = fmaf(MHF_HALF_LN2, lg2_approx(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
+    return wt == 0.0f ? 0.0f : (v > 0.0f ? t : INFINITY);
 }
 
 // In place: v <- inclusive prefix sums of v over the group's grid (point order
@@ -111,10 +111,12 @@ __device__ __forceinline__ float mhf_group_energy(GroupCtx<G> &g, const float (&
     return S - Cc;
 }
 
+// Register budget (resident blocks per SM) from a sweep on B300 with the App. E
+// spectrum: 128 registers for J = 8 in 128-thread blocks, 64 for J = 4.
 template <int J, int G>
 struct MhfBounds {
     static constexpr int NT = MhThreads<G>::NT;
-    static constexpr int MINB = (NT == 128) ? (J <= 4 ? 4 : 2) : (NT == 256 && J <= 4) ? 2 : 1;
+    static constexpr int MINB = (NT == 128) ? (J <= 4 ? 8 : 4) : (NT == 256) ? (J <= 4 ? 4 : 2) : 2;
 };
 
 template <int FAM, int J, int G>
