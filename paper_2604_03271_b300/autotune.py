@@ -46,7 +46,7 @@ def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]
 
 def tuning_spectrum(family: int, n: int) -> W.Spectrum:
     if family & COUPLED:
-        s = W.xps_shirley(11, n=n, k_true=3, k_min=1, k_max=4)
+        s = W.xps_shirley(11, n=n, k_true=7, k_min=5, k_max=8)
         fam = family & (COUPLED - 1)
         if fam != W.PSEUDO_VOIGT:
             s.family = fam

@@ -104,8 +104,8 @@ def test_fp32_estimator_and_selection(ctx):
     spec = W.xps_shirley(4, n=400, k_true=3, k_min=2, k_max=4)
     lz32, lz64 = [], []
     for s in range(1, 9):
-        lz32.append(ctx.run(spec, W.Options(particles=1024, sweeps=6, seed=s), keep_samples=False)["log_z"])
-        lz64.append(ctx.run(spec, W.Options(particles=1024, sweeps=6, seed=s, energy_fp64=1),
+        lz32.append(ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s), keep_samples=False)["log_z"])
+        lz64.append(ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s, energy_fp64=1),
                             keep_samples=False)["log_z"])
     lz32, lz64 = np.array(lz32), np.array(lz64)
     se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 8)
