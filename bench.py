@@ -42,7 +42,7 @@ SM_COUNT = 148
 # in profiles/k_mh_xps-pv-1001.md (one spectrum per step), valid only for the
 # kernel source (k_mh_impl.cuh) it was taken on; scaled by the spectra a launch
 # processes (the particle state of each spectrum's jobs is its own)
-MH_TRAFFIC = {"sha1": "82a8414cd80e", "bytes_per_spectrum": 6.374e6 + 0.392e6, "workload": "xps"}
+MH_TRAFFIC = {"sha1": "0dc5128c1393", "bytes_per_spectrum": 6.380e6 + 0.481e6, "workload": "xps"}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
