@@ -52,7 +52,10 @@ class Job(C.Structure):
                 ("particles", C.c_int64), ("ess_target", C.c_double),
                 ("sweeps", C.c_int32), ("waste_free", C.c_int32),
                 ("seed", C.c_uint64), ("max_stages", C.c_int32),
-                ("noise", C.c_int32), ("noise_par", C.c_double * 3)]
+                ("noise", C.c_int32), ("noise_par", C.c_double * 3),
+                ("ref_pos", C.POINTER(C.c_double)), ("ref_int", C.POINTER(C.c_double)),
+                ("ref_off", C.POINTER(C.c_int32)), ("n_phase", C.c_int32),
+                ("phase", Prior * 9)]
 
 
 class Out(C.Structure):
@@ -79,6 +82,13 @@ def lib():
         _lib.orc_model_vec.argtypes = [i32, i32, i32, i32, P(d), P(d), i64, P(d)]
         _lib.orc_energy_model.argtypes = [i32, i32, i32, i32, i32, P(d), P(d), P(d), P(d), P(d), i64]
         _lib.orc_energy_model.restype = d
+        _lib.orc_energy_job.argtypes = [P(Job), P(d)]
+        _lib.orc_energy_job.restype = d
+        _lib.orc_xrd_phase.argtypes = [P(d), P(d), P(d), i32, d]
+        _lib.orc_xrd_phase.restype = d
+        _lib.orc_xrd_background.argtypes = [P(d), d]
+        _lib.orc_xrd_background.restype = d
+        _lib.orc_model_vec_xrd.argtypes = [i32, i32, P(d), P(d), i64, P(d), P(d), P(C.c_int32), P(d)]
         _lib.orc_dim.argtypes = [i32, i32, i32, i32]
         _lib.orc_dim.restype = i32
         _lib.orc_prior_draw.argtypes = [Prior, C.c_uint64, u32, u32, u32]
@@ -148,11 +158,43 @@ def model_vec(family: int, K: int, bg: int, bg_degree: int, nat, x) -> np.ndarra
 
 
 def energy_spec(spec, K: int, nat) -> float:
-    """Energy of natural parameters for the spectrum's background and noise model."""
-    nat, x, y, sg = _f64(nat), _f64(spec.x), _f64(spec.y), _f64(spec.sigma)
-    par = (C.c_double * 3)(*getattr(spec, "noise_par", (0.0, 0.0, 0.0)))
-    return lib().orc_energy_model(spec.family, K, spec.bg, spec.bg_degree, getattr(spec, "noise", 0), par,
-                                  _dp(nat), _dp(x), _dp(y), _dp(sg), x.shape[0])
+    """Energy of natural parameters for the spectrum's model, background and noise."""
+    h = _JobHolder(spec, K, _ENERGY_OPTS)
+    nat = _f64(nat)
+    return lib().orc_energy_job(C.byref(h.job), _dp(nat))
+
+
+def xrd_phase(nat_phase, positions, intensities, x: float) -> float:
+    """One phase of the App. D model at x (degrees 2 theta)."""
+    q, pos, it = _f64(nat_phase), _f64(positions), _f64(intensities)
+    return lib().orc_xrd_phase(_dp(q), _dp(pos), _dp(it), pos.shape[0], float(x))
+
+
+def xrd_background(bg, x: float) -> float:
+    b = _f64(bg)
+    return lib().orc_xrd_background(_dp(b), float(x))
+
+
+def model_spec(spec, K: int, nat) -> np.ndarray:
+    """Forward model of natural parameters at every grid point of the spectrum."""
+    nat, x = _f64(nat), _f64(spec.x)
+    if spec.family != 4:
+        return model_vec(spec.family, K, spec.bg, spec.bg_degree, nat, x)
+    pos, it, off = _refs_arrays(spec)
+    f = np.zeros(x.shape[0])
+    lib().orc_model_vec_xrd(K, spec.bg, _dp(nat), _dp(x), x.shape[0], _dp(pos), _dp(it),
+                            off.ctypes.data_as(C.POINTER(C.c_int32)), _dp(f))
+    return f
+
+
+def _refs_arrays(spec):
+    refs = getattr(spec, "refs", None) or []
+    pos = _f64(np.concatenate([np.asarray(r[0], float) for r in refs]) if refs else np.zeros(1))
+    it = _f64(np.concatenate([np.asarray(r[1], float) for r in refs]) if refs else np.zeros(1))
+    off = np.zeros(len(refs) + 1, dtype=np.int32)
+    for k, r in enumerate(refs):
+        off[k + 1] = off[k] + len(r[0])
+    return pos, it, off
 
 
 def prior_draw(kind: int, p1: float, p2: float, seed: int, comp: int, particle: int, tag: int) -> float:
@@ -190,6 +232,13 @@ def resample(q: np.ndarray, M: int, u32: int) -> np.ndarray:
 # jobs
 # ----------------------------------------------------------------------------
 
+class _EnergyOpts:
+    particles, ess_target, sweeps, waste_free, seed, max_stages = 2, 0.5, 1, 0, 1, 1
+
+
+_ENERGY_OPTS = _EnergyOpts()
+
+
 class _JobHolder:
     """Keeps the numpy buffers referenced by a Job structure alive."""
 
@@ -216,6 +265,13 @@ class _JobHolder:
         j.noise = getattr(spec, "noise", 0)
         for i, v in enumerate(getattr(spec, "noise_par", (0.0, 0.0, 0.0))):
             j.noise_par[i] = v
+        if getattr(spec, "refs", None):
+            self.rp, self.ri, self.ro = _refs_arrays(spec)
+            j.ref_pos, j.ref_int = _dp(self.rp), _dp(self.ri)
+            j.ref_off = self.ro.ctypes.data_as(C.POINTER(C.c_int32))
+            j.n_phase = len(spec.refs)
+        for i, q in enumerate(getattr(spec, "phase_priors", None) or []):
+            j.phase[i] = Prior(q.kind, q.p1, q.p2)
         self.job = j
         self.d = dim(spec.family, K, spec.bg, spec.bg_degree)
 

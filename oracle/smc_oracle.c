@@ -18,6 +18,16 @@
  *     E = sum [1/2 ln(2 pi sigma_i^2) + 1/2 (y_i - f_i)^2 / sigma_i^2]
  *     (the 1/N factor and the missing 1/2 of the printed formula read as
  *     garbles of the Gaussian negative log-likelihood);
+ *   - XRD phase model (App. D): phase k contributes A_k sum_j I_kj
+ *     V(x; mu_kj + d2theta_k, Sigma_k(x), Omega_k(x), r_k) over its reference
+ *     reflections (positions mu_kj, relative intensities I_kj: inputs), with
+ *     Sigma = asym sqrt(u tan^2(x/2) - v tan(x/2) + w), Omega = asym (s sec(x/2)
+ *     + t tan(x/2)), asym = alpha for x >= mu, 1 below (x in degrees, halved
+ *     and converted to radians), V = (1 - r) exp(-4 ln2 (x - mu)^2 / Sigma^2) +
+ *     r / (1 + 4 (x - mu)^2 / Omega^2); G = 0 where the Caglioti radicand is not
+ *     positive, L = 0 where Omega is not; background a V(x; 0, sbg, sbg, rbg) + b;
+ *     Poisson likelihood with energy sum [(f - y) - y ln(f / y)] (f for y = 0,
+ *     +inf where f <= 0) and normaliser sum [y ln y - y - ln Gamma(y + 1)];
  *   - Shirley background (App. E): B_i = a + (b - a) C_i / C_N with C_i the
  *     integral of the peak signal from the first grid point to x_i by the
  *     right-end rectangle rule, C_i = sum_{1 < j <= i} P_j |x_j - x_{j-1}|,
@@ -44,9 +54,9 @@
 #define ORC_EMAXSTAGES 5
 #define ORC_ENUMERIC 8
 
-enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2, FAM_GAUSS_PREC = 3 };
-enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3, BG_SHIRLEY = 4 };
-enum { NOISE_KNOWN = 0, NOISE_MODEL = 1 };
+enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2, FAM_GAUSS_PREC = 3, FAM_XRD_PHASE = 4 };
+enum { BG_NONE = 0, BG_CONST = 1, BG_LINEAR = 2, BG_POLY = 3, BG_SHIRLEY = 4, BG_XRD_PV = 5 };
+enum { NOISE_KNOWN = 0, NOISE_MODEL = 1, NOISE_POISSON = 2 };
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
 
 typedef struct {
@@ -66,8 +76,13 @@ typedef struct {
     int32_t sweeps, waste_free;
     uint64_t seed;
     int32_t max_stages;
-    int32_t noise;        /* NOISE_KNOWN: sigma[]; NOISE_MODEL: noise_par */
+    int32_t noise;        /* NOISE_KNOWN: sigma[]; NOISE_MODEL: noise_par; NOISE_POISSON */
     double noise_par[3];  /* s0, s1, s2 of sigma_i^2 = s0^2 f + s1^2 f^2 + s2^2 */
+    /* XRD phase model: reflections ref_off[k] .. ref_off[k+1] of phase k */
+    const double *ref_pos, *ref_int;
+    const int32_t *ref_off;
+    int32_t n_phase;
+    orc_prior phase[9]; /* shared priors of (A, d2theta, alpha, r, u, v, w, s, t) */
 } orc_job;
 
 typedef struct {
@@ -133,7 +148,7 @@ static double box_muller(uint32_t a, uint32_t b)
 /* Model layout: peak k has components (A, mu, width[, eta]), then the        */
 /* background coefficients (forward model, Sec. II A, Eq. (1)).               */
 /* ------------------------------------------------------------------------- */
-static int peak_params(int family) { return family == FAM_PV ? 4 : 3; }
+static int peak_params(int family) { return family == FAM_XRD_PHASE ? 9 : (family == FAM_PV ? 4 : 3); }
 
 static int bg_params(int kind, int degree)
 {
@@ -142,6 +157,7 @@ static int bg_params(int kind, int degree)
     case BG_CONST: return 1;
     case BG_LINEAR: return 2;
     case BG_SHIRLEY: return 2;
+    case BG_XRD_PV: return 4;
     default: return degree + 1;
     }
 }
@@ -155,6 +171,7 @@ static orc_prior comp_prior(const orc_job *job, int j)
 {
     if (job->n_comp_priors > 0) return job->comp_priors[j];
     int p = peak_params(job->family);
+    if (job->family == FAM_XRD_PHASE) return j < p * job->K ? job->phase[j % p] : job->bg[j - p * job->K];
     if (j < p * job->K) {
         switch (j % p) {
         case 0: return job->amp;
@@ -209,6 +226,36 @@ double orc_peak(int family, double x, double A, double mu, double w, double eta)
     double gau = exp(-dx * dx / (2.0 * s * s));
     return A * (eta * gau + (1.0 - eta) * lor);
 }
+
+/* App. D pseudo-Voigt with separate Gaussian and Lorentzian FWHM:
+ * (1 - r) exp(-4 ln2 dx^2 / S^2) + r / (1 + 4 dx^2 / W^2); a part whose width is
+ * not positive is 0. */
+static double xrd_pv(double dx, double S, double W, double r)
+{
+    double g = S > 0.0 ? exp(-4.0 * log(2.0) * dx * dx / (S * S)) : 0.0;
+    double l = W > 0.0 ? 1.0 / (1.0 + 4.0 * dx * dx / (W * W)) : 0.0;
+    return (1.0 - r) * g + r * l;
+}
+
+/* Phase k at x (degrees): sum over its reflections (App. D Eqs. (D1)-(D6)). */
+double orc_xrd_phase(const double *q, const double *pos, const double *inten, int nref, double x)
+{
+    double A = q[0], shift = q[1], alpha = q[2], r = q[3], u = q[4], v = q[5], w = q[6], s = q[7],
+           t = q[8];
+    double th = x * M_PI / 360.0; /* x / 2 in radians */
+    double tn = tan(th), sc = 1.0 / cos(th);
+    double rad = u * tn * tn - v * tn + w;
+    double S0 = rad > 0.0 ? sqrt(rad) : 0.0, W0 = s * sc + t * tn;
+    double sum = 0.0;
+    for (int j = 0; j < nref; ++j) {
+        double mu = pos[j] + shift, dx = x - mu, asym = x >= mu ? alpha : 1.0;
+        sum += inten[j] * xrd_pv(dx, asym * S0, asym * W0, r);
+    }
+    return A * sum;
+}
+
+/* App. D background a V(x; 0, sbg, sbg, rbg) + b. */
+double orc_xrd_background(const double *bg, double x) { return bg[0] * xrd_pv(x, bg[1], bg[1], bg[2]) + bg[3]; }
 
 /* Chebyshev polynomial T_j(t) by the three-term recurrence. */
 static double chebyshev(int j, double t)
@@ -270,6 +317,21 @@ double orc_energy_nat(int family, int K, int nbg, const double *nat, const doubl
 
 /* Forward model at every grid point, f[i] (Eq. (1); App. E for the Shirley
  * background, whose value at x_i integrates the peak signal up to x_i). */
+/* Forward model of the XRD phase model at every grid point. */
+void orc_model_vec_xrd(int K, int bg_kind, const double *nat, const double *x, int64_t n,
+                       const double *ref_pos, const double *ref_int, const int32_t *ref_off,
+                       double *f)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double v = 0.0;
+        for (int k = 0; k < K; ++k)
+            v += orc_xrd_phase(nat + 9 * k, ref_pos + ref_off[k], ref_int + ref_off[k],
+                               ref_off[k + 1] - ref_off[k], x[i]);
+        if (bg_kind == BG_XRD_PV) v += orc_xrd_background(nat + 9 * K, x[i]);
+        f[i] = v;
+    }
+}
+
 void orc_model_vec(int family, int K, int bg_kind, int bg_degree, const double *nat,
                    const double *x, int64_t n, double *f)
 {
@@ -322,6 +384,48 @@ double orc_energy_model(int family, int K, int bg_kind, int bg_degree, int noise
     return e;
 }
 
+/* Poisson energy term (f - y) - y ln(f / y), f for y = 0 (App. D Eq. (D8) up
+ * to the saturated-model constant y ln y - y, which the normaliser carries). */
+static double poisson_term(double f, double y)
+{
+    if (!(f > 0.0)) return INFINITY;
+    if (y == 0.0) return f;
+    return (f - y) - y * log(f / y);
+}
+
+/* Energy of natural parameters for a job (any family, background and noise). */
+double orc_energy_job(const orc_job *job, const double *nat)
+{
+    int64_t n = job->n;
+    double *f = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!f) return NAN;
+    if (job->family == FAM_XRD_PHASE)
+        orc_model_vec_xrd(job->K, job->bg_kind, nat, job->x, n, job->ref_pos, job->ref_int,
+                          job->ref_off, f);
+    else
+        orc_model_vec(job->family, job->K, job->bg_kind, job->bg_degree, nat, job->x, n, f);
+    double e = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = job->y[i] - f[i];
+        if (job->noise == NOISE_KNOWN) {
+            e += 0.5 * (r / job->sigma[i]) * (r / job->sigma[i]);
+        } else if (job->noise == NOISE_POISSON) {
+            e += poisson_term(f[i], job->y[i]);
+        } else {
+            const double *np_ = job->noise_par;
+            double v = np_[0] * np_[0] * f[i] + np_[1] * np_[1] * f[i] * f[i] + np_[2] * np_[2];
+            if (!(v > 0.0)) {
+                e = INFINITY;
+                break;
+            }
+            e += 0.5 * log(2.0 * M_PI * v) + 0.5 * r * r / v;
+        }
+        if (!isfinite(e)) break;
+    }
+    free(f);
+    return e;
+}
+
 typedef struct {
     const orc_job *job;
     int d, p, nbg;
@@ -334,6 +438,8 @@ static double energy_u(ctx_t *c, const double *u)
 {
     for (int j = 0; j < c->d; ++j) c->nat[j] = to_natural(c->pri[j], u[j]);
     const orc_job *job = c->job;
+    if (job->family == FAM_XRD_PHASE || job->noise == NOISE_POISSON)
+        return orc_energy_job(job, c->nat);
     if (job->bg_kind == BG_SHIRLEY || job->noise == NOISE_MODEL)
         return orc_energy_model(job->family, job->K, job->bg_kind, job->bg_degree, job->noise,
                                 job->noise_par, c->nat, job->x, job->y, job->sigma, job->n);
@@ -616,7 +722,12 @@ static int validate(const orc_job *job, int d)
     if (job->n < 2 || job->K < 0 || job->particles < 2 || job->sweeps < 1) return ORC_EINVAL;
     if (!(job->ess_target > 0.0 && job->ess_target < 1.0)) return ORC_EINVAL;
     if (job->n_comp_priors > 0 && job->n_comp_priors != d) return ORC_EINVAL;
-    if (job->noise != NOISE_KNOWN && job->noise != NOISE_MODEL) return ORC_EINVAL;
+    if (job->noise != NOISE_KNOWN && job->noise != NOISE_MODEL && job->noise != NOISE_POISSON)
+        return ORC_EINVAL;
+    if (job->family == FAM_XRD_PHASE && (!job->ref_off || job->K > job->n_phase)) return ORC_EINVAL;
+    if (job->noise == NOISE_POISSON)
+        for (int64_t i = 0; i < job->n; ++i)
+            if (job->y[i] < 0.0) return ORC_EINVAL;
     for (int64_t i = 0; i < job->n; ++i) {
         if (!isfinite(job->y[i]) || !isfinite(job->x[i])) return ORC_EINVAL;
         if (job->noise == NOISE_KNOWN && (!(job->sigma[i] > 0.0) || !isfinite(job->sigma[i])))
@@ -669,6 +780,11 @@ int orc_run_job(const orc_job *job, orc_out *out)
     double lognorm = 0.0;
     if (job->noise == NOISE_KNOWN)
         for (int64_t i = 0; i < job->n; ++i) lognorm -= log(sqrt(2.0 * M_PI) * job->sigma[i]);
+    if (job->noise == NOISE_POISSON) /* log p(y | f) = -e - (y - y ln y + ln y!) */
+        for (int64_t i = 0; i < job->n; ++i) {
+            double y = job->y[i];
+            lognorm += (y > 0.0 ? y * log(y) : 0.0) - y - lgamma(y + 1.0);
+        }
 
     /* stage 0: prior draws, beta_0 = 0 (Eq. (9)) */
     for (int64_t i = 0; i < Tc; ++i) {

@@ -30,9 +30,9 @@ from typing import List, Optional
 
 import numpy as np
 
-GAUSS, LORENTZ, PSEUDO_VOIGT, GAUSS_PRECISION = 0, 1, 2, 3
-BG_NONE, BG_CONST, BG_LINEAR, BG_POLY, BG_SHIRLEY = 0, 1, 2, 3, 4
-NOISE_KNOWN, NOISE_MODEL = 0, 1
+GAUSS, LORENTZ, PSEUDO_VOIGT, GAUSS_PRECISION, XRD_PHASE = 0, 1, 2, 3, 4
+BG_NONE, BG_CONST, BG_LINEAR, BG_POLY, BG_SHIRLEY, BG_XRD_PV = 0, 1, 2, 3, 4, 5
+NOISE_KNOWN, NOISE_MODEL, NOISE_POISSON = 0, 1, 2
 UNIFORM, LOG_UNIFORM, NORMAL, GAMMA, FIXED = 0, 1, 2, 3, 4
 
 
@@ -83,6 +83,10 @@ class Spectrum:
     # s0^2 f + s1^2 f^2 + s2^2 of the model value f, App. E; sigma unused)
     noise: int = 0
     noise_par: tuple = (0.0, 0.0, 0.0)
+    # XRD phase model (App. D): per phase (reference positions, relative
+    # intensities), and the shared priors of (A, d2theta, alpha, r, u, v, w, s, t)
+    refs: Optional[list] = None
+    phase_priors: Optional[List[Prior]] = None
 
     @property
     def n(self) -> int:
@@ -108,7 +112,7 @@ def _synth_cheb(x, coeffs):
 
 
 def bg_count(bg: int, bg_degree: int) -> int:
-    return {BG_NONE: 0, BG_CONST: 1, BG_LINEAR: 2, BG_SHIRLEY: 2}.get(bg, bg_degree + 1)
+    return {BG_NONE: 0, BG_CONST: 1, BG_LINEAR: 2, BG_SHIRLEY: 2, BG_XRD_PV: 4}.get(bg, bg_degree + 1)
 
 
 def data_bg_priors(y: np.ndarray, nbg: int) -> List[Prior]:
@@ -286,6 +290,73 @@ def xps_shirley(seed: int = 1, n: int = 840, k_true: int = 7, k_min: int = 5, k_
                     truth={"K": len(mus), "A": amp.tolist(), "mu": mus, "hwhm": hwhm.tolist(),
                            "eta": eta.tolist(), "a": 0.3 * scale, "b": 0.9 * scale},
                     name=f"xps-shirley-{n}", noise=NOISE_MODEL, noise_par=(s0, s1, s2))
+
+
+# App. D stand-in reference reflections (2 theta in degrees for Cu K-alpha,
+# relative intensities) of rutile, anatase and brookite: approximate values of
+# the common powder patterns, standing in for the crystallographic references
+# the paper uses but does not list.
+XRD_REFS = [
+    ([27.45, 36.09, 39.19, 41.23, 44.05, 54.32, 56.64, 62.74, 64.04, 69.01, 69.79],
+     [1.00, 0.50, 0.08, 0.25, 0.10, 0.60, 0.20, 0.10, 0.10, 0.20, 0.12]),
+    ([25.28, 36.95, 37.80, 38.58, 48.05, 53.89, 55.06, 62.12, 62.69, 68.76, 70.31, 75.03],
+     [1.00, 0.10, 0.20, 0.10, 0.35, 0.20, 0.20, 0.04, 0.14, 0.06, 0.06, 0.10]),
+    ([25.34, 25.69, 30.81, 36.25, 37.30, 38.37, 39.21, 40.15, 42.34, 46.07, 48.01, 49.17, 52.02,
+      54.20, 55.23, 57.18, 62.06, 63.65, 64.10, 65.01],
+     [1.00, 0.80, 0.90, 0.25, 0.18, 0.04, 0.18, 0.18, 0.16, 0.16, 0.30, 0.18, 0.08, 0.20, 0.30,
+      0.13, 0.10, 0.12, 0.10, 0.12]),
+]
+# App. D table of true phase parameters (A, d2theta, alpha, r, u, v, w, s, t) and background
+XRD_TRUTH = [(10000.0, 0.035, 0.6, 0.50, 0.03, 0.03, 0.06, 0.06, 0.03),
+             (3500.0, 0.055, 0.9, 0.65, 0.1, 0.1, 0.2, 0.2, 0.1),
+             (1000.0, 0.04, 1.0, 0.75, 0.1, 0.1, 0.2, 0.2, 0.1)]
+XRD_BG_TRUTH = (60000.0, 10.0, 0.0, 100.0)
+
+
+def _synth_xrd(x, phases, refs, bg):
+    """App. D forward model, written out with numpy for data generation."""
+    th = np.radians(x / 2.0)
+    tn, sc = np.tan(th), 1.0 / np.cos(th)
+
+    def pv(dx, S, W, r):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.where(S > 0, np.exp(-4.0 * math.log(2.0) * dx * dx / np.where(S > 0, S * S, 1.0)), 0.0)
+            l = np.where(W > 0, 1.0 / (1.0 + 4.0 * dx * dx / np.where(W > 0, W * W, 1.0)), 0.0)
+        return (1.0 - r) * g + r * l
+
+    f = np.zeros_like(x)
+    for q, (pos, inten) in zip(phases, refs):
+        A, sh, al, r, u, v, w, s, t = q
+        S0 = np.sqrt(np.maximum(u * tn * tn - v * tn + w, 0.0))
+        W0 = s * sc + t * tn
+        for m, I in zip(pos, inten):
+            mu = m + sh
+            asym = np.where(x >= mu, al, 1.0)
+            f += A * I * pv(x - mu, asym * S0, asym * W0, r)
+    a, sbg, rbg, b = bg
+    return f + a * pv(x, np.full_like(x, sbg), np.full_like(x, sbg), rbg) + b
+
+
+def xrd_phase(seed: int = 1, n: int = 1000, k_min: int = 1, k_max: int = 3) -> Spectrum:
+    """The paper's XRD artificial data (App. D): rutile, anatase and brookite
+    phases (stand-in reference reflections XRD_REFS) with the printed true
+    parameters, on n points of 2 theta in [20, 80] degrees, Poisson counts; the
+    App. D priors with y_min / y_max from the data; K = number of phases."""
+    rng = np.random.default_rng(seed)
+    x = np.linspace(20.0, 80.0, n)
+    f = _synth_xrd(x, XRD_TRUTH, XRD_REFS, XRD_BG_TRUTH)
+    y = rng.poisson(f).astype(np.float64)
+    ymin, ymax = float(y.min()), float(y.max())
+    phase_pri = [Prior(GAMMA, 4.0, 4.0 / (ymax - ymin)), Prior(NORMAL, 0.0, 0.05), Prior(GAMMA, 5.0, 4.0),
+                 Prior(UNIFORM, 0.0, 1.0), Prior(GAMMA, 1.0, 10.0), Prior(GAMMA, 1.0, 10.0),
+                 Prior(GAMMA, 2.0, 20.0), Prior(GAMMA, 2.0, 20.0), Prior(GAMMA, 1.0, 10.0)]
+    bg = [Prior(GAMMA, 2.0, 1.0 / ymax), Prior(GAMMA, 2.0, 0.4), Prior(UNIFORM, 0.0, 1.0),
+          Prior(UNIFORM, ymin - math.sqrt(ymin), ymin + math.sqrt(ymin))]
+    pri = Priors(amp=phase_pri[0], centre=phase_pri[1], width=phase_pri[2], bg=bg)
+    return Spectrum(x, y, np.ones_like(x), XRD_PHASE, k_min, k_max, BG_XRD_PV, 0, pri,
+                    truth={"phases": XRD_TRUTH, "bg": XRD_BG_TRUTH, "K": 3}, name=f"xrd-phase-{n}",
+                    noise=NOISE_POISSON, refs=[(list(p), list(i)) for p, i in XRD_REFS],
+                    phase_priors=phase_pri)
 
 
 def xrd_like(seed: int = 1, n: int = 4096, k_true: int = 10, k_max: int = 12) -> Spectrum:

@@ -538,3 +538,72 @@ def test_evidence_k1_quadrature_model_variance_shirley():
     vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=s))["log_z"] for s in range(1, 6)]
     se = np.std(vals, ddof=1) / math.sqrt(len(vals))
     assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
+
+
+# --------------------------------------------------------------------------
+# XRD phase model of App. D: Caglioti widths, asymmetry, PV background, Poisson
+# --------------------------------------------------------------------------
+
+def test_xrd_phase_model_matches_independent_synthesis():
+    # the oracle's model against the numpy synthesis of the data generator
+    # (written separately), at the printed true parameters and at perturbed ones
+    spec = W.xrd_phase(1, n=700)
+    rng = np.random.default_rng(2)
+    for scale in (0.0, 0.3):
+        ph = [tuple(v * (1 + scale * rng.uniform(-1, 1)) for v in q) for q in W.XRD_TRUTH]
+        bg = tuple(v * (1 + scale * rng.uniform(-1, 1)) for v in W.XRD_BG_TRUTH)
+        nat = [v for q in ph for v in q] + list(bg)
+        f = oracle.model_spec(spec, 3, nat)
+        ref = W._synth_xrd(spec.x, ph, W.XRD_REFS, bg)
+        np.testing.assert_allclose(f, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_xrd_phase_reduces_to_gaussian_peak():
+    # one reflection, no asymmetry, u = v = 0 (constant Gaussian FWHM sqrt(w)),
+    # no Lorentzian part: a Gaussian of sd FWHM / sqrt(8 ln 2) (Eq. (C1) form)
+    fwhm, A, mu = 0.3, 5.0, 40.0
+    q = [A, 0.0, 1.0, 0.0, 0.0, 0.0, fwhm ** 2, 0.0, 0.0]
+    for x in (39.7, 39.9, 40.0, 40.05, 40.4):
+        assert oracle.xrd_phase(q, [mu], [1.0], x) == pytest.approx(
+            oracle.peak(GAUSS, x, A, mu, fwhm / math.sqrt(8 * math.log(2))), rel=1e-13, abs=1e-300)
+    # asymmetry: the right side is stretched by alpha (half height at alpha FWHM / 2)
+    q[2] = 1.7
+    assert oracle.xrd_phase(q, [mu], [1.0], mu + 1.7 * fwhm / 2) == pytest.approx(A / 2, rel=1e-12)
+    assert oracle.xrd_phase(q, [mu], [1.0], mu - fwhm / 2) == pytest.approx(A / 2, rel=1e-12)
+
+
+def test_xrd_poisson_log_z_of_fixed_background_is_exact():
+    # no phase (K = 0) and every background parameter fixed: one stage, and
+    # log Z = sum_i log Poisson(y_i; f_i) exactly
+    spec = W.xrd_phase(3, n=150, k_min=0, k_max=0)
+    bg = [500.0, 12.0, 0.3, 90.0]
+    spec.comp_priors = [W.Prior(W.FIXED, v) for v in bg]
+    f = np.array([oracle.xrd_background(bg, xi) for xi in spec.x])
+    exact = float(np.sum(stats.poisson.logpmf(spec.y, f)))
+    r = oracle.run_job(spec, 0, W.Options(particles=64, sweeps=2, seed=1))
+    assert r["n_stages"] == 1
+    assert r["log_z"] == pytest.approx(exact, rel=1e-12)
+
+
+def test_xrd_evidence_k1_quadrature_amplitude():
+    # rutile only, every parameter fixed but the intensity A ~ Gamma(4, rate):
+    # Z = int Ga(A) p(D | A) dA by adaptive quadrature
+    spec = W.xrd_phase(5, n=200, k_min=1, k_max=1)
+    q = list(W.XRD_TRUTH[0])
+    bg = list(W.XRD_BG_TRUTH)
+    rate = 4.0 / 10000.0
+    spec.comp_priors = ([W.Prior(W.GAMMA, 4.0, rate)] + [W.Prior(W.FIXED, v) for v in q[1:]]
+                        + [W.Prior(W.FIXED, v) for v in bg])
+    # data from rutile alone
+    f = W._synth_xrd(spec.x, [tuple(q)], W.XRD_REFS[:1], tuple(bg))
+    spec.y = np.random.default_rng(6).poisson(f).astype(float)
+    ll = lambda A: float(np.sum(stats.poisson.logpmf(spec.y, oracle.model_spec(spec, 1, [A] + q[1:] + bg))))
+    grid = np.linspace(8000, 12000, 401)
+    lmax = max(ll(A) for A in grid)
+    Z, _ = integrate.quad(lambda A: stats.gamma(4.0, scale=1 / rate).pdf(A) * math.exp(ll(A) - lmax),
+                          5000, 15000, points=[float(grid[np.argmax([ll(A) for A in grid])])],
+                          limit=400, epsabs=0, epsrel=1e-10)
+    exact = math.log(Z) + lmax
+    vals = [oracle.run_job(spec, 1, W.Options(particles=2000, sweeps=6, seed=s))["log_z"] for s in range(1, 6)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
