@@ -65,6 +65,11 @@ def workload(name: str, seed: int):
         # App. E: PV peaks on a Shirley background, model-dependent variance,
         # the paper's data-derived priors, K = 5..8 (the paper compares 6, 7, 8)
         return W.xps_shirley(seed), W.Options(particles=16384, sweeps=20, seed=seed)
+    if name == "xrd_phase":
+        # App. D: three TiO2-like phases (31 parameters) on 1000 points of 2 theta,
+        # Poisson counts, the paper's n = 10 sweeps; T from the paper's range
+        # (100 x {1 .. 10000})
+        return W.xrd_phase(seed, n=1000, k_min=3, k_max=3), W.Options(particles=100000, sweeps=10, seed=seed)
     if name.startswith("deconv"):
         # App. C Gaussian deconvolution at the true K, the paper's sweeps per
         # stage; particles from the paper's range (100 x {3 .. 10000})
@@ -79,12 +84,13 @@ def config_of(name: str, batch: int) -> dict:
     s, o = workload(name, 1)
     return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301",
                          "mixed": "mixed-256", "xps_shirley": "xps-shirley-model-variance-840",
+                         "xrd_phase": "xrd-phase-poisson-K3-1000",
                          "deconv3": "deconv-gauss-K3-300",
                          "deconv10": "deconv-gauss-K10-1000", "deconv30": "deconv-gauss-K30-3000"}[name],
             "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
             "sweeps": o.sweeps, "ess_target": o.ess_target, "spectra_per_step": batch,
             "family": {W.GAUSS: "gauss", W.LORENTZ: "lorentz", W.PSEUDO_VOIGT: "pseudo-voigt",
-                       W.GAUSS_PRECISION: "gauss-precision"}[s.family],
+                       W.GAUSS_PRECISION: "gauss-precision", W.XRD_PHASE: "xrd-phase"}[s.family],
             "l2": "flushed between steps (256 MiB write)"}
 
 
@@ -207,7 +213,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "xps_shirley", "deconv3", "deconv10",
+    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "deconv3", "deconv10",
                                                        "deconv30"])
     ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -418,7 +424,11 @@ def plain_sample(ctx, name: str, units_per_spec: float) -> dict:
     particle count.  Its particle-point evaluation rate, scaled by the
     workload's evaluations per spectrum, gives its spectra/s."""
     spec, o = workload(name, 1)
-    opts = W.Options(particles=o.particles, sweeps=o.sweeps, seed=1, energy_fp64=1, max_stages=1)
+    # the App. D model costs ~40 FP64 pseudo-Voigts per particle-point: a fifth
+    # of its particles keeps the sample near ten seconds (the rate per
+    # particle-point is what is scaled; 20000 threads fill the device)
+    T = min(o.particles, 20000) if name == "xrd_phase" else o.particles
+    opts = W.Options(particles=T, sweeps=o.sweeps, seed=1, energy_fp64=1, max_stages=1)
     ctx.profile_reset(events=False)
     t0 = time.perf_counter()
     ctx.run(spec, opts, keep_samples=False)

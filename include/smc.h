@@ -17,13 +17,26 @@
  *                             + (1-eta) w^2/(w^2 + (x-mu)^2)]   w: shared HWHM,
  *                                                               eta: Gaussian fraction (Eq. (E1))
  *   SMC_GAUSS_PRECISION g = A exp(-b/2 (x-mu)^2)               b: precision (App. C Eq. (C1))
+ *   SMC_XRD_PHASE      phase k of the App. D powder model, components
+ *                      (A, d2theta, alpha, r, u, v, w, s, t):
+ *                      A sum_j I_j [(1 - r) exp(-4 ln2 (x - m_j)^2 / S^2)
+ *                                   + r / (1 + 4 (x - m_j)^2 / W^2)],
+ *                      m_j = ref_j + d2theta, S = a sqrt(u T^2 - v T + w),
+ *                      W = a (s / cos(x/2) + t T), T = tan(x/2) (x in degrees
+ *                      2 theta), a = alpha for x >= m_j, 1 below; a part whose
+ *                      width is not positive is 0.  Reference positions ref_j
+ *                      and relative intensities I_j per phase are inputs
+ *                      (smc_request.ref_*); phase k of a K-phase model is the
+ *                      k-th listed phase; phases are not sorted in summaries.
  * and background b(x) = sum_j c_j T_j(t), T_j Chebyshev polynomials of the first
  * kind, t = (2x - (x_min + x_max)) / (x_max - x_min), or the Shirley background
  * of App. E (SMC_BG_SHIRLEY, components a, b):
  *   B_i = a + (b - a) C_i / C_N,  C_i = sum_{1 < j <= i} P_j |x_j - x_{j-1}|,
  * P the peak sum, points in data order: the running integral of the peak signal
  * from the first point (right-end rectangle rule), B = a at the first point and
- * b at the last (B = a if C_N = 0).
+ * b at the last (B = a if C_N = 0); or the App. D background (SMC_BG_XRD_PV,
+ * components a, s_bg, r_bg, b): a [(1 - r_bg) exp(-4 ln2 x^2 / s_bg^2)
+ * + r_bg / (1 + 4 x^2 / s_bg^2)] + b.
  * Components per job, in this order (the Metropolis sweep order): for each peak
  * (A, mu, w[, eta]), then c_0 .. c_{nbg-1}.  d = p K + nbg, p = 3 or 4.
  *
@@ -33,8 +46,11 @@
  * SMC_NOISE_MODEL (App. E), variance following the model value,
  *   sigma_i^2 = s0^2 f_i + s1^2 f_i^2 + s2^2   (noise_par = {s0, s1, s2}),
  * E = sum_i [1/2 ln(2 pi sigma_i^2) + 1/2 (y_i - f_i)^2 / sigma_i^2] (+inf where
- * sigma_i^2 <= 0), sigma unused.  Either way log Z is the log marginal likelihood
- * of Eq. (5) and F = -log Z.  The Shirley background and the model variance run
+ * sigma_i^2 <= 0), sigma unused; or SMC_NOISE_POISSON (App. D), counts y_i >= 0,
+ * E = sum_i [(f_i - y_i) - y_i ln(f_i / y_i)] (f_i for y_i = 0, +inf where
+ * f_i <= 0) with the normaliser sum_i [y_i ln y_i - y_i - ln Gamma(y_i + 1)] in
+ * log Z.  Either way log Z is the log marginal likelihood of Eq. (5) and
+ * F = -log Z.  The Shirley background and the model variance run
  * in the coupled-grid Metropolis kernel and are combined with no Chebyshev
  * background.
  *
@@ -60,6 +76,7 @@ extern "C" {
 #define SMC_MAX_BG 8     /* background coefficients (polynomial degree <= 7) */
 #define SMC_MAX_DIM 128  /* components per job: p K + nbg <= 128              */
 #define SMC_MAX_K 32     /* peaks per job                                     */
+#define SMC_MAX_REFS 64  /* reflections per phase (SMC_XRD_PHASE)            */
 
 typedef struct smc_ctx smc_ctx;
 typedef uint64_t smc_job;
@@ -76,9 +93,11 @@ enum smc_status {
     SMC_ENUMERIC = 8      /* every particle's energy is non-finite                 */
 };
 
-enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2, SMC_GAUSS_PRECISION = 3 };
-enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3, SMC_BG_SHIRLEY = 4 };
-enum smc_noise { SMC_NOISE_KNOWN = 0, SMC_NOISE_MODEL = 1 };
+enum smc_family { SMC_GAUSS = 0, SMC_LORENTZ = 1, SMC_PSEUDO_VOIGT = 2, SMC_GAUSS_PRECISION = 3,
+                  SMC_XRD_PHASE = 4 };
+enum smc_bg { SMC_BG_NONE = 0, SMC_BG_CONST = 1, SMC_BG_LINEAR = 2, SMC_BG_POLY = 3, SMC_BG_SHIRLEY = 4,
+              SMC_BG_XRD_PV = 5 };
+enum smc_noise { SMC_NOISE_KNOWN = 0, SMC_NOISE_MODEL = 1, SMC_NOISE_POISSON = 2 };
 
 /* Prior kinds.  Sampling coordinates: log v for LOG_UNIFORM, v otherwise.
  *   SMC_UNIFORM      p1 = lower, p2 = upper
@@ -101,6 +120,7 @@ typedef struct {
     smc_prior amp, centre, width, eta, bg[SMC_MAX_BG];
     const smc_prior *comp;
     int32_t n_comp;
+    smc_prior phase[9];  /* SMC_XRD_PHASE: shared priors of the nine phase components */
 } smc_priors;
 
 typedef struct {
@@ -130,6 +150,11 @@ typedef struct {
     const smc_options *opts;
     int32_t noise;                /* smc_noise (SMC_NOISE_KNOWN = 0)              */
     double noise_par[3];          /* s0, s1, s2 of SMC_NOISE_MODEL                */
+    /* SMC_XRD_PHASE: reflections ref_off[k] .. ref_off[k+1] - 1 of phase k
+     * (host arrays, copied at call time; n_phase >= k_max)                   */
+    const double *ref_pos, *ref_int;
+    const int32_t *ref_off;
+    int32_t n_phase;
 } smc_request;
 
 /* Result of one spectrum: arrays indexed by K - k_min.  Views are owned by the

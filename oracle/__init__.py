@@ -354,6 +354,8 @@ def posterior_over_k(log_z: Sequence[float]) -> np.ndarray:
 def sorted_summary(samples: np.ndarray, family: int, K: int):
     """Posterior mean and SD per component after ordering each sample's peaks by
     centre (peaks are exchangeable in Eq. (1), so labels are fixed by sorting)."""
+    if family == 4:  # App. D phases: not exchangeable, not sorted
+        return samples.mean(axis=0), samples.std(axis=0)
     p = 4 if family == 2 else 3
     s = np.array(samples, dtype=np.float64, copy=True)
     if K > 1:

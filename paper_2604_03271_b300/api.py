@@ -34,7 +34,8 @@ class Prior(C.Structure):
 
 class Priors(C.Structure):
     _fields_ = [("amp", Prior), ("centre", Prior), ("width", Prior), ("eta", Prior),
-                ("bg", Prior * 8), ("comp", C.POINTER(Prior)), ("n_comp", C.c_int32)]
+                ("bg", Prior * 8), ("comp", C.POINTER(Prior)), ("n_comp", C.c_int32),
+                ("phase", Prior * 9)]
 
 
 class CreateOpts(C.Structure):
@@ -52,7 +53,9 @@ class Request(C.Structure):
                 ("k_min", C.c_int32), ("k_max", C.c_int32), ("family", C.c_int32),
                 ("bg", C.c_int32), ("bg_degree", C.c_int32),
                 ("priors", C.POINTER(Priors)), ("opts", C.POINTER(Options)),
-                ("noise", C.c_int32), ("noise_par", C.c_double * 3)]
+                ("noise", C.c_int32), ("noise_par", C.c_double * 3),
+                ("ref_pos", C.c_void_p), ("ref_int", C.c_void_p), ("ref_off", C.c_void_p),
+                ("n_phase", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -153,6 +156,8 @@ class _Marshalled:
         self.pri.width, self.pri.eta = _c_prior(pr.width), _c_prior(pr.eta)
         for i, b in enumerate(pr.bg[:8]):
             self.pri.bg[i] = _c_prior(b)
+        for i, q in enumerate((getattr(spec, "phase_priors", None) or [])[:9]):
+            self.pri.phase[i] = _c_prior(q)
         if spec.comp_priors:
             self.comp = (Prior * len(spec.comp_priors))(*[_c_prior(p) for p in spec.comp_priors])
             self.pri.comp = self.comp
@@ -170,10 +175,18 @@ class _Marshalled:
                            spec.bg_degree, C.pointer(self.pri), C.pointer(self.opts),
                            int(getattr(spec, "noise", 0)),
                            (C.c_double * 3)(*getattr(spec, "noise_par", (0.0, 0.0, 0.0))))
+        refs = getattr(spec, "refs", None)
+        if refs:
+            self.rpos = _f64(np.concatenate([np.asarray(p, np.float64) for p, _ in refs]))
+            self.rint = _f64(np.concatenate([np.asarray(i, np.float64) for _, i in refs]))
+            self.roff = np.ascontiguousarray(np.cumsum([0] + [len(p) for p, _ in refs]), dtype=np.int32)
+            self.req.ref_pos, self.req.ref_int = self.rpos.ctypes.data, self.rint.ctypes.data
+            self.req.ref_off, self.req.n_phase = self.roff.ctypes.data, len(refs)
 
 
 def _dim(family: int, K: int, bg: int, bg_degree: int) -> int:
-    return (4 if family == W.PSEUDO_VOIGT else 3) * K + W.bg_count(bg, bg_degree)
+    p = 9 if family == W.XRD_PHASE else (4 if family == W.PSEUDO_VOIGT else 3)
+    return p * K + W.bg_count(bg, bg_degree)
 
 
 class Context:

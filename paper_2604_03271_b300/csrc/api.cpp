@@ -440,6 +440,13 @@ static smc_prior prior_of(const Request &r, int K, int j)
     return r.pri.bg[j - r.p * K];
 }
 
+// peak centres are held relative to the grid midpoint in FP32 jobs; the App. D
+// phase shift d2theta (component 1 of a phase) is an offset, not a centre
+static bool is_centre_comp(const Request &r, int K, int j)
+{
+    return r.family != SMC_XRD_PHASE && j < r.p * K && j % r.p == 1;
+}
+
 static int upload_particles(Ctx &c, const Request &r, int K, const double *nat, int64_t count,
                             double xref, void *dst_th, int64_t stride)
 {
@@ -449,14 +456,14 @@ static int upload_particles(Ctx &c, const Request &r, int K, const double *nat, 
         for (int j = 0; j < d; ++j)
             for (int64_t i = 0; i < count; ++i)
                 buf[(size_t)j * stride + i] =
-                    to_sampling(r, prior_of(r, K, j), j < r.p * K && j % r.p == 1, nat[i * d + j], xref);
+                    to_sampling(r, prior_of(r, K, j), is_centre_comp(r, K, j), nat[i * d + j], xref);
         CKS(cudaMemcpy(dst_th, buf.data(), 8 * buf.size(), cudaMemcpyHostToDevice));
     } else {
         std::vector<float> buf((size_t)d * stride, 0.0f);
         for (int j = 0; j < d; ++j)
             for (int64_t i = 0; i < count; ++i)
                 buf[(size_t)j * stride + i] = (float)to_sampling(
-                    r, prior_of(r, K, j), j < r.p * K && j % r.p == 1, nat[i * d + j], xref);
+                    r, prior_of(r, K, j), is_centre_comp(r, K, j), nat[i * d + j], xref);
         CKS(cudaMemcpy(dst_th, buf.data(), 4 * buf.size(), cudaMemcpyHostToDevice));
     }
     return SMC_OK;
@@ -477,7 +484,7 @@ static int download_particles(Ctx &c, const Request &r, int K, const void *src_t
     }
     for (int j = 0; j < d; ++j)
         for (int64_t i = 0; i < count; ++i)
-            nat[i * d + j] = to_natural(r, prior_of(r, K, j), j < r.p * K && j % r.p == 1,
+            nat[i * d + j] = to_natural(r, prior_of(r, K, j), is_centre_comp(r, K, j),
                                         buf[(size_t)j * stride + i], xref);
     return SMC_OK;
 }

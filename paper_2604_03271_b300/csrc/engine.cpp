@@ -18,7 +18,10 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? SMC_OK : (e == cudaEr
 
 static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-static int peak_params(int family) { return family == SMC_PSEUDO_VOIGT ? 4 : 3; }
+static int peak_params(int family)
+{
+    return family == SMC_XRD_PHASE ? 9 : (family == SMC_PSEUDO_VOIGT ? 4 : 3);
+}
 static int bg_params(int bg, int deg)
 {
     switch (bg) {
@@ -26,6 +29,7 @@ static int bg_params(int bg, int deg)
     case SMC_BG_CONST: return 1;
     case SMC_BG_LINEAR: return 2;
     case SMC_BG_SHIRLEY: return 2;
+    case SMC_BG_XRD_PV: return 4;
     default: return deg + 1;
     }
 }
@@ -81,7 +85,8 @@ Tile choose_tile(int family, int n)
     return best;
 }
 
-static bool prior_ok(const smc_prior &p, int role)  // role: 0 amp, 1 centre, 2 width, 3 eta, 4 bg
+// role: 0 amp, 1 centre, 2 width, 3 eta, 4 background, 5 App. D phase component
+static bool prior_ok(const smc_prior &p, int role)
 {
     if (!std::isfinite(p.p1) || (p.kind != SMC_FIXED && !std::isfinite(p.p2))) return false;
     switch (p.kind) {
@@ -101,6 +106,7 @@ static smc_prior comp_prior(const Request &r, int K, int j)
 {
     if (!r.comp.empty()) return r.comp[j];
     const int p = r.p;
+    if (r.family == SMC_XRD_PHASE) return j < p * K ? r.pri.phase[j % p] : r.pri.bg[j - p * K];
     if (j < p * K) {
         switch (j % p) {
         case 0: return r.pri.amp;
@@ -114,6 +120,7 @@ static smc_prior comp_prior(const Request &r, int K, int j)
 
 static int comp_role(const Request &r, int K, int j)
 {
+    if (r.family == SMC_XRD_PHASE) return j < r.p * K ? 5 : 4;
     if (j < r.p * K) return j % r.p;
     return 4;
 }
@@ -121,16 +128,29 @@ static int comp_role(const Request &r, int K, int j)
 int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 {
     if (!rq.priors || !rq.opts || !rq.x || !rq.y) return SMC_EINVAL;
-    if (rq.noise != SMC_NOISE_KNOWN && rq.noise != SMC_NOISE_MODEL) return SMC_EINVAL;
+    if (rq.noise != SMC_NOISE_KNOWN && rq.noise != SMC_NOISE_MODEL && rq.noise != SMC_NOISE_POISSON)
+        return SMC_EINVAL;
     if (rq.noise == SMC_NOISE_KNOWN && !rq.sigma) return SMC_EINVAL;
     if (rq.noise == SMC_NOISE_MODEL)
         for (int q = 0; q < 3; ++q)
             if (!std::isfinite(rq.noise_par[q])) return SMC_EINVAL;
     const smc_options &o = *rq.opts;
     if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
-    if (rq.family < 0 || rq.family > 3 || rq.bg < 0 || rq.bg > 4) return SMC_EINVAL;
-    const bool full = rq.bg == SMC_BG_SHIRLEY || rq.noise == SMC_NOISE_MODEL;
-    if (full && rq.bg != SMC_BG_NONE && rq.bg != SMC_BG_SHIRLEY) return SMC_EINVAL;
+    if (rq.family < 0 || rq.family > 4 || rq.bg < 0 || rq.bg > 5) return SMC_EINVAL;
+    const bool xrd = rq.family == SMC_XRD_PHASE;
+    const bool full = xrd || rq.bg == SMC_BG_SHIRLEY || rq.noise != SMC_NOISE_KNOWN;
+    if (xrd && rq.bg != SMC_BG_NONE && rq.bg != SMC_BG_XRD_PV) return SMC_EINVAL;
+    if (!xrd && full && rq.bg != SMC_BG_NONE && rq.bg != SMC_BG_SHIRLEY) return SMC_EINVAL;
+    if (xrd) {  // reflections of every candidate phase
+        if (!rq.ref_pos || !rq.ref_int || !rq.ref_off || rq.n_phase < rq.k_max || rq.ref_off[0] != 0)
+            return SMC_EINVAL;
+        for (int k = 0; k < rq.n_phase; ++k) {
+            const int nr = rq.ref_off[k + 1] - rq.ref_off[k];
+            if (nr < 1 || nr > SMC_MAX_REFS) return SMC_EINVAL;
+        }
+        for (int j = 0; j < rq.ref_off[rq.n_phase]; ++j)
+            if (!std::isfinite(rq.ref_pos[j]) || !std::isfinite(rq.ref_int[j])) return SMC_EINVAL;
+    }
     if (rq.bg == SMC_BG_POLY && (rq.bg_degree < 0 || rq.bg_degree >= SMC_MAX_BG)) return SMC_EINVAL;
     if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
     if (job_dim(rq.family, rq.k_max, rq.bg, rq.bg_degree) > SMC_MAX_DIM) return SMC_EINVAL;
@@ -152,6 +172,12 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     r->noise = rq.noise;
     for (int q = 0; q < 3; ++q) r->noise_par[q] = rq.noise == SMC_NOISE_MODEL ? rq.noise_par[q] : 0.0;
     r->full = full;
+    if (xrd) {
+        const int nref = rq.ref_off[rq.n_phase];
+        r->ref_pos.assign(rq.ref_pos, rq.ref_pos + nref);
+        r->ref_int.assign(rq.ref_int, rq.ref_int + nref);
+        r->ref_off.assign(rq.ref_off, rq.ref_off + rq.n_phase + 1);
+    }
     r->opts = o;
     r->pri = *rq.priors;
     r->fp64 = o.energy_fp64 != 0;
@@ -214,7 +240,8 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 // Device memory of a request: one arena for the spectrum and results, one per job.
 // ---------------------------------------------------------------------------
 struct SpecLayout {
-    size_t raw, x64, y64, is64, xc, wt, y, ts, scal, slots, off, pk, mean, sd, fpart, fcnt, samples, total;
+    size_t raw, x64, y64, is64, tn64, sc64, xc, wt, y, ts, sec2, rpos64, rint64, rpos, rint, roff, scal, slots, off, pk,
+        mean, sd, fpart, fcnt, samples, total;
 };
 
 static SpecLayout spec_layout(const Request &r, int64_t T_out)
@@ -227,10 +254,20 @@ static SpecLayout spec_layout(const Request &r, int64_t T_out)
     L.x64 = o;  o += al(n * 8);
     L.y64 = o;  o += al(n * 8);
     L.is64 = o; o += al(n * 8);
+    const size_t nx = r.family == SMC_XRD_PHASE ? n : 1;
+    L.tn64 = o; o += al(nx * 8);
+    L.sc64 = o; o += al(nx * 8);
     L.xc = o;   o += al(np * 4);
     L.wt = o;   o += al(np * 4);
     L.y = o;    o += al(np * 4);
     L.ts = o;   o += al(np * 4);
+    const size_t nref = std::max<size_t>(1, r.ref_pos.size());
+    L.sec2 = o; o += al(np * 4);
+    L.rpos64 = o; o += al(nref * 8);
+    L.rint64 = o; o += al(nref * 8);
+    L.rpos = o; o += al(nref * 4);
+    L.rint = o; o += al(nref * 4);
+    L.roff = o; o += al(std::max<size_t>(2, r.ref_off.size()) * 4);
     L.scal = o; o += al(sizeof(SpecScal));
     L.slots = o; o += al(nK * 4);
     L.off = o;  o += al(2 * 4);
@@ -363,9 +400,23 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
     r.sd.wt = (float *)(sa + SL.wt);
     r.sd.y = (float *)(sa + SL.y);
     r.sd.ts = (float *)(sa + SL.ts);
+    r.sd.sec2 = (float *)(sa + SL.sec2);
+    r.sd.rpos64 = (double *)(sa + SL.rpos64);
+    r.sd.rint64 = (double *)(sa + SL.rint64);
+    r.sd.rpos = (float *)(sa + SL.rpos);
+    r.sd.rint = (float *)(sa + SL.rint);
+    r.sd.roff = (int *)(sa + SL.roff);
+    r.sd.nref = (int)r.ref_pos.size();
+    if (!r.ref_pos.empty()) {
+        CK(cudaMemcpyAsync(r.sd.rpos64, r.ref_pos.data(), 8 * r.ref_pos.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(r.sd.rint64, r.ref_int.data(), 8 * r.ref_int.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(r.sd.roff, r.ref_off.data(), 4 * r.ref_off.size(), cudaMemcpyHostToDevice, c.stream));
+    }
     r.sd.x64 = (double *)(sa + SL.x64);
     r.sd.y64 = (double *)(sa + SL.y64);
     r.sd.is64 = (double *)(sa + SL.is64);
+    r.sd.tn64 = (double *)(sa + SL.tn64);
+    r.sd.sc64 = (double *)(sa + SL.sc64);
     r.sd.scal = (SpecScal *)(sa + SL.scal);
     const double *ix = r.dx, *iy = r.dy, *is = r.ds;
     if (!ix) {
@@ -379,8 +430,8 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         iy = raw + r.n;
         is = r.hs.empty() ? nullptr : raw + 2 * r.n;
     }
-    CK(launch_spec_prep(ix, iy, is, r.n, r.n_pad, r.fp64 ? 0 : 1, r.noise,
-                        r.bg == SMC_BG_SHIRLEY ? 1 : 0, r.sd, c.stream));
+    const int coord = r.family == SMC_XRD_PHASE ? 2 : (r.bg == SMC_BG_SHIRLEY ? 1 : 0);
+    CK(launch_spec_prep(ix, iy, is, r.n, r.n_pad, r.fp64 ? 0 : 1, r.noise, coord, r.sd, c.stream));
 
     std::vector<int> slots;
     for (int K = r.k_min; K <= r.k_max; ++K) {
@@ -412,9 +463,17 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.wt = r.sd.wt;
         jb.y = r.sd.y;
         jb.ts = r.sd.ts;
+        jb.sec2 = r.sd.sec2;
+        jb.rpos = r.sd.rpos;
+        jb.rint = r.sd.rint;
+        jb.rpos64 = r.sd.rpos64;
+        jb.rint64 = r.sd.rint64;
+        jb.roff = r.sd.roff;
         jb.x64 = r.sd.x64;
         jb.y64 = r.sd.y64;
         jb.is64 = r.sd.is64;
+        jb.tn64 = r.sd.tn64;
+        jb.sc64 = r.sd.sc64;
         jb.n = r.n;
         jb.n_pad = r.n_pad;
         jb.family = kernel_family(r.family);

@@ -40,6 +40,8 @@ struct Request {
     int n = 0;
     int noise = 0;                 // SMC_NOISE_*
     double noise_par[3] = {0, 0, 0};
+    std::vector<double> ref_pos, ref_int;  // App. D reflections (all phases)
+    std::vector<int32_t> ref_off;
     bool full = false;             // coupled-grid Metropolis kernel
     smc_options opts{};
     smc_priors pri{};

@@ -12,6 +12,7 @@ mh_fn mh_pick_pv(int J, int G);
 mh_fn mhf_pick_gauss(int J, int G);
 mh_fn mhf_pick_lor(int J, int G);
 mh_fn mhf_pick_pv(int J, int G);
+mh_fn mhp_pick(int J, int G);
 
 static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 
@@ -19,6 +20,7 @@ static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 static mh_fn pick(int family, int J, int G)
 {
     const int fam = family & (MH_COUPLED - 1);
+    if (fam == FAM_XRD) return (family & MH_COUPLED) ? mhp_pick(J, G) : nullptr;
     if (family & MH_COUPLED) {
         if (fam == FAM_GAUSS) return mhf_pick_gauss(J, G);
         if (fam == FAM_LORENTZ) return mhf_pick_lor(J, G);

@@ -29,14 +29,20 @@ constexpr float MHF_HALF_LN2 = 0.34657359027997264f;     // 1/2 ln 2
 
 // energy term of one grid point (wt = 0: padding point, term 0); the model
 // variance's term is computed unconditionally and selected (no branch)
-__device__ __forceinline__ float mhf_eterm(bool model, float f, float y, float wt, float nv0,
+__device__ __forceinline__ float mhf_eterm(int noise, float f, float y, float wt, float nv0,
                                            float nv1, float nv2)
 {
     const float r = y - f;
-    if (!model) return 0.5f * wt * r * r;
-    const float v = fmaf(fmaf(nv1, f, nv0), f, nv2);
-    const float t = fmaf(MHF_HALF_LN2, lg2_approx(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
-    return wt == 0.0f ? 0.0f : (v > 0.0f ? t : INFINITY);
+    if (noise == NZ_KNOWN) return 0.5f * wt * r * r;
+    float t;
+    if (noise == NZ_MODEL) {
+        const float v = fmaf(fmaf(nv1, f, nv0), f, nv2);
+        t = fmaf(MHF_HALF_LN2, lg2_approx(v), MHF_HALF_LN_2PI) + 0.5f * r * r * rcp_approx(v);
+        t = v > 0.0f ? t : INFINITY;
+    } else {
+        t = poisson_term_f(f, y);
+    }
+    return wt == 0.0f ? 0.0f : t;
 }
 
 // In place: v <- inclusive prefix sums of v over the group's grid (point order
@@ -181,7 +187,8 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhfBounds<J, G>::MINB))
         const JobDev &jb = jobs[slot];
         const int K = jb.K, d = jb.d, nbg = jb.nbg, S = jb.S, T = jb.T, n = jb.sweeps;
         const int wf = jb.waste_free, wprec = jb.wprec;
-        const bool model = jb.noise == NZ_MODEL, shir = jb.bg_kind == BGK_SHIRLEY;
+        const int model = jb.noise;
+        const bool shir = jb.bg_kind == BGK_SHIRLEY;
         const float nv0 = jb.nv0, nv1 = jb.nv1, nv2 = jb.nv2;
         const float beta = (float)jb.beta;
         const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhfBounds<J, G>::MINB))
                 atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
                 atomicAdd(&jobs[slot].sfu_ops,
                           (unsigned long long)n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
-                if (model) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
+                if (model == NZ_MODEL) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
             }
         }
         __syncwarp();

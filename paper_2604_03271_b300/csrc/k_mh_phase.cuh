@@ -1,0 +1,389 @@
+// k_mh_phase.cuh -- fused FP32 Metropolis rejuvenation (Sec. II B 4) for the
+// powder-diffraction phase model of App. D: phase k contributes
+//   A_k sum_j I_kj [(1 - r_k) G(x; m_kj, S_k(x)) + r_k L(x; m_kj, W_k(x))],
+//   m_kj = ref_kj + d2theta_k,  S = a sqrt(u T^2 - v T + w),
+//   W = a (s / cos(x/2) + t T),  T = tan(x/2),  a = alpha_k right of m_kj,
+// G = 2^(-4 (dx/S)^2), L = 1 / (1 + 4 (dx/W)^2), over the phase's reference
+// reflections, plus the background a_bg PV(x; 0, s_bg, s_bg, r_bg) + b; any
+// noise model (known sigma, model variance, Poisson).
+//
+// Scheduling and the proposal table are those of k_mh / k_mh_full.  A lane owns
+// J consecutive grid points and keeps per point y, w, the model value f, the
+// energy term e, the current phase's unit profile U (A = 1) and the
+// background's unit PV; the centred angle, tan(x/2) and 1/cos(x/2) are re-read
+// (L1-resident) whenever a profile is rebuilt.  A proposal of the phase's
+// amplitude changes f by dA U; any other phase component rebuilds the unit
+// profile U' (per reflection and point one EX2 and one RCP, per point one
+// rsqrt and one reciprocal) and changes f by A (U' - U).  Every proposal
+// recomputes the energy term at every point; dE is one group reduction.
+// Phases are not exchangeable and are never reordered.
+#pragma once
+#include "k_mh_full.cuh"
+
+namespace smc {
+
+// unit profile (A = 1) of one phase at one point, from the natural components
+// (A, d2theta, alpha, r, u, v, w, s, t) of the phase, ia = 1 / alpha
+__device__ __forceinline__ float mhp_unit(float xc, float tn, float sc, float shift, float ia, float r,
+                                          float u, float v, float w, float s, float t,
+                                          const float *__restrict__ rpos, const float *__restrict__ rint,
+                                          int j0, int j1)
+{
+    const float rad = fmaf(u * tn, tn, fmaf(-v, tn, w));
+    const float W0 = fmaf(s, sc, t * tn);
+    const bool gok = rad > 0.0f, lok = W0 > 0.0f;
+    const float rs = gok ? rsqrtf(rad) : 0.0f, iom = lok ? rcp_approx(W0) : 0.0f;
+    float U = 0.0f;
+    for (int j = j0; j < j1; ++j) {
+        const float dx = xc - (__ldg(rpos + j) + shift);
+        const float a = dx >= 0.0f ? ia : 1.0f;
+        const float zg = dx * rs * a, zl = dx * iom * a;
+        const float g = gok ? ex2_approx(-4.0f * zg * zg) : 0.0f;
+        const float l = lok ? rcp_approx(fmaf(4.0f * zl, zl, 1.0f)) : 0.0f;
+        U = fmaf(__ldg(rint + j), fmaf(r, l - g, g), U);
+    }
+    return U;
+}
+
+// unit background PV(x; 0, s_bg, s_bg, r_bg) at the absolute angle x
+__device__ __forceinline__ float mhp_bg_unit(float xabs, float sbg, float rbg)
+{
+    if (!(sbg > 0.0f)) return 0.0f;
+    const float z = xabs * rcp_approx(sbg);
+    const float g = ex2_approx(-4.0f * z * z), l = rcp_approx(fmaf(4.0f * z, z, 1.0f));
+    return fmaf(rbg, l - g, g);
+}
+
+// Register budget (resident blocks per SM): the phase kernel holds eight
+// values per point plus a phase's nine components, so J = 4 gets up to 80
+// registers and J = 8 up to 128 (no spills with the groups of four or more
+// warps that grids of about a thousand points take).
+template <int J, int G>
+struct MhpBounds {
+    static constexpr int NT = MhThreads<G>::NT;
+    static constexpr int MINB = (NT == 128) ? (J <= 4 ? 6 : 4) : (NT == 256) ? (J <= 4 ? 3 : 2) : 1;
+};
+
+template <int J, int G>
+__global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
+    k_mh_phase(JobDev *__restrict__ jobs, const int *__restrict__ slots, int nslots)
+{
+    constexpr int NT = MhThreads<G>::NT;
+    constexpr int P = 9;
+    __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
+    __shared__ int work_sh[MH_MAX_GROUPS][2];
+    __shared__ WarpComp comp_sh[NT / 32];
+    __shared__ PropTable prop_sh[NT / 32 / G][2];
+    GroupCtx<G> g;
+    g.lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    g.grp = warp / G;
+    g.gw = warp - g.grp * G;
+    g.par = 0;
+    constexpr int ngroups = (NT / 32) / G;
+    if (g.grp >= ngroups) return;
+    g.red = &red_sh[g.grp][0][0];
+    const int lane = g.lane;
+    WarpComp &cs = comp_sh[warp];
+
+    int li = 0;
+    for (;;) {
+        // ---- claim the next chain (dynamic scheduling over the bucket's jobs)
+        int slot = -1, m = 0;
+        if (g.gw == 0 && lane == 0) {
+            while (li < nslots) {
+                const int sl = slots[li];
+                JobDev &jq = jobs[sl];
+                if (jq.state == JOB_ACTIVE && jq.status == 0) {
+                    const int c = atomicAdd(&jq.next_chain, 1);
+                    if (c < jq.S) {
+                        slot = sl;
+                        m = c;
+                        break;
+                    }
+                }
+                ++li;
+            }
+            if constexpr (G > 1) {
+                work_sh[g.grp][0] = slot;
+                work_sh[g.grp][1] = m;
+            }
+        }
+        if constexpr (G == 1) {
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            m = __shfl_sync(FULL_MASK, m, 0);
+        } else {
+            named_barrier(1 + g.grp, 32 * G);
+            slot = work_sh[g.grp][0];
+            m = work_sh[g.grp][1];
+            named_barrier(1 + g.grp, 32 * G);
+        }
+        if (slot < 0) break;
+
+        const JobDev &jb = jobs[slot];
+        const int K = jb.K, d = jb.d, nbg = jb.nbg, S = jb.S, T = jb.T, n = jb.sweeps;
+        const int wf = jb.waste_free, noise = jb.noise;
+        const float nv0 = jb.nv0, nv1 = jb.nv1, nv2 = jb.nv2;
+        const float beta = (float)jb.beta, xref = (float)jb.x_ref;
+        const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
+        const unsigned long long seed = jb.seed;
+        const float *rpos = jb.rpos, *rint = jb.rint;
+        const int *roff = jb.roff;
+        const int i0 = (g.gw * 32 + lane) * J;
+
+        for (int j = lane; j < d; j += 32) {
+            const float u = jb.ths[(size_t)j * S + m];
+            cs.th[j] = u;
+            cs.nat[j] = natural_f(jb.pri[j], u);
+            cs.acc[j] = 0u;
+        }
+        __syncwarp();
+
+        const float *gx = jb.xc + i0, *gt = jb.ts + i0, *gs = jb.sec2 + i0;
+        float y[J], w[J], f[J], e[J], U[J], Un[J], en[J], Bv[J];
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            y[jj] = __ldg(jb.y + i0 + jj);
+            w[jj] = __ldg(jb.wt + i0 + jj);
+            f[jj] = 0.0f;
+        }
+        for (int k = 0; k < K; ++k) {
+            const float *q = cs.nat + P * k;
+            const int j0 = roff[k], j1 = roff[k + 1];
+            const float ia = 1.0f / q[2];
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj)
+                f[jj] = fmaf(q[0],
+                             mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), q[1], ia, q[3], q[4], q[5],
+                                      q[6], q[7], q[8], rpos, rint, j0, j1),
+                             f[jj]);
+        }
+        float ba = 0.0f, bs = 0.0f, br = 0.0f, bb = 0.0f;
+        if (nbg > 0) {
+            ba = cs.nat[P * K];
+            bs = cs.nat[P * K + 1];
+            br = cs.nat[P * K + 2];
+            bb = cs.nat[P * K + 3];
+        }
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            Bv[jj] = nbg > 0 ? mhp_bg_unit(__ldg(gx + jj) + xref, bs, br) : 0.0f;
+            f[jj] += fmaf(ba, Bv[jj], bb);
+            e[jj] = mhf_eterm(noise, f[jj], y[jj], w[jj], nv0, nv1, nv2);
+        }
+
+        unsigned n_eval = 0, n_shape = 0;
+        for (int sw = 0; sw < n; ++sw) {
+            PropTable &tb = prop_sh[g.grp][sw & 1];
+            if (g.gw == 0)
+                for (int j = lane; j < d; j += 32) {
+                    const PriorDev &pr = jb.pri[j];
+                    float thr = INFINITY, u = 0.0f, v = 0.0f;
+                    if (pr.kind != PR_FIXED) {
+                        const uint4 wv = draw(seed, (uint32_t)(sw * d + j), (uint32_t)m, stage, tag);
+                        const float z = box_muller_f(wv.x, wv.y);
+                        const float lu = logf(u01f(wv.z));
+                        const float t0 = cs.th[j];
+                        u = fmaf(jb.stepf[j], z, t0);
+                        if (in_support_f(pr, u)) {
+                            thr = lu - (log_prior_f(pr, u) - log_prior_f(pr, t0));
+                            v = pr.kind == PR_LOG_UNIFORM ? expf(u) : u;
+                        }
+                    }
+                    tb.tv[j] = make_float2(thr, v);
+                    tb.un[j] = u;
+                }
+            group_sync(g);
+
+            // ---- phase blocks; the current components are read from cs.nat
+            for (int k = 0; k < K; ++k) {
+                const int jc0 = P * k, j0 = roff[k], j1 = roff[k + 1];
+                const float *q = cs.nat + jc0;
+                {
+                    const float ia = 1.0f / q[2];
+#pragma unroll
+                    for (int jj = 0; jj < J; ++jj)
+                        U[jj] = mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), q[1], ia, q[3], q[4], q[5],
+                                         q[6], q[7], q[8], rpos, rint, j0, j1);
+                }
+#pragma unroll 1
+                for (int c = 0; c < P; ++c) {
+                    const int j = jc0 + c;
+                    const float2 q2 = tb.tv[j];
+                    const float tj = q2.x;
+                    if (tj == INFINITY) continue;
+                    const float v = q2.y;
+                    const float A = q[0];
+                    ++n_eval;
+                    float p0 = 0.0f, p1 = 0.0f;
+                    if (c == 0) {
+                        const float dA = v - A;
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) {
+                            en[jj] = mhf_eterm(noise, fmaf(dA, U[jj], f[jj]), y[jj], w[jj], nv0, nv1, nv2);
+                            if (jj & 1)
+                                p1 += en[jj] - e[jj];
+                            else
+                                p0 += en[jj] - e[jj];
+                        }
+                    } else {
+                        ++n_shape;
+                        // the phase's components with component c replaced by v
+                        const float sh = c == 1 ? v : q[1], al = c == 2 ? v : q[2], r = c == 3 ? v : q[3];
+                        const float cu = c == 4 ? v : q[4], cv = c == 5 ? v : q[5], cw = c == 6 ? v : q[6];
+                        const float cs_ = c == 7 ? v : q[7], ct = c == 8 ? v : q[8];
+                        const float ia = 1.0f / al;
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) {
+                            Un[jj] = mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), sh, ia, r, cu, cv, cw,
+                                              cs_, ct, rpos, rint, j0, j1);
+                            en[jj] = mhf_eterm(noise, fmaf(A, Un[jj] - U[jj], f[jj]), y[jj], w[jj], nv0, nv1, nv2);
+                            if (jj & 1)
+                                p1 += en[jj] - e[jj];
+                            else
+                                p0 += en[jj] - e[jj];
+                        }
+                    }
+                    const float dE = group_sum(g, p0 + p1);
+                    if (tj < -beta * dE) {
+                        if (c == 0) {
+                            const float dA = v - A;
+#pragma unroll
+                            for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(dA, U[jj], f[jj]);
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < J; ++jj) {
+                                f[jj] = fmaf(A, Un[jj] - U[jj], f[jj]);
+                                U[jj] = Un[jj];
+                            }
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < J; ++jj) e[jj] = en[jj];
+                        __syncwarp();
+                        if (lane == 0) {
+                            cs.th[j] = tb.un[j];
+                            cs.nat[j] = v;
+                            cs.acc[j] += 1u;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            // ---- background (a, s_bg, r_bg, b)
+            for (int qb = 0; qb < nbg; ++qb) {
+                const int j = P * K + qb;
+                const float2 q2 = tb.tv[j];
+                const float tj = q2.x;
+                if (tj == INFINITY) continue;
+                const float v = q2.y;
+                ++n_eval;
+                float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj) {
+                    float fn;
+                    if (qb == 0) {
+                        fn = fmaf(v - ba, Bv[jj], f[jj]);
+                    } else if (qb == 3) {
+                        fn = f[jj] + (v - bb);
+                    } else {
+                        Un[jj] = mhp_bg_unit(__ldg(gx + jj) + xref, qb == 1 ? v : bs, qb == 2 ? v : br);
+                        fn = fmaf(ba, Un[jj] - Bv[jj], f[jj]);
+                    }
+                    en[jj] = mhf_eterm(noise, fn, y[jj], w[jj], nv0, nv1, nv2);
+                    if (jj & 1)
+                        p1 += en[jj] - e[jj];
+                    else
+                        p0 += en[jj] - e[jj];
+                }
+                const float dE = group_sum(g, p0 + p1);
+                if (tj < -beta * dE) {
+#pragma unroll
+                    for (int jj = 0; jj < J; ++jj) {
+                        if (qb == 0) {
+                            f[jj] = fmaf(v - ba, Bv[jj], f[jj]);
+                        } else if (qb == 3) {
+                            f[jj] += v - bb;
+                        } else {
+                            f[jj] = fmaf(ba, Un[jj] - Bv[jj], f[jj]);
+                            Bv[jj] = Un[jj];
+                        }
+                        e[jj] = en[jj];
+                    }
+                    if (qb == 0)
+                        ba = v;
+                    else if (qb == 1)
+                        bs = v;
+                    else if (qb == 2)
+                        br = v;
+                    else
+                        bb = v;
+                    if (lane == 0) {
+                        cs.th[j] = tb.un[j];
+                        cs.nat[j] = v;
+                        cs.acc[j] += 1u;
+                    }
+                    __syncwarp();
+                }
+            }
+            if (wf) {
+                const float E = mhf_group_energy<J, G>(g, e);
+                const size_t o = (size_t)m * n + sw;
+                if (g.gw == 0) {
+                    for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
+                    if (lane == 0) jb.E[o] = E;
+                }
+            }
+        }
+        if (!wf) {
+            const float E = mhf_group_energy<J, G>(g, e);
+            if (g.gw == 0) {
+                for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
+                if (lane == 0) jb.E[m] = E;
+            }
+        }
+        if (g.gw == 0) {
+            for (int j = lane; j < d; j += 32)
+                if (jb.pri[j].kind != PR_FIXED) {
+                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)cs.acc[j]);
+                    atomicAdd(&jobs[slot].prop[j], (unsigned long long)n);
+                }
+            if (lane == 0) {
+                const unsigned long long npts = (unsigned long long)jb.n;
+                atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
+                // SFU work of the phase rebuilds: per point one rsqrt and one
+                // reciprocal plus an EX2 and an RCP per reflection (counted as
+                // a PV's EX2 + RCP per reflection and point)
+                unsigned long long nref_all = 0;
+                for (int k = 0; k < K; ++k) nref_all += (unsigned long long)(roff[k + 1] - roff[k]);
+                const unsigned long long per_shape = K > 0 ? 2ull * nref_all / (unsigned long long)K + 2ull : 0ull;
+                atomicAdd(&jobs[slot].sfu_ops, (unsigned long long)n_shape * npts * per_shape);
+                if (noise == NZ_MODEL) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int G>
+static mh_fn mhp_pick_j(int J)
+{
+    switch (J) {
+    case 4: return k_mh_phase<4, G>;
+    case 8: return k_mh_phase<8, G>;
+    default: return nullptr;
+    }
+}
+
+static mh_fn mhp_pick_tile(int J, int G)
+{
+    switch (G) {
+    case 1: return mhp_pick_j<1>(J);
+    case 2: return mhp_pick_j<2>(J);
+    case 4: return mhp_pick_j<4>(J);
+    case 8: return mhp_pick_j<8>(J);
+    case 16: return mhp_pick_j<16>(J);
+    default: return nullptr;
+    }
+}
+
+}  // namespace smc

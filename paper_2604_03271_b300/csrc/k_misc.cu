@@ -155,7 +155,8 @@ __device__ __forceinline__ float energy_warp_full(const JobDev &jb, const float 
 {
     const int lane = threadIdx.x & 31;
     const int K = jb.K, p = jb.p, n = jb.n;
-    const bool shir = jb.bg_kind == BGK_SHIRLEY, model = jb.noise == NZ_MODEL;
+    const bool shir = jb.bg_kind == BGK_SHIRLEY;
+    const int noise = jb.noise;
     const int ch = (n + 31) / 32, lo = min(n, lane * ch), hi = min(n, lo + ch);
     auto peaks = [&](int pt) {
         const float x = jb.xc[pt];
@@ -190,12 +191,80 @@ __device__ __forceinline__ float energy_warp_full(const JobDev &jb, const float 
         }
         const float r = jb.y[pt] - f;
         float term;
-        if (!model) {
+        if (noise == NZ_KNOWN) {
             term = 0.5f * jb.wt[pt] * r * r;
-        } else {
+        } else if (noise == NZ_MODEL) {
             const float v = fmaf(fmaf(jb.nv1, f, jb.nv0), f, jb.nv2);
             term = v > 0.0f ? fmaf(0.34657359027997264f, lg2_approx(v), 0.91893853320467274f) + 0.5f * r * r / v
                             : INFINITY;
+        } else {
+            term = poisson_term_f(f, jb.y[pt]);
+        }
+        const float yk = term - c;
+        const float tk = s + yk;
+        c = (tk - s) - yk;
+        s = tk;
+    }
+    c = -c;
+    warp_sum2(s, c);
+    return s + c;
+}
+
+// App. D phase model (FP32, one warp per particle): phases with Caglioti widths
+// and asymmetry from their reference reflections, the PV background, any noise
+// model; P holds natural parameters.
+__device__ __forceinline__ float xrd_phase_unit_f(float xc, float tn, float sc, const float *q,
+                                                  const float *rpos, const float *rint, int j0, int j1)
+{
+    const float rad = fmaf(q[4] * tn, tn, fmaf(-q[5], tn, q[6]));
+    const float W0 = fmaf(q[7], sc, q[8] * tn);
+    const bool gok = rad > 0.0f, lok = W0 > 0.0f;
+    const float rs = gok ? rsqrtf(rad) : 0.0f, iom = lok ? 1.0f / W0 : 0.0f, ia = 1.0f / q[2];
+    float U = 0.0f;
+    for (int j = j0; j < j1; ++j) {
+        const float dx = xc - (rpos[j] + q[1]);
+        const float a = dx >= 0.0f ? ia : 1.0f;
+        const float zg = dx * rs * a, zl = dx * iom * a;
+        const float g = gok ? ex2_approx(-4.0f * zg * zg) : 0.0f;
+        const float l = lok ? rcp_approx(fmaf(4.0f * zl, zl, 1.0f)) : 0.0f;
+        U = fmaf(rint[j], fmaf(q[3], l - g, g), U);
+    }
+    return U;
+}
+
+__device__ __forceinline__ float xrd_bg_unit_f(float xabs, float sbg, float rbg)
+{
+    if (!(sbg > 0.0f)) return 0.0f;
+    const float z = xabs / sbg;
+    const float g = ex2_approx(-4.0f * z * z), l = rcp_approx(fmaf(4.0f * z, z, 1.0f));
+    return fmaf(rbg, l - g, g);
+}
+
+__device__ __forceinline__ float energy_warp_xrd(const JobDev &jb, const float *P)
+{
+    const int lane = threadIdx.x & 31;
+    const int K = jb.K, noise = jb.noise;
+    const float xref = (float)jb.x_ref;
+    float s = 0.0f, c = 0.0f;
+    for (int pt = lane; pt < jb.n; pt += 32) {
+        const float xc = jb.xc[pt], tn = jb.ts[pt], sc = jb.sec2[pt];
+        float f = 0.0f;
+        for (int k = 0; k < K; ++k)
+            f = fmaf(P[9 * k], xrd_phase_unit_f(xc, tn, sc, P + 9 * k, jb.rpos, jb.rint, jb.roff[k], jb.roff[k + 1]), f);
+        if (jb.bg_kind == BGK_XRD_PV) {
+            const float *b = P + 9 * K;
+            f += fmaf(b[0], xrd_bg_unit_f(xc + xref, b[1], b[2]), b[3]);
+        }
+        const float r = jb.y[pt] - f;
+        float term;
+        if (noise == NZ_KNOWN) {
+            term = 0.5f * jb.wt[pt] * r * r;
+        } else if (noise == NZ_MODEL) {
+            const float v = fmaf(fmaf(jb.nv1, f, jb.nv0), f, jb.nv2);
+            term = v > 0.0f ? fmaf(0.34657359027997264f, lg2_approx(v), 0.91893853320467274f) + 0.5f * r * r / v
+                            : INFINITY;
+        } else {
+            term = poisson_term_f(f, jb.y[pt]);
         }
         const float yk = term - c;
         const float tk = s + yk;
@@ -219,14 +288,16 @@ __global__ void __launch_bounds__(256) k_energy_f32(JobDev *jobs, const int *slo
     // natural parameters of this particle, widths turned into inverse scales
     for (int j = lane; j < d; j += 32) {
         float v = natural_f(jb.pri[j], jb.th[(size_t)j * jb.T + i]);
-        if (j < p * K && j % p == 2)
+        if (jb.family != FAM_XRD && j < p * K && j % p == 2)
             v = (jb.family != FAM_GAUSS) ? 1.0f / v
                                          : (jb.wprec ? sqrtf(v) * SMC_INV_SQRT_2LN2 : SMC_INV_SQRT_2LN2 / v);
         P[j] = v;
     }
     __syncwarp();
     float e;
-    if (jb.full) {
+    if (jb.family == FAM_XRD) {
+        e = energy_warp_xrd(jb, P);
+    } else if (jb.full) {
         if (jb.family == FAM_GAUSS)
             e = energy_warp_full<FAM_GAUSS>(jb, P);
         else if (jb.family == FAM_LORENTZ)
@@ -426,7 +497,9 @@ __global__ void k_finalize(JobDev *jobs, const int *slots, int split, double *me
     extern __shared__ __align__(16) unsigned char fin_sh[];
     const int a = blockIdx.x / split, sp = blockIdx.x - a * split;
     const JobDev &jb = jobs[slots[a]];
-    const int T = jb.T, d = jb.d, K = jb.K, p = jb.p, NT = blockDim.x, tid = threadIdx.x;
+    // App. D phases are not exchangeable (each has its own reflections): no sorting
+    const int T = jb.T, d = jb.d, K = jb.family == FAM_XRD ? 0 : jb.K, p = jb.p, NT = blockDim.x,
+              tid = threadIdx.x;
     double *acc1 = (double *)fin_sh;                 // [d][NT]
     double *acc2 = acc1 + (size_t)d * NT;            // [d][NT]
     double *shift = acc2 + (size_t)d * NT;           // [d]

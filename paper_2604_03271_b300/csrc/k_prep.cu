@@ -18,7 +18,7 @@ namespace smc {
 
 __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const double *y,
                                                     const double *sg, int n, int n_pad,
-                                                    int centre, int noise, int shirley, SpecDev sd)
+                                                    int centre, int noise, int coord, SpecDev sd)
 {
     __shared__ double r0[32], r1[32], r2[32];
     __shared__ double s_lo, s_hi;
@@ -33,6 +33,9 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
             const double si = sg[i];
             if (!isfinite(si) || !(si > 0.0)) bad = 1;
             ln -= log(sqrt(2.0 * 3.141592653589793) * si);
+        } else if (noise == NZ_POISSON) {
+            if (!(yi >= 0.0)) bad = 1;
+            ln += (yi > 0.0 ? yi * log(yi) : 0.0) - yi - lgamma(yi + 1.0);
         }
         lo = fmin(lo, xi);
         hi = fmax(hi, xi);
@@ -76,11 +79,27 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
             sd.xc[i] = (float)(xi - xref);
             sd.wt[i] = noise == NZ_KNOWN ? (float)(1.0 / (sg[i] * sg[i])) : 1.0f;
             sd.y[i] = (float)y[i];
-            sd.ts[i] = shirley ? (i > 0 ? (float)fabs(xi - x[i - 1]) : 0.0f)
-                               : (float)((2.0 * xi - (xmin + xmax)) / (xmax - xmin));
+            if (coord == 1) {
+                sd.ts[i] = i > 0 ? (float)fabs(xi - x[i - 1]) : 0.0f;
+            } else if (coord == 2) {
+                const double th = xi * (3.141592653589793 / 360.0);
+                const double t = tan(th), c = 1.0 / cos(th);
+                sd.ts[i] = (float)t;
+                sd.sec2[i] = (float)c;
+                sd.tn64[i] = t;
+                sd.sc64[i] = c;
+            } else {
+                sd.ts[i] = (float)((2.0 * xi - (xmin + xmax)) / (xmax - xmin));
+            }
             sd.x64[i] = xi;
             sd.y64[i] = y[i];
             sd.is64[i] = noise == NZ_KNOWN ? 1.0 / sg[i] : 1.0;
+        } else if (coord == 2) {
+            sd.xc[i] = 0.0f;
+            sd.wt[i] = 0.0f;
+            sd.y[i] = 0.0f;
+            sd.ts[i] = 0.0f;
+            sd.sec2[i] = 1.0f;
         } else {
             sd.xc[i] = 0.0f;
             sd.wt[i] = 0.0f;
@@ -88,12 +107,16 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
             sd.ts[i] = 0.0f;
         }
     }
+    for (int j = tid; j < sd.nref; j += blockDim.x) {
+        sd.rpos[j] = (float)(sd.rpos64[j] - xref);
+        sd.rint[j] = (float)sd.rint64[j];
+    }
 }
 
 cudaError_t launch_spec_prep(const double *x, const double *y, const double *sg, int n, int n_pad,
-                             int centre, int noise, int shirley, const SpecDev &sd, cudaStream_t s)
+                             int centre, int noise, int coord, const SpecDev &sd, cudaStream_t s)
 {
-    k_spec_prep<<<1, 1024, 0, s>>>(x, y, sg, n, n_pad, centre, noise, shirley, sd);
+    k_spec_prep<<<1, 1024, 0, s>>>(x, y, sg, n, n_pad, centre, noise, coord, sd);
     return cudaGetLastError();
 }
 

@@ -17,11 +17,11 @@
 #define SMC_DMAX 128
 #define SMC_KMAX 32
 
-enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2 };
+enum { FAM_GAUSS = 0, FAM_LORENTZ = 1, FAM_PV = 2, FAM_XRD = 4 };  // FAM_XRD: App. D phases
 enum { PR_UNIFORM = 0, PR_LOG_UNIFORM = 1, PR_NORMAL = 2, PR_GAMMA = 3, PR_FIXED = 4 };
 enum { JOB_FREE = 0, JOB_ACTIVE = 1, JOB_DONE = 2 };
-enum { BGK_SHIRLEY = 4 };                 // smc_bg value of the Shirley background
-enum { NZ_KNOWN = 0, NZ_MODEL = 1 };      // smc_noise values
+enum { BGK_SHIRLEY = 4, BGK_XRD_PV = 5 };  // smc_bg values of the coupled backgrounds
+enum { NZ_KNOWN = 0, NZ_MODEL = 1, NZ_POISSON = 2 };  // smc_noise values
 
 // Prior of one component in sampling coordinates.
 //   support [lo, hi] (UNIFORM, LOG_UNIFORM), u > 0 (GAMMA), all (NORMAL)
@@ -40,6 +40,7 @@ struct JobDev {
     // spectrum
     const float *xc, *wt, *y, *ts;
     const double *x64, *y64, *is64;
+    const double *tn64, *sc64;  // App. D: tan(x/2), 1/cos(x/2) in FP64
     int n, n_pad;
     double x_ref;          // centring offset of centre coordinates
     double t_scale, t_off; // Chebyshev coordinate t = x * t_scale + t_off (raw x)
@@ -50,6 +51,12 @@ struct JobDev {
     int bg_kind, noise, full;
     float nv0, nv1, nv2;
     double nd0, nd1, nd2;
+    // App. D phases: per grid point tan(x/2) (in ts) and 1/cos(x/2); reflections
+    // roff[k] .. roff[k+1] - 1 of phase k: centred positions and intensities
+    // (FP32), absolute positions and intensities (FP64)
+    const float *sec2, *rpos, *rint;
+    const double *rpos64, *rint64;
+    const int *roff;
     // tile of the Metropolis kernel (points per lane J, warps per chain G)
     int J, G;
     // particles
@@ -138,6 +145,31 @@ __device__ __forceinline__ float lg2_approx(float a)
     float r;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
+}
+
+// Poisson energy term (f - y) - y ln(f / y) = y g(z), z = (f - y) / y,
+// g(z) = z - ln(1 + z): its Taylor series to z^8 for |z| < 1/8 (the dropped
+// terms are below 2^-22 of g there), z - log1p(z) otherwise; f for y = 0,
+// +inf where f <= 0
+__device__ __forceinline__ float poisson_term_f(float f, float y)
+{
+    if (!(f > 0.0f)) return INFINITY;
+    if (y == 0.0f) return f;
+    const float z = (f - y) / y;
+    float g;
+    if (fabsf(z) < 0.125f) {
+        float p = 0.125f;
+        p = fmaf(z, p, -1.0f / 7.0f);
+        p = fmaf(z, p, 1.0f / 6.0f);
+        p = fmaf(z, p, -0.2f);
+        p = fmaf(z, p, 0.25f);
+        p = fmaf(z, p, -1.0f / 3.0f);
+        p = fmaf(z, p, 0.5f);
+        g = z * z * p;
+    } else {
+        g = z - log1pf(z);
+    }
+    return y * g;
 }
 
 // 1 / sqrt(2 ln 2): exp(-v^2/2) = 2^(-(v / sqrt(2 ln 2))^2)

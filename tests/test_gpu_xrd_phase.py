@@ -1,0 +1,163 @@
+"""The App. D powder-diffraction phase model on the GPU: phases with Caglioti
+widths S = a sqrt(u T^2 - v T + w), W = a (s / cos(x/2) + t T), T = tan(x/2),
+asymmetry a = alpha right of each reflection, pseudo-Voigt (1 - r) G + r L over
+the phase's reference reflections, the PV background a_bg V(x; 0, s, s, r) + b
+and the Poisson energy sum [(f - y) - y ln(f / y)] (normaliser in log Z).  The
+FP32 path runs in k_mh_phase.cuh and the XRD branch of the energy kernel.
+
+Against the FP64 oracle on the same seeded inputs: FP64 energies relative
+1e-12, FP64 Metropolis replays (accept counts equal, states to 1e-9), FP64 full
+runs (log Z to 1e-7); FP32 energies within 2e-5 (|E| + N); FP32 runs as an
+estimator over seeds (max(0.05, 3 SE)) with the same selected K."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_03271_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TRUTH_NAT = [v for q in W.XRD_TRUTH for v in q] + list(W.XRD_BG_TRUTH)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_03271_b300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _known_sigma(spec):
+    """The same phases with the Gaussian known-sigma energy (sigma = sqrt(y + 1))."""
+    return W.Spectrum(spec.x, spec.y, np.sqrt(spec.y + 1.0), W.XRD_PHASE, spec.k_min, spec.k_max, W.BG_XRD_PV, 0,
+                      spec.priors, truth=spec.truth, name="xrd-known", noise=W.NOISE_KNOWN, refs=spec.refs,
+                      phase_priors=spec.phase_priors)
+
+
+def _no_bg(spec):
+    """The phases alone, Poisson counts of the phase signal plus 50."""
+    rng = np.random.default_rng(11)
+    sig = np.array([sum(oracle.xrd_phase(W.XRD_TRUTH[k], *spec.refs[k], xv) for k in range(3)) for xv in spec.x])
+    y = rng.poisson(sig + 50.0).astype(np.float64)
+    return W.Spectrum(spec.x, y, np.ones_like(y), W.XRD_PHASE, spec.k_min, spec.k_max, W.BG_NONE, 0,
+                      spec.priors, truth={}, name="xrd-nobg", noise=W.NOISE_POISSON, refs=spec.refs,
+                      phase_priors=spec.phase_priors)
+
+
+def _variants(n=1000, seed=1, K=3):
+    full = W.xrd_phase(seed, n=n, k_min=K, k_max=K)
+    return [full, _known_sigma(full), _no_bg(full)]
+
+
+@pytest.mark.parametrize("which", range(3))
+def test_energies_fp64_and_fp32(ctx, which):
+    spec = _variants()[which]
+    K = spec.k_min
+    opts = W.Options(particles=256, seed=5)
+    u, E_or = oracle.init_particles(spec, K, opts, 256)
+    nat64, E64 = ctx.prior(spec, K, opts, 256, precision=1)
+    np.testing.assert_allclose(nat64, u, rtol=1e-12, atol=1e-9)
+    fin = np.isfinite(E_or)
+    assert np.array_equal(fin, np.isfinite(E64))
+    np.testing.assert_allclose(E64[fin], E_or[fin], rtol=1e-12)
+    E32 = ctx.energy(spec, K, opts, u, precision=0)
+    assert np.all(np.abs(E32[fin] - E_or[fin]) <= 2e-5 * (np.abs(E_or[fin]) + spec.n))
+    if which == 0:  # at the truth: about N / 2
+        e_or = oracle.energy_spec(spec, 3, TRUTH_NAT)
+        assert 0.3 * spec.n < e_or < 0.8 * spec.n
+        e_gpu = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=1)[0]
+        assert e_gpu == pytest.approx(e_or, rel=1e-12)
+        e32 = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=0)[0]
+        assert abs(e32 - e_or) <= 2e-5 * (abs(e_or) + spec.n)
+
+
+@pytest.mark.parametrize("which,beta", [(0, 1e-3), (1, 1e-2), (2, 1e-3)])
+def test_mh_stage_replay_and_tracking(ctx, which, beta):
+    spec = _variants(n=300, seed=2, K=2)[which]
+    K = 2
+    opts = W.Options(particles=64, sweeps=3, seed=9)
+    u, E = oracle.init_particles(spec, K, opts, 64)
+    ok = np.isfinite(E)
+    u, E = u[ok][:48], E[ok][:48]
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, beta, 4)
+    nat_g, E_g, acc_g, prop_g = ctx.mh_stage(spec, K, opts, u, E, step, beta, 4, precision=1)
+    np.testing.assert_array_equal(prop_g, prop_or)
+    np.testing.assert_array_equal(acc_g, acc_or)
+    np.testing.assert_allclose(nat_g, u_or, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(E_g, E_or, rtol=1e-9)
+    assert acc_or.sum() > 0.05 * prop_or.sum()
+    # FP32 phase kernel on the same streams
+    nat32, E32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u, E, step, beta, 4, precision=0)
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+def test_full_run_fp64_replays_oracle(ctx):
+    spec = W.xrd_phase(3, n=120, k_min=1, k_max=2)
+    opts = W.Options(particles=64, sweeps=3, seed=2)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=64, sweeps=3, seed=2, energy_fp64=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7, rtol=0)
+    np.testing.assert_array_equal(r["n_stages"], [j["n_stages"] for j in ref["jobs"]])
+
+
+def test_fp32_estimator_and_selection(ctx):
+    # the three phases on 150 points, K = 2, 3 (the first K listed phases):
+    # FP32 batched runs over 8 seeds vs the plain FP64 path over 4
+    spec = W.xrd_phase(4, n=150, k_min=2, k_max=3)
+    lz32 = np.array([ctx.run(spec, W.Options(particles=192, sweeps=3, seed=s), keep_samples=False)["log_z"]
+                     for s in range(1, 9)])
+    lz64 = np.array([ctx.run(spec, W.Options(particles=192, sweeps=3, seed=s, energy_fp64=1),
+                             keep_samples=False)["log_z"] for s in range(1, 5)])
+    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 4)
+    diff = np.abs(lz32.mean(0) - lz64.mean(0))
+    assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
+    assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0)) == 1
+
+
+def test_more_phases_than_listed_is_rejected(ctx):
+    from paper_2604_03271_b300 import api
+    spec = W.xrd_phase(4, n=200, k_min=1, k_max=4)
+    with pytest.raises(api.SmcError):
+        ctx.run(spec, W.Options(particles=64, sweeps=2, seed=1))
+
+
+def test_phase_posterior_means(ctx):
+    """Phases keep their order (no sorting): the K = 3 posterior means of the
+    amplitudes lie near the truth's on the 1000-point pattern."""
+    spec = W.xrd_phase(1, n=1000, k_min=3, k_max=3)
+    r = ctx.run(spec, W.Options(particles=4096, sweeps=10, seed=7))
+    m = r["post_mean"][0]
+    A = m[[0, 9, 18]]
+    assert np.all(np.abs(A / np.array([q[0] for q in W.XRD_TRUTH]) - 1.0) < 0.2), A
+
+
+def test_full_size_sampled_energies(ctx):
+    """The App. D-shaped pattern (1000 points, K = 3, 31 parameters, T = 16384,
+    10 sweeps): two stages of the FP32 phase kernel, sampled final energies vs
+    the oracle."""
+    spec = W.xrd_phase(1, k_min=3, k_max=3)
+    opts = W.Options(particles=16384, sweeps=10, seed=3, max_stages=2)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["job_status"][0] == 5 and np.isfinite(r["log_z"][0])
+    smp = r["samples"][0].astype(np.float64)
+    idx = np.random.default_rng(3).choice(16384, 32, replace=False)
+    e64 = np.array([oracle.energy_spec(spec, 3, v) for v in smp[idx]])
+    e32 = ctx.energy(spec, 3, opts, smp[idx], precision=0)
+    assert np.all(np.abs(e32 - e64) <= 2e-5 * (np.abs(e64) + spec.n))
+
+
+def test_long_grid_at_truth(ctx):
+    """A 4000-point pattern (near the 4096 points one FP32 chain tile holds):
+    FP32 and FP64 energies at the truth."""
+    spec = W.xrd_phase(5, n=4000, k_min=3, k_max=3)
+    opts = W.Options(particles=64, seed=1)
+    e_or = oracle.energy_spec(spec, 3, TRUTH_NAT)
+    e64 = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=1)[0]
+    e32 = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=0)[0]
+    assert e64 == pytest.approx(e_or, rel=1e-12)
+    assert abs(e32 - e_or) <= 2e-5 * (abs(e_or) + spec.n)
