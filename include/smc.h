@@ -151,7 +151,9 @@ typedef struct {
     int32_t noise;                /* smc_noise (SMC_NOISE_KNOWN = 0)              */
     double noise_par[3];          /* s0, s1, s2 of SMC_NOISE_MODEL                */
     /* SMC_XRD_PHASE: reflections ref_off[k] .. ref_off[k+1] - 1 of phase k
-     * (host arrays, copied at call time; n_phase >= k_max)                   */
+     * (host arrays, copied at call time; n_phase >= k_max; 1 .. SMC_MAX_REFS
+     * reflections per phase; positions finite, intensities finite and >= 0;
+     * SMC_EINVAL otherwise)                                                  */
     const double *ref_pos, *ref_int;
     const int32_t *ref_off;
     int32_t n_phase;

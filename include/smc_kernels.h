@@ -80,7 +80,8 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
  * has at most n_max points: J points per lane (4, 8, 12, 16; also 24, 32 for
  * Gaussian/Lorentzian) and G warps per chain (1, 2, 4, 8; 16 with J <= 8),
  * 32 G J >= N.  family | SMC_TILE_COUPLED sets the tile of the coupled-grid
- * kernel (Shirley background or model variance: J = 4 or 8).
+ * kernel (Shirley background or model variance: J = 4 or 8); SMC_XRD_PHASE
+ * (always coupled) that of the phase kernel (J = 4 or 8).
  * Entries are matched in the order they were set; the first whose family
  * matches and n_max >= N wins; without a match a padding-minimising default
  * is used.  J = 0 clears the table.  Used by the autotuner. */

@@ -45,6 +45,9 @@ def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]
 
 
 def tuning_spectrum(family: int, n: int) -> W.Spectrum:
+    if family == W.XRD_PHASE | COUPLED:
+        # App. D: three phases (31 parameters), Poisson counts
+        return W.xrd_phase(11, n=n, k_min=3, k_max=3)
     if family & COUPLED:
         s = W.xps_shirley(11, n=n, k_true=7, k_min=5, k_max=8)
         fam = family & (COUPLED - 1)
@@ -61,7 +64,8 @@ def tuning_spectrum(family: int, n: int) -> W.Spectrum:
     return s
 
 
-def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COUPLED), buckets=BUCKETS,
+def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COUPLED, W.XRD_PHASE | COUPLED),
+         buckets=BUCKETS,
          particles: int = 8192, sweeps: int = 4, stages: int = 6, verbose: bool = True) -> List[Dict]:
     table = []
     for fam in families:
@@ -101,11 +105,19 @@ def load(ctx, path: Optional[str] = None) -> int:
     return len(rows)
 
 
-def main():
+def main(argv=None):
+    """Tune every family, or only the families given as arguments (their rows
+    replace those of the same family in the stored table)."""
+    import sys
     from . import api
+    fams = [int(a) for a in (sys.argv[1:] if argv is None else argv)]
     ctx = api.Context(0)
     t0 = time.time()
-    rows = tune(ctx)
+    rows = tune(ctx, families=tuple(fams)) if fams else tune(ctx)
+    if fams and os.path.exists(TABLE):
+        with open(TABLE) as fh:
+            old = [r for r in json.load(fh)["tiles"] if r["family"] not in fams]
+        rows = old + rows
     with open(TABLE, "w") as fh:
         json.dump({"device": "B300", "seconds": time.time() - t0, "tiles": rows}, fh, indent=1)
     print("wrote", TABLE)

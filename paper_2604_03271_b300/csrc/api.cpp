@@ -754,7 +754,7 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
     }
     const int coupled = family & MH_COUPLED;
     family &= ~MH_COUPLED;
-    if (family < 0 || family > 3) return SMC_EINVAL;
+    if (family < 0 || family > 4 || (family == SMC_XRD_PHASE && !coupled)) return SMC_EINVAL;
     family = kernel_family(family) | coupled;
     if (n_max < 1 || !mh_tile_supported(family, J, G) || 32L * J * G < 1) return SMC_EINVAL;
     ctx->c.tiles.push_back({family, n_max, J, G});

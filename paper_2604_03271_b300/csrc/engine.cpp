@@ -149,7 +149,8 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
             if (nr < 1 || nr > SMC_MAX_REFS) return SMC_EINVAL;
         }
         for (int j = 0; j < rq.ref_off[rq.n_phase]; ++j)
-            if (!std::isfinite(rq.ref_pos[j]) || !std::isfinite(rq.ref_int[j])) return SMC_EINVAL;
+            if (!std::isfinite(rq.ref_pos[j]) || !std::isfinite(rq.ref_int[j]) || rq.ref_int[j] < 0.0)
+                return SMC_EINVAL;
     }
     if (rq.bg == SMC_BG_POLY && (rq.bg_degree < 0 || rq.bg_degree >= SMC_MAX_BG)) return SMC_EINVAL;
     if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
@@ -240,7 +241,7 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
 // Device memory of a request: one arena for the spectrum and results, one per job.
 // ---------------------------------------------------------------------------
 struct SpecLayout {
-    size_t raw, x64, y64, is64, tn64, sc64, xc, wt, y, ts, sec2, rpos64, rint64, rpos, rint, roff, scal, slots, off, pk,
+    size_t raw, x64, y64, is64, tn64, sc64, xc, wt, y, ts, sec2, rpos64, rint64, rtab, roff, scal, slots, off, pk,
         mean, sd, fpart, fcnt, samples, total;
 };
 
@@ -265,8 +266,7 @@ static SpecLayout spec_layout(const Request &r, int64_t T_out)
     L.sec2 = o; o += al(np * 4);
     L.rpos64 = o; o += al(nref * 8);
     L.rint64 = o; o += al(nref * 8);
-    L.rpos = o; o += al(nref * 4);
-    L.rint = o; o += al(nref * 4);
+    L.rtab = o; o += al(nref * 16);
     L.roff = o; o += al(std::max<size_t>(2, r.ref_off.size()) * 4);
     L.scal = o; o += al(sizeof(SpecScal));
     L.slots = o; o += al(nK * 4);
@@ -403,8 +403,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
     r.sd.sec2 = (float *)(sa + SL.sec2);
     r.sd.rpos64 = (double *)(sa + SL.rpos64);
     r.sd.rint64 = (double *)(sa + SL.rint64);
-    r.sd.rpos = (float *)(sa + SL.rpos);
-    r.sd.rint = (float *)(sa + SL.rint);
+    r.sd.rtab = (float4 *)(sa + SL.rtab);
     r.sd.roff = (int *)(sa + SL.roff);
     r.sd.nref = (int)r.ref_pos.size();
     if (!r.ref_pos.empty()) {
@@ -464,8 +463,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.y = r.sd.y;
         jb.ts = r.sd.ts;
         jb.sec2 = r.sd.sec2;
-        jb.rpos = r.sd.rpos;
-        jb.rint = r.sd.rint;
+        jb.rtab = r.sd.rtab;
         jb.rpos64 = r.sd.rpos64;
         jb.rint64 = r.sd.rint64;
         jb.roff = r.sd.roff;

@@ -13,8 +13,8 @@
 // background's unit PV; the centred angle, tan(x/2) and 1/cos(x/2) are re-read
 // (L1-resident) whenever a profile is rebuilt.  A proposal of the phase's
 // amplitude changes f by dA U; any other phase component rebuilds the unit
-// profile U' (per reflection and point one EX2 and one RCP, per point one
-// rsqrt and one reciprocal) and changes f by A (U' - U).  Every proposal
+// profile U' (per reflection and point one EX2 and one RCP, per point two
+// reciprocals) and changes f by A (U' - U).  Every proposal
 // recomputes the energy term at every point; dE is one group reduction.
 // Phases are not exchangeable and are never reordered.
 #pragma once
@@ -22,27 +22,49 @@
 
 namespace smc {
 
-// unit profile (A = 1) of one phase at one point, from the natural components
-// (A, d2theta, alpha, r, u, v, w, s, t) of the phase, ia = 1 / alpha
-__device__ __forceinline__ float mhp_unit(float xc, float tn, float sc, float shift, float ia, float r,
-                                          float u, float v, float w, float s, float t,
-                                          const float *__restrict__ rpos, const float *__restrict__ rint,
-                                          int j0, int j1)
+// Unit profile (A = 1) of one phase at the lane's J points, from the phase's
+// natural components (A, d2theta, alpha, r, u, v, w, s, t); iam1 = 1/alpha - 1.
+// Per point: K1 = -4 / S^2 (S^2 = u T^2 - v T + w) and K2 = 4 / W^2 (0 where
+// the width is not positive); per reflection (R = centred position, I,
+// log2 I) and point: dx = x - (R.x + d2theta), q = dx scaled by 1/alpha right
+// of the reflection, I G = 2^(K1 q^2 + log2 I), L = 1 / (1 + K2 q^2):
+// one EX2 and one RCP, eight ALU operations.  The reflections are read once per
+// lane (a uniform address), outside the loop over the lane's points.
+template <int J>
+__device__ __forceinline__ void mhp_profile(float (&U)[J], const float *__restrict__ gx,
+                                            const float *__restrict__ gt, const float *__restrict__ gs,
+                                            float shift, float iam1, float r, float u, float v, float w,
+                                            float s, float t, const float4 *__restrict__ rtab, int j0, int j1)
 {
-    const float rad = fmaf(u * tn, tn, fmaf(-v, tn, w));
-    const float W0 = fmaf(s, sc, t * tn);
-    const bool gok = rad > 0.0f, lok = W0 > 0.0f;
-    const float rs = gok ? rsqrtf(rad) : 0.0f, iom = lok ? rcp_approx(W0) : 0.0f;
-    float U = 0.0f;
-    for (int j = j0; j < j1; ++j) {
-        const float dx = xc - (__ldg(rpos + j) + shift);
-        const float a = dx >= 0.0f ? ia : 1.0f;
-        const float zg = dx * rs * a, zl = dx * iom * a;
-        const float g = gok ? ex2_approx(-4.0f * zg * zg) : 0.0f;
-        const float l = lok ? rcp_approx(fmaf(4.0f * zl, zl, 1.0f)) : 0.0f;
-        U = fmaf(__ldg(rint + j), fmaf(r, l - g, g), U);
+    float xs[J], K1[J], K2[J], Ug[J], Ul[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        const float tn = __ldg(gt + jj), sc = __ldg(gs + jj);
+        const float rad = fmaf(u * tn, tn, fmaf(-v, tn, w));
+        const float W0 = fmaf(s, sc, t * tn);
+        // clamped so that q = 0 never meets an infinite factor
+        K1[jj] = rad > 0.0f ? fmaxf(-4.0f * rcp_approx(rad), -3.0e38f) : 0.0f;
+        K2[jj] = W0 > 0.0f ? fminf(4.0f * rcp_approx(W0 * W0), 3.0e38f) : 0.0f;
+        xs[jj] = __ldg(gx + jj) - shift;
+        Ug[jj] = 0.0f;
+        Ul[jj] = 0.0f;
     }
-    return U;
+    for (int j = j0; j < j1; ++j) {
+        const float4 R = __ldg(rtab + j);
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            const float dx = xs[jj] - R.x;
+            const float q = fmaf(fmaxf(dx, 0.0f), iam1, dx);
+            const float q2 = q * q;
+            Ug[jj] += ex2_approx(fmaf(q2, K1[jj], R.z));
+            Ul[jj] = fmaf(R.y, rcp_approx(fmaf(q2, K2[jj], 1.0f)), Ul[jj]);
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        const float cg = K1[jj] < 0.0f ? 1.0f - r : 0.0f, cl = K2[jj] > 0.0f ? r : 0.0f;
+        U[jj] = fmaf(cg, Ug[jj], cl * Ul[jj]);
+    }
 }
 
 // unit background PV(x; 0, s_bg, s_bg, r_bg) at the absolute angle x
@@ -127,7 +149,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
         const float beta = (float)jb.beta, xref = (float)jb.x_ref;
         const uint32_t stage = (uint32_t)(jb.stage + 1), tag = jb.tag;
         const unsigned long long seed = jb.seed;
-        const float *rpos = jb.rpos, *rint = jb.rint;
+        const float4 *rtab = jb.rtab;
         const int *roff = jb.roff;
         const int i0 = (g.gw * 32 + lane) * J;
 
@@ -149,14 +171,10 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
         }
         for (int k = 0; k < K; ++k) {
             const float *q = cs.nat + P * k;
-            const int j0 = roff[k], j1 = roff[k + 1];
-            const float ia = 1.0f / q[2];
+            mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8], rtab,
+                           roff[k], roff[k + 1]);
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj)
-                f[jj] = fmaf(q[0],
-                             mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), q[1], ia, q[3], q[4], q[5],
-                                      q[6], q[7], q[8], rpos, rint, j0, j1),
-                             f[jj]);
+            for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(q[0], U[jj], f[jj]);
         }
         float ba = 0.0f, bs = 0.0f, br = 0.0f, bb = 0.0f;
         if (nbg > 0) {
@@ -172,7 +190,8 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
             e[jj] = mhf_eterm(noise, f[jj], y[jj], w[jj], nv0, nv1, nv2);
         }
 
-        unsigned n_eval = 0, n_shape = 0;
+        unsigned n_eval = 0;
+        unsigned long long n_shape_ref = 0;  // reflections over the shape proposals
         for (int sw = 0; sw < n; ++sw) {
             PropTable &tb = prop_sh[g.grp][sw & 1];
             if (g.gw == 0)
@@ -199,13 +218,8 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
             for (int k = 0; k < K; ++k) {
                 const int jc0 = P * k, j0 = roff[k], j1 = roff[k + 1];
                 const float *q = cs.nat + jc0;
-                {
-                    const float ia = 1.0f / q[2];
-#pragma unroll
-                    for (int jj = 0; jj < J; ++jj)
-                        U[jj] = mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), q[1], ia, q[3], q[4], q[5],
-                                         q[6], q[7], q[8], rpos, rint, j0, j1);
-                }
+                mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8], rtab,
+                               j0, j1);
 #pragma unroll 1
                 for (int c = 0; c < P; ++c) {
                     const int j = jc0 + c;
@@ -227,16 +241,14 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
                                 p0 += en[jj] - e[jj];
                         }
                     } else {
-                        ++n_shape;
+                        n_shape_ref += (unsigned long long)(j1 - j0);
                         // the phase's components with component c replaced by v
                         const float sh = c == 1 ? v : q[1], al = c == 2 ? v : q[2], r = c == 3 ? v : q[3];
                         const float cu = c == 4 ? v : q[4], cv = c == 5 ? v : q[5], cw = c == 6 ? v : q[6];
                         const float cs_ = c == 7 ? v : q[7], ct = c == 8 ? v : q[8];
-                        const float ia = 1.0f / al;
+                        mhp_profile<J>(Un, gx, gt, gs, sh, 1.0f / al - 1.0f, r, cu, cv, cw, cs_, ct, rtab, j0, j1);
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
-                            Un[jj] = mhp_unit(__ldg(gx + jj), __ldg(gt + jj), __ldg(gs + jj), sh, ia, r, cu, cv, cw,
-                                              cs_, ct, rpos, rint, j0, j1);
                             en[jj] = mhf_eterm(noise, fmaf(A, Un[jj] - U[jj], f[jj]), y[jj], w[jj], nv0, nv1, nv2);
                             if (jj & 1)
                                 p1 += en[jj] - e[jj];
@@ -350,13 +362,10 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
             if (lane == 0) {
                 const unsigned long long npts = (unsigned long long)jb.n;
                 atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
-                // SFU work of the phase rebuilds: per point one rsqrt and one
-                // reciprocal plus an EX2 and an RCP per reflection (counted as
-                // a PV's EX2 + RCP per reflection and point)
-                unsigned long long nref_all = 0;
-                for (int k = 0; k < K; ++k) nref_all += (unsigned long long)(roff[k + 1] - roff[k]);
-                const unsigned long long per_shape = K > 0 ? 2ull * nref_all / (unsigned long long)K + 2ull : 0ull;
-                atomicAdd(&jobs[slot].sfu_ops, (unsigned long long)n_shape * npts * per_shape);
+                // SFU work of the proposals' profile rebuilds: an EX2 and an
+                // RCP per reflection and point (the two per-point reciprocals
+                // and the rebuild of the current profile are not counted)
+                atomicAdd(&jobs[slot].sfu_ops, 2ull * n_shape_ref * npts);
                 if (noise == NZ_MODEL) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
             }
         }

@@ -214,7 +214,7 @@ __device__ __forceinline__ float energy_warp_full(const JobDev &jb, const float 
 // and asymmetry from their reference reflections, the PV background, any noise
 // model; P holds natural parameters.
 __device__ __forceinline__ float xrd_phase_unit_f(float xc, float tn, float sc, const float *q,
-                                                  const float *rpos, const float *rint, int j0, int j1)
+                                                  const float4 *rtab, int j0, int j1)
 {
     const float rad = fmaf(q[4] * tn, tn, fmaf(-q[5], tn, q[6]));
     const float W0 = fmaf(q[7], sc, q[8] * tn);
@@ -222,12 +222,13 @@ __device__ __forceinline__ float xrd_phase_unit_f(float xc, float tn, float sc, 
     const float rs = gok ? rsqrtf(rad) : 0.0f, iom = lok ? 1.0f / W0 : 0.0f, ia = 1.0f / q[2];
     float U = 0.0f;
     for (int j = j0; j < j1; ++j) {
-        const float dx = xc - (rpos[j] + q[1]);
+        const float4 R = rtab[j];
+        const float dx = xc - (R.x + q[1]);
         const float a = dx >= 0.0f ? ia : 1.0f;
         const float zg = dx * rs * a, zl = dx * iom * a;
         const float g = gok ? ex2_approx(-4.0f * zg * zg) : 0.0f;
         const float l = lok ? rcp_approx(fmaf(4.0f * zl, zl, 1.0f)) : 0.0f;
-        U = fmaf(rint[j], fmaf(q[3], l - g, g), U);
+        U = fmaf(R.y, fmaf(q[3], l - g, g), U);
     }
     return U;
 }
@@ -250,7 +251,7 @@ __device__ __forceinline__ float energy_warp_xrd(const JobDev &jb, const float *
         const float xc = jb.xc[pt], tn = jb.ts[pt], sc = jb.sec2[pt];
         float f = 0.0f;
         for (int k = 0; k < K; ++k)
-            f = fmaf(P[9 * k], xrd_phase_unit_f(xc, tn, sc, P + 9 * k, jb.rpos, jb.rint, jb.roff[k], jb.roff[k + 1]), f);
+            f = fmaf(P[9 * k], xrd_phase_unit_f(xc, tn, sc, P + 9 * k, jb.rtab, jb.roff[k], jb.roff[k + 1]), f);
         if (jb.bg_kind == BGK_XRD_PV) {
             const float *b = P + 9 * K;
             f += fmaf(b[0], xrd_bg_unit_f(xc + xref, b[1], b[2]), b[3]);

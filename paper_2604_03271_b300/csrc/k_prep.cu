@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(1024) k_spec_prep(const double *x, const doubl
         }
     }
     for (int j = tid; j < sd.nref; j += blockDim.x) {
-        sd.rpos[j] = (float)(sd.rpos64[j] - xref);
-        sd.rint[j] = (float)sd.rint64[j];
+        const double I = sd.rint64[j];
+        sd.rtab[j] = make_float4((float)(sd.rpos64[j] - xref), (float)I, (float)log2(I), 0.0f);
     }
 }
 

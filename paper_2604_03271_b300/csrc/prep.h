@@ -18,7 +18,7 @@ struct SpecDev {
     SpecScal *scal;
     // App. D reflections: absolute (FP64, uploaded) and centred (FP32, by prep)
     double *rpos64, *rint64;
-    float *rpos, *rint;
+    float4 *rtab;
     int *roff;
     int nref;
 };
@@ -27,7 +27,7 @@ struct SpecDev {
 // NZ_POISSON: sigma not read, wt = 1, y >= 0 required, lognorm = sum [y ln y -
 // y - ln Gamma(y + 1)].  coord = 1 (Shirley): ts holds |x_i - x_{i-1}| (0 at
 // the first point); coord = 2 (App. D): ts = tan(x/2), sec2 = 1/cos(x/2) (x in
-// degrees; FP64 copies in tn64 / sc64) and the sd.nref reflections are centred into rpos / rint; otherwise
+// degrees; FP64 copies in tn64 / sc64) and the sd.nref reflections are centred into rtab = (x - x_ref, I, log2 I, 0); otherwise
 // ts is the Chebyshev coordinate.  Padding points have wt = 0 (and ts = 0).
 cudaError_t launch_spec_prep(const double *x, const double *y, const double *sg, int n, int n_pad,
                              int centre, int noise, int coord, const SpecDev &sd, cudaStream_t s);

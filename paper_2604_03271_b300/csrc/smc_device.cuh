@@ -54,7 +54,8 @@ struct JobDev {
     // App. D phases: per grid point tan(x/2) (in ts) and 1/cos(x/2); reflections
     // roff[k] .. roff[k+1] - 1 of phase k: centred positions and intensities
     // (FP32), absolute positions and intensities (FP64)
-    const float *sec2, *rpos, *rint;
+    const float *sec2;
+    const float4 *rtab;  // App. D reflections: (centred position, I, log2 I, 0)
     const double *rpos64, *rint64;
     const int *roff;
     // tile of the Metropolis kernel (points per lane J, warps per chain G)
