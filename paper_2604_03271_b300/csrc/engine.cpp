@@ -47,10 +47,13 @@ int kernel_family(int family) { return family == SMC_GAUSS_PRECISION ? SMC_GAUSS
 Tile choose_tile(int family, int n)
 {
     if (family & MH_COUPLED) {  // coupled-grid kernel: J = 8 or 4, least padding
+        // G > 16 (multiples of 8): the phase kernel's cluster-spanning chains
+        static const int Gs[] = {1,  2,  4,  8,  16, 24, 32, 40,  48,  56,  64,
+                                 72, 80, 88, 96, 104, 112, 120, 128};
         Tile best{0, 0};
         long best_pad = -1;
         for (int J : {8, 4})
-            for (int G : {1, 2, 4, 8, 16}) {
+            for (int G : Gs) {
                 if (!mh_tile_supported(family, J, G) || 32L * G * J < n) continue;
                 if (best_pad < 0 || 32L * G * J < best_pad) {
                     best = {J, G};

@@ -16,6 +16,13 @@ mh_fn mhp_pick(int J, int G);
 
 static int block_threads(int G) { return G <= 4 ? 128 : 32 * G; }
 
+// CTAs per chain: the phase kernel spreads chains of more than 16 warps over
+// a thread-block cluster of 8-warp CTAs
+static int cluster_of(int family, int G)
+{
+    return ((family & (MH_COUPLED - 1)) == FAM_XRD && G > 16) ? G / 8 : 1;
+}
+
 // family: FAM_* of the peaks, plus MH_COUPLED for the coupled-grid kernel
 static mh_fn pick(int family, int J, int G)
 {
@@ -33,10 +40,40 @@ static mh_fn pick(int family, int J, int G)
 
 bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
 
+static cudaLaunchConfig_t cluster_config(int C, int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 int mh_resident_grid(int family, int J, int G)
 {
     mh_fn f = pick(family, J, G);
     if (!f) return 0;
+    const int C = cluster_of(family, G);
+    if (C > 1) {
+        // clusters of C CTAs resident at once (every CTA of a cluster runs the
+        // same chain, so the grid holds whole clusters)
+        if (C > 8) cudaFuncSetAttribute((const void *)f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(C, C * 148, nullptr, attr);
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, (const void *)f, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            return 0;
+        }
+        return ncl * C;
+    }
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -52,6 +89,13 @@ cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, in
     if (!f) return cudaErrorInvalidValue;
     if (nslots <= 0) return cudaSuccess;
     if (grid <= 0) grid = mh_resident_grid(family, J, G);
+    const int C = cluster_of(family, G);
+    if (C > 1) {
+        if (grid < C || grid % C != 0) return cudaErrorInvalidConfiguration;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(C, grid, s, attr);
+        return cudaLaunchKernelEx(&cfg, f, jobs, slots, nslots);
+    }
     f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots);
     return cudaGetLastError();
 }

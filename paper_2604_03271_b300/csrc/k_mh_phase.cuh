@@ -17,6 +17,15 @@
 // reciprocals) and changes f by A (U' - U).  Every proposal
 // recomputes the energy term at every point; dE is one group reduction.
 // Phases are not exchangeable and are never reordered.
+//
+// Grids longer than one block's tile (32 G J points) run with CL = true: a
+// chain spans a thread-block cluster of C CTAs of G = 8 warps (C = 2..16, the
+// tile's warps per chain are 8 C), CTA r owning points [r, r + 1) x 256 J.  Every
+// CTA draws the same proposals from the same Philox counters; per proposal each
+// warp pushes its partial dE into every CTA's shared memory (distributed shared
+// memory), one cluster barrier follows, and every CTA sums the 8 C partials in
+// the same order, so all CTAs take the same decisions.  The first CTA claims the
+// chains and alone writes the chain's results.
 #pragma once
 #include "k_mh_full.cuh"
 
@@ -80,22 +89,120 @@ __device__ __forceinline__ float mhp_bg_unit(float xabs, float sbg, float rbg)
 // values per point plus a phase's nine components, so J = 4 gets up to 80
 // registers and J = 8 up to 128 (no spills with the groups of four or more
 // warps that grids of about a thousand points take).
-template <int J, int G>
+constexpr int MHP_MAX_CL = 16;  // CTAs per cluster at most (non-portable above 8)
+constexpr int MHP_CL_WARPS = 8;
+
+__device__ __forceinline__ unsigned mhp_cl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned mhp_cl_size()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster; orders the shared::cluster stores
+// issued before it with the reads after it
+__device__ __forceinline__ void mhp_cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// store v at the address of `local` in the shared memory of CTA `rank`
+__device__ __forceinline__ void mhp_cl_store(const void *local, unsigned rank, float v)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+}
+__device__ __forceinline__ void mhp_cl_store_i(const void *local, unsigned rank, int v)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+// Cluster-wide sum of one value per warp (v: the warp's total, equal in its
+// lanes); every thread of every CTA returns the same sum (CTA order, then warp
+// order).  xch: [2][MHP_MAX_CL * G] in this CTA's shared memory.
+template <int G>
+__device__ __forceinline__ float mhp_cl_sum(float (*xch)[MHP_MAX_CL * G], int &cpar, unsigned crank,
+                                            unsigned csize, int gw, int lane, float v)
+{
+    if ((unsigned)lane < csize) mhp_cl_store(&xch[cpar][crank * G + gw], (unsigned)lane, v);
+    __syncwarp();
+    mhp_cl_sync();
+    float s = 0.0f;
+    for (unsigned r = 0; r < csize; ++r) {
+#pragma unroll
+        for (int w = 0; w < G; w += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(&xch[cpar][r * G + w]);
+            s += q.x;
+            s += q.y;
+            s += q.z;
+            s += q.w;
+        }
+    }
+    cpar ^= 1;
+    return s;
+}
+
+// A proposal's dE: the group sum, then (clusters) the exchange between CTAs
+template <int G, bool CL>
+__device__ __forceinline__ float mhp_dE(GroupCtx<G> &g, float (*xch)[CL ? MHP_MAX_CL * G : 4], int &cpar,
+                                        unsigned crank, unsigned csize, float v)
+{
+    if constexpr (CL)
+        return mhp_cl_sum<G>(xch, cpar, crank, csize, g.gw, g.lane, warp_sum(v));
+    else
+        return group_sum(g, v);
+}
+
+// The chain's energy: the compensated group sum, then (clusters) the CTAs'
+// totals added in CTA order
+template <int J, int G, bool CL>
+__device__ __forceinline__ float mhp_chain_energy(GroupCtx<G> &g, const float (&e)[J],
+                                                  float (*xch)[CL ? MHP_MAX_CL * G : 4], int &cpar,
+                                                  unsigned crank, unsigned csize)
+{
+    const float E = mhf_group_energy<J, G>(g, e);
+    if constexpr (CL)
+        return mhp_cl_sum<G>(xch, cpar, crank, csize, g.gw, g.lane, g.gw == 0 ? E : 0.0f);
+    else
+        return E;
+}
+
+template <int J, int G, bool CL>
 struct MhpBounds {
-    static constexpr int NT = MhThreads<G>::NT;
+    static constexpr int NT = CL ? 32 * G : MhThreads<G>::NT;
     static constexpr int MINB = (NT == 128) ? (J <= 4 ? 6 : 4) : (NT == 256) ? (J <= 4 ? 3 : 2) : 1;
 };
 
-template <int J, int G>
-__global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
+template <int J, int G, bool CL>
+__global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL>::MINB))
     k_mh_phase(JobDev *__restrict__ jobs, const int *__restrict__ slots, int nslots)
 {
-    constexpr int NT = MhThreads<G>::NT;
+    static_assert(!CL || G == MHP_CL_WARPS, "cluster chains use 8-warp CTAs");
+    constexpr int NT = MhpBounds<J, G, CL>::NT;
     constexpr int P = 9;
     __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
     __shared__ WarpComp comp_sh[NT / 32];
     __shared__ PropTable prop_sh[NT / 32 / G][2];
+    __shared__ __align__(16) float xch_sh[CL ? 2 : 1][CL ? MHP_MAX_CL * G : 4];
+    __shared__ int claim_sh[2][2];
+    unsigned crank = 0, csize = 1;
+    int cpar = 0;
+    if constexpr (CL) {
+        crank = mhp_cl_rank();
+        csize = mhp_cl_size();
+        // every CTA of the cluster runs before any shared::cluster access
+        mhp_cl_sync();
+    }
     GroupCtx<G> g;
     g.lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -112,7 +219,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
     for (;;) {
         // ---- claim the next chain (dynamic scheduling over the bucket's jobs)
         int slot = -1, m = 0;
-        if (g.gw == 0 && lane == 0) {
+        if (g.gw == 0 && lane == 0 && crank == 0) {
             while (li < nslots) {
                 const int sl = slots[li];
                 JobDev &jq = jobs[sl];
@@ -126,12 +233,23 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
                 }
                 ++li;
             }
-            if constexpr (G > 1) {
+            if constexpr (CL) {
+                for (unsigned r = 0; r < csize; ++r) {
+                    mhp_cl_store_i(&claim_sh[cpar][0], r, slot);
+                    mhp_cl_store_i(&claim_sh[cpar][1], r, m);
+                }
+            } else if constexpr (G > 1) {
                 work_sh[g.grp][0] = slot;
                 work_sh[g.grp][1] = m;
             }
         }
-        if constexpr (G == 1) {
+        if constexpr (CL) {
+            __syncwarp();
+            mhp_cl_sync();
+            slot = claim_sh[cpar][0];
+            m = claim_sh[cpar][1];
+            cpar ^= 1;
+        } else if constexpr (G == 1) {
             slot = __shfl_sync(FULL_MASK, slot, 0);
             m = __shfl_sync(FULL_MASK, m, 0);
         } else {
@@ -151,7 +269,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
         const unsigned long long seed = jb.seed;
         const float4 *rtab = jb.rtab;
         const int *roff = jb.roff;
-        const int i0 = (g.gw * 32 + lane) * J;
+        const int i0 = (((int)crank * G + g.gw) * 32 + lane) * J;
 
         for (int j = lane; j < d; j += 32) {
             const float u = jb.ths[(size_t)j * S + m];
@@ -256,7 +374,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
                                 p0 += en[jj] - e[jj];
                         }
                     }
-                    const float dE = group_sum(g, p0 + p1);
+                    const float dE = mhp_dE<G, CL>(g, xch_sh, cpar, crank, csize, p0 + p1);
                     if (tj < -beta * dE) {
                         if (c == 0) {
                             const float dA = v - A;
@@ -307,7 +425,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
                     else
                         p0 += en[jj] - e[jj];
                 }
-                const float dE = group_sum(g, p0 + p1);
+                const float dE = mhp_dE<G, CL>(g, xch_sh, cpar, crank, csize, p0 + p1);
                 if (tj < -beta * dE) {
 #pragma unroll
                     for (int jj = 0; jj < J; ++jj) {
@@ -338,22 +456,22 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
                 }
             }
             if (wf) {
-                const float E = mhf_group_energy<J, G>(g, e);
+                const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, cpar, crank, csize);
                 const size_t o = (size_t)m * n + sw;
-                if (g.gw == 0) {
+                if (g.gw == 0 && crank == 0) {
                     for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
                     if (lane == 0) jb.E[o] = E;
                 }
             }
         }
         if (!wf) {
-            const float E = mhf_group_energy<J, G>(g, e);
-            if (g.gw == 0) {
+            const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, cpar, crank, csize);
+            if (g.gw == 0 && crank == 0) {
                 for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
                 if (lane == 0) jb.E[m] = E;
             }
         }
-        if (g.gw == 0) {
+        if (g.gw == 0 && crank == 0) {
             for (int j = lane; j < d; j += 32)
                 if (jb.pri[j].kind != PR_FIXED) {
                     atomicAdd(&jobs[slot].acc[j], (unsigned long long)cs.acc[j]);
@@ -371,27 +489,34 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhpBounds<J, G>::MINB))
         }
         __syncwarp();
     }
+    // no CTA leaves while a peer could still address its shared memory
+    if constexpr (CL) mhp_cl_sync();
 }
 
-template <int G>
+template <int G, bool CL>
 static mh_fn mhp_pick_j(int J)
 {
     switch (J) {
-    case 4: return k_mh_phase<4, G>;
-    case 8: return k_mh_phase<8, G>;
+    case 4: return k_mh_phase<4, G, CL>;
+    case 8: return k_mh_phase<8, G, CL>;
     default: return nullptr;
     }
 }
 
+// G warps per chain: 1..16 in one block; multiples of 8 above (a cluster of
+// G / 8 CTAs of 8 warps, at most MHP_MAX_CL)
 static mh_fn mhp_pick_tile(int J, int G)
 {
     switch (G) {
-    case 1: return mhp_pick_j<1>(J);
-    case 2: return mhp_pick_j<2>(J);
-    case 4: return mhp_pick_j<4>(J);
-    case 8: return mhp_pick_j<8>(J);
-    case 16: return mhp_pick_j<16>(J);
-    default: return nullptr;
+    case 1: return mhp_pick_j<1, false>(J);
+    case 2: return mhp_pick_j<2, false>(J);
+    case 4: return mhp_pick_j<4, false>(J);
+    case 8: return mhp_pick_j<8, false>(J);
+    case 16: return mhp_pick_j<16, false>(J);
+    default:
+        if (G > 16 && G % MHP_CL_WARPS == 0 && G / MHP_CL_WARPS <= MHP_MAX_CL)
+            return mhp_pick_j<MHP_CL_WARPS, true>(J);
+        return nullptr;
     }
 }
 

@@ -151,13 +151,72 @@ def test_full_size_sampled_energies(ctx):
     assert np.all(np.abs(e32 - e64) <= 2e-5 * (np.abs(e64) + spec.n))
 
 
-def test_long_grid_at_truth(ctx):
-    """A 4000-point pattern (near the 4096 points one FP32 chain tile holds):
-    FP32 and FP64 energies at the truth."""
-    spec = W.xrd_phase(5, n=4000, k_min=3, k_max=3)
+def test_paper_grid_at_truth(ctx):
+    """The largest App. D grid (N = 10000): FP32 and FP64 energies at the truth."""
+    spec = W.xrd_phase(5, n=10000, k_min=3, k_max=3)
     opts = W.Options(particles=64, seed=1)
     e_or = oracle.energy_spec(spec, 3, TRUTH_NAT)
     e64 = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=1)[0]
     e32 = ctx.energy(spec, 3, opts, np.array([TRUTH_NAT]), precision=0)[0]
     assert e64 == pytest.approx(e_or, rel=1e-12)
     assert abs(e32 - e_or) <= 2e-5 * (abs(e_or) + spec.n)
+
+
+@pytest.mark.parametrize("J,G", [(4, 24), (8, 32), (8, 128)])
+def test_cluster_chains_track_the_oracle(ctx, J, G):
+    """A chain spread over a thread-block cluster of G / 8 CTAs (forced on a
+    1000-point grid, most CTAs holding padding only at G = 128): the same
+    proposals as the oracle, accept counts within the FP32 band, final
+    energies equal to the oracle's energies of the returned states."""
+    spec = W.xrd_phase(2, n=1000, k_min=2, k_max=2)
+    K = 2
+    opts = W.Options(particles=64, sweeps=3, seed=9)
+    u, E = oracle.init_particles(spec, K, opts, 64)
+    ok = np.isfinite(E)
+    u, E = u[ok][:40], E[ok][:40]
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, 1e-3, 4)
+    ctx.clear_tiles()
+    ctx.set_tile(W.XRD_PHASE | 16, 1 << 20, J, G)
+    try:
+        nat32, E32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u, E, step, 1e-3, 4, precision=0)
+    finally:
+        ctx.clear_tiles()
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+def test_cluster_stage_on_a_long_grid(ctx):
+    """N = 6000 (three 8-warp CTAs per chain at J = 8): one Metropolis stage
+    against the oracle's on the same streams."""
+    spec = W.xrd_phase(3, n=6000, k_min=2, k_max=2)
+    K = 2
+    opts = W.Options(particles=16, sweeps=2, seed=4)
+    u, E = oracle.init_particles(spec, K, opts, 16)
+    ok = np.isfinite(E)
+    u, E = u[ok], E[ok]
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, 1e-3, 2)
+    nat32, E32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u, E, step, 1e-3, 2, precision=0)
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+@pytest.mark.parametrize("n", [5000, 10000])
+def test_paper_grid_sizes_sampled(ctx, n):
+    """The paper's App. D grids N = 5000 and 10000 (K = 3, T = 8192, n = 10):
+    two stages of the cluster-spanning FP32 chains, sampled final energies vs
+    the oracle."""
+    spec = W.xrd_phase(1, n=n, k_min=3, k_max=3)
+    opts = W.Options(particles=8192, sweeps=10, seed=3, max_stages=2)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["job_status"][0] == 5 and np.isfinite(r["log_z"][0])
+    smp = r["samples"][0].astype(np.float64)
+    idx = np.random.default_rng(3).choice(8192, 16, replace=False)
+    e64 = np.array([oracle.energy_spec(spec, 3, v) for v in smp[idx]])
+    e32 = ctx.energy(spec, 3, opts, smp[idx], precision=0)
+    assert np.all(np.abs(e32 - e64) <= 2e-5 * (np.abs(e64) + spec.n))
