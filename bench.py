@@ -65,11 +65,13 @@ def workload(name: str, seed: int):
         # App. E: PV peaks on a Shirley background, model-dependent variance,
         # the paper's data-derived priors, K = 5..8 (the paper compares 6, 7, 8)
         return W.xps_shirley(seed), W.Options(particles=16384, sweeps=20, seed=seed)
-    if name == "xrd_phase":
-        # App. D: three TiO2-like phases (31 parameters) on 1000 points of 2 theta,
-        # Poisson counts, the paper's n = 10 sweeps; T from the paper's range
-        # (100 x {1 .. 10000})
-        return W.xrd_phase(seed, n=1000, k_min=3, k_max=3), W.Options(particles=100000, sweeps=10, seed=seed)
+    if name.startswith("xrd_phase"):
+        # App. D: three TiO2-like phases (31 parameters) on N = 1000 / 5000 /
+        # 10000 points of 2 theta, Poisson counts, the paper's n = 10 sweeps; T
+        # from the paper's range (100 x {1 .. 10000}): 10^5 / 3 10^4 / 10^4
+        n = {"xrd_phase": 1000, "xrd_phase_5000": 5000, "xrd_phase_10000": 10000}[name]
+        T = {1000: 100000, 5000: 30000, 10000: 10000}[n]
+        return W.xrd_phase(seed, n=n, k_min=3, k_max=3), W.Options(particles=T, sweeps=10, seed=seed)
     if name.startswith("deconv"):
         # App. C Gaussian deconvolution at the true K, the paper's sweeps per
         # stage; particles from the paper's range (100 x {3 .. 10000})
@@ -84,7 +86,8 @@ def config_of(name: str, batch: int) -> dict:
     s, o = workload(name, 1)
     return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301",
                          "mixed": "mixed-256", "xps_shirley": "xps-shirley-model-variance-840",
-                         "xrd_phase": "xrd-phase-poisson-K3-1000",
+                         "xrd_phase": "xrd-phase-poisson-K3-1000", "xrd_phase_5000": "xrd-phase-poisson-K3-5000",
+                         "xrd_phase_10000": "xrd-phase-poisson-K3-10000",
                          "deconv3": "deconv-gauss-K3-300",
                          "deconv10": "deconv-gauss-K10-1000", "deconv30": "deconv-gauss-K30-3000"}[name],
             "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
@@ -200,7 +203,7 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12,
+UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 9.7e11,
                       "deconv3": 3.6e10, "deconv10": 8.2e11, "deconv30": 4.8e13}
 
 
@@ -213,7 +216,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "deconv3", "deconv10",
+    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "xrd_phase_5000",
+                                                       "xrd_phase_10000", "deconv3", "deconv10",
                                                        "deconv30"])
     ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -427,7 +431,7 @@ def plain_sample(ctx, name: str, units_per_spec: float) -> dict:
     # the App. D model costs ~40 FP64 pseudo-Voigts per particle-point: a fifth
     # of its particles keeps the sample near ten seconds (the rate per
     # particle-point is what is scaled; 20000 threads fill the device)
-    T = min(o.particles, 20000) if name == "xrd_phase" else o.particles
+    T = min(o.particles, 20000 * 1000 // spec.n) if name.startswith("xrd_phase") else o.particles
     opts = W.Options(particles=T, sweeps=o.sweeps, seed=1, energy_fp64=1, max_stages=1)
     ctx.profile_reset(events=False)
     t0 = time.perf_counter()

@@ -25,14 +25,18 @@ J_SET = {W.PSEUDO_VOIGT: (4, 8, 12, 16), W.GAUSS: (4, 8, 12, 16, 24, 32), W.LORE
 COUPLED = 16  # family flag of the coupled-grid kernel (Shirley background, model variance)
 J_SET_COUPLED = (4, 8)
 G_SET = (1, 2, 4, 8, 16)
+# the phase kernel also spreads a chain over a cluster of 8-warp CTAs (G = 8 C)
+G_SET_CLUSTER = tuple(8 * c for c in range(3, 17))
+BUCKETS_XRD = (512, 1024, 2048, 4096, 5120, 10240)
 
 
 def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]:
     """Admissible tiles for an n-point grid whose padding is within `slack` of
     the smallest one."""
     tiles = []
+    gs = G_SET + (G_SET_CLUSTER if family == W.XRD_PHASE | COUPLED else ())
     for J in (J_SET_COUPLED if family & COUPLED else J_SET[family]):
-        for G in G_SET:
+        for G in gs:
             if G == 16 and J > 8:
                 continue
             if J > 16 and G > 1:
@@ -69,7 +73,7 @@ def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COU
          particles: int = 8192, sweeps: int = 4, stages: int = 6, verbose: bool = True) -> List[Dict]:
     table = []
     for fam in families:
-        for n in buckets:
+        for n in (BUCKETS_XRD if fam == W.XRD_PHASE | COUPLED else buckets):
             spec = tuning_spectrum(fam, n)
             opts = W.Options(particles=particles, sweeps=sweeps, seed=5, max_stages=stages)
             results = []
