@@ -716,7 +716,7 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
         if (r->fp64)
             st = cuda_status(launch_mh_plain(c.d_jobs, c.d_lists, 1, (int)S, c.stream));
         else
-            st = cuda_status(launch_mh(c.d_jobs, c.d_lists, 1, kernel_family(r->family) | (r->full ? MH_COUPLED : 0), r->tile.J, r->tile.G, 0, c.stream));
+            st = cuda_status(launch_mh(c.d_jobs, c.d_lists, 1, kernel_family(r->family) | (r->full ? MH_COUPLED : 0), r->tile.J, r->tile.G, 0, c.stream, K));
     }
     if (st == SMC_OK) st = cuda_status(cudaStreamSynchronize(c.stream));
     if (st == SMC_OK)

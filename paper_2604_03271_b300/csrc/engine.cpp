@@ -550,6 +550,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
 struct Bucket {
     int family, J, G;
     std::vector<int> slots;
+    int kcap = 0;  // most peaks (phases) of its jobs
 };
 
 struct Plan {
@@ -583,6 +584,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
                 b = &P.buckets.back();
             }
             b->slots.push_back(sl);
+            b->kcap = std::max(b->kcap, jb.K);
         }
     }
     if (P.all.empty()) return SMC_OK;
@@ -596,7 +598,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
     for (Bucket &b : P.buckets) {
         P.boff.push_back(host_lists.size());
         host_lists.insert(host_lists.end(), b.slots.begin(), b.slots.end());
-        P.grids.push_back(mh_resident_grid(b.family, b.J, b.G));
+        P.grids.push_back(mh_resident_grid(b.family, b.J, b.G, b.kcap));
     }
     if ((int)host_lists.size() > LIST_AREA) return SMC_ENOMEM;
     CK(cudaMemcpyAsync(c.d_lists, host_lists.data(), 4 * host_lists.size(), cudaMemcpyHostToDevice,
@@ -626,8 +628,8 @@ static cudaError_t iteration(Ctx &c, const Plan &P, cudaEvent_t *ev, int k)
     if ((e = mark(3)) != cudaSuccess) return e;
     for (size_t b = 0; b < P.buckets.size(); ++b)
         if ((e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
-                           P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b],
-                           c.stream)) != cudaSuccess)
+                           P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream,
+                           P.buckets[b].kcap)) != cudaSuccess)
             return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_stage_end(c.d_jobs, c.d_lists, nall, c.d_nactive, c.h_nactive_dev + k, c.stream)) !=
@@ -677,7 +679,8 @@ static bool run_whole_graph(Ctx &c, const Plan &P, int *status)
         if (e == cudaSuccess) e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream);
         for (size_t b = 0; b < P.buckets.size() && e == cudaSuccess; ++b)
             e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
-                          P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream);
+                          P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream,
+                          P.buckets[b].kcap);
         if (e == cudaSuccess)
             e = launch_stage_end_cond(c.d_jobs, c.d_lists, nall, c.d_nactive, h, c.d_nactive + 1,
                                       max_iter, c.stream);

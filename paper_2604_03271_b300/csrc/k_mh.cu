@@ -40,12 +40,22 @@ static mh_fn pick(int family, int J, int G)
 
 bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
 
-static cudaLaunchConfig_t cluster_config(int C, int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+// Dynamic shared memory of the phase kernel's profile cache: kcap profiles of
+// every point of the block (threads x J points), if at most 96 KB
+static size_t mh_smem(int family, int J, int G, int kcap)
+{
+    if ((family & (MH_COUPLED - 1)) != FAM_XRD || kcap < 1) return 0;
+    const int threads = cluster_of(family, G) > 1 ? 256 : block_threads(G);
+    const size_t b = (size_t)kcap * threads * J * sizeof(float);
+    return b <= 96 * 1024 ? b : 0;
+}
+
+static cudaLaunchConfig_t cluster_config(int C, int grid, size_t smem, cudaStream_t s, cudaLaunchAttribute *attr)
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
@@ -56,17 +66,20 @@ static cudaLaunchConfig_t cluster_config(int C, int grid, cudaStream_t s, cudaLa
     return cfg;
 }
 
-int mh_resident_grid(int family, int J, int G)
+int mh_resident_grid(int family, int J, int G, int kcap)
 {
     mh_fn f = pick(family, J, G);
     if (!f) return 0;
     const int C = cluster_of(family, G);
+    const size_t smem = mh_smem(family, J, G, kcap);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (C > 1) {
         // clusters of C CTAs resident at once (every CTA of a cluster runs the
         // same chain, so the grid holds whole clusters)
         if (C > 8) cudaFuncSetAttribute((const void *)f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = cluster_config(C, C * 148, nullptr, attr);
+        cudaLaunchConfig_t cfg = cluster_config(C, C * 148, smem, nullptr, attr);
         int ncl = 0;
         if (cudaOccupancyMaxActiveClusters(&ncl, (const void *)f, &cfg) != cudaSuccess || ncl < 1) {
             cudaGetLastError();
@@ -77,26 +90,27 @@ int mh_resident_grid(int family, int J, int G)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)f, block_threads(G), 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)f, block_threads(G), smem);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
-                      int grid, cudaStream_t s)
+                      int grid, cudaStream_t s, int kcap)
 {
     mh_fn f = pick(family, J, G);
     if (!f) return cudaErrorInvalidValue;
     if (nslots <= 0) return cudaSuccess;
-    if (grid <= 0) grid = mh_resident_grid(family, J, G);
+    if (grid <= 0) grid = mh_resident_grid(family, J, G, kcap);
     const int C = cluster_of(family, G);
+    const size_t smem = mh_smem(family, J, G, kcap);
     if (C > 1) {
         if (grid < C || grid % C != 0) return cudaErrorInvalidConfiguration;
         cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = cluster_config(C, grid, s, attr);
+        cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, s, attr);
         return cudaLaunchKernelEx(&cfg, f, jobs, slots, nslots);
     }
-    f<<<grid, block_threads(G), 0, s>>>(jobs, slots, nslots);
+    f<<<grid, block_threads(G), smem, s>>>(jobs, slots, nslots);
     return cudaGetLastError();
 }
 

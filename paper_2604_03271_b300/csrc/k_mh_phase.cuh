@@ -16,7 +16,10 @@
 // profile U' (per reflection and point one EX2 and one RCP, per point two
 // reciprocals) and changes f by A (U' - U).  Every proposal
 // recomputes the energy term at every point; dE is one group reduction.
-// Phases are not exchangeable and are never reordered.
+// Phases are not exchangeable and are never reordered.  When the launch
+// gives dynamic shared memory for K profiles per group, each phase's unit
+// profile is kept there across sweeps (rewritten when a shape proposal of
+// the phase is accepted), so a phase's block starts from it without a rebuild.
 //
 // Grids longer than one block's tile (32 G J points) run with CL = true: a
 // chain spans a thread-block cluster of C CTAs of G = 8 warps (C = 2..16, the
@@ -151,6 +154,34 @@ __device__ __forceinline__ float mhp_cl_sum(float (*xch)[MHP_MAX_CL * G], int &c
     return s;
 }
 
+// Per-phase unit profiles of the lane's J points, kept in dynamic shared
+// memory across sweeps ([K][32 G J] per group, the lane's J points contiguous)
+template <int J>
+__device__ __forceinline__ void mhp_cache_store(float *uc, const float (&U)[J])
+{
+#pragma unroll
+    for (int jj = 0; jj < J; jj += 4)
+        *reinterpret_cast<float4 *>(uc + jj) = make_float4(U[jj], U[jj + 1], U[jj + 2], U[jj + 3]);
+}
+template <int J>
+__device__ __forceinline__ void mhp_cache_load(const float *uc, float (&U)[J])
+{
+#pragma unroll
+    for (int jj = 0; jj < J; jj += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(uc + jj);
+        U[jj] = q.x;
+        U[jj + 1] = q.y;
+        U[jj + 2] = q.z;
+        U[jj + 3] = q.w;
+    }
+}
+__device__ __forceinline__ unsigned mhp_dyn_smem_bytes()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 // A proposal's dE: the group sum, then (clusters) the exchange between CTAs
 template <int G, bool CL>
 __device__ __forceinline__ float mhp_dE(GroupCtx<G> &g, float (*xch)[CL ? MHP_MAX_CL * G : 4], int &cpar,
@@ -214,6 +245,11 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
     g.red = &red_sh[g.grp][0][0];
     const int lane = g.lane;
     WarpComp &cs = comp_sh[warp];
+    // profile cache: as many phases as the launch's dynamic shared memory holds
+    extern __shared__ __align__(16) float ucache_sh[];
+    constexpr int GP = 32 * G * J;  // points of a group (of a CTA with clusters)
+    const int kcache = (int)(mhp_dyn_smem_bytes() / (4u * (unsigned)(ngroups * GP)));
+    float *ucg = ucache_sh + (size_t)g.grp * kcache * GP + (g.gw * 32 + lane) * J;
 
     int li = 0;
     for (;;) {
@@ -287,10 +323,12 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
             w[jj] = __ldg(jb.wt + i0 + jj);
             f[jj] = 0.0f;
         }
+        const bool cached = K <= kcache;
         for (int k = 0; k < K; ++k) {
             const float *q = cs.nat + P * k;
             mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8], rtab,
                            roff[k], roff[k + 1]);
+            if (cached) mhp_cache_store<J>(ucg + k * GP, U);
 #pragma unroll
             for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(q[0], U[jj], f[jj]);
         }
@@ -336,8 +374,12 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
             for (int k = 0; k < K; ++k) {
                 const int jc0 = P * k, j0 = roff[k], j1 = roff[k + 1];
                 const float *q = cs.nat + jc0;
-                mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8], rtab,
-                               j0, j1);
+                if (cached)
+                    mhp_cache_load<J>(ucg + k * GP, U);
+                else
+                    mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8],
+                                   rtab, j0, j1);
+                bool changed = false;
 #pragma unroll 1
                 for (int c = 0; c < P; ++c) {
                     const int j = jc0 + c;
@@ -386,6 +428,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                                 f[jj] = fmaf(A, Un[jj] - U[jj], f[jj]);
                                 U[jj] = Un[jj];
                             }
+                            changed = true;
                         }
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) e[jj] = en[jj];
@@ -398,6 +441,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                         __syncwarp();
                     }
                 }
+                if (cached && changed) mhp_cache_store<J>(ucg + k * GP, U);
             }
             // ---- background (a, s_bg, r_bg, b)
             for (int qb = 0; qb < nbg; ++qb) {

@@ -46,10 +46,12 @@ cudaError_t launch_gather(JobDev *jobs, const int *slots, int nslots, int64_t ma
 // family = FAM_* of the peaks, | MH_COUPLED for the coupled-grid kernel (Shirley
 // background and/or model variance).
 constexpr int MH_COUPLED = 16;
+// kcap: most peaks (phases) of the launch's jobs; the phase kernel then gets
+// dynamic shared memory for that many cached profiles per chain (if it fits)
 cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
-                      int grid, cudaStream_t s);
+                      int grid, cudaStream_t s, int kcap = 0);
 bool mh_tile_supported(int family, int J, int G);
-int mh_resident_grid(int family, int J, int G);
+int mh_resident_grid(int family, int J, int G, int kcap = 0);
 
 // Plain FP64 Metropolis stage (thread per chain, full energy per proposal).
 cudaError_t launch_mh_plain(JobDev *jobs, const int *slots, int nslots, int max_S,
