@@ -101,14 +101,13 @@ def test_full_run_fp64_replays_oracle(ctx):
 def test_fp32_estimator_and_selection(ctx):
     # three true peaks (two lines and a satellite) on a Shirley background,
     # model variance; K = 2..4: FP32 batched vs the FP64 path over seeds
+    # (FP32 over 8 seeds, the plain FP64 path over 4)
     spec = W.xps_shirley(4, n=400, k_true=3, k_min=2, k_max=4)
-    lz32, lz64 = [], []
-    for s in range(1, 9):
-        lz32.append(ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s), keep_samples=False)["log_z"])
-        lz64.append(ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s, energy_fp64=1),
-                            keep_samples=False)["log_z"])
-    lz32, lz64 = np.array(lz32), np.array(lz64)
-    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 8)
+    lz32 = np.array([ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s), keep_samples=False)["log_z"]
+                     for s in range(1, 9)])
+    lz64 = np.array([ctx.run(spec, W.Options(particles=512, sweeps=4, seed=s, energy_fp64=1),
+                             keep_samples=False)["log_z"] for s in range(1, 5)])
+    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 4)
     diff = np.abs(lz32.mean(0) - lz64.mean(0))
     assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
     assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0)) == 1

@@ -45,12 +45,20 @@ def _no_bg(spec):
                       phase_priors=spec.phase_priors)
 
 
+def _gauss_approx(spec):
+    """App. D's Gaussian approximation to the counts (variance = f): the
+    model-variance likelihood with (s0, s1, s2) = (1, 0, 0)."""
+    return W.Spectrum(spec.x, spec.y, np.ones_like(spec.y), W.XRD_PHASE, spec.k_min, spec.k_max, W.BG_XRD_PV, 0,
+                      spec.priors, truth=spec.truth, name="xrd-gauss-approx", noise=W.NOISE_MODEL,
+                      noise_par=(1.0, 0.0, 0.0), refs=spec.refs, phase_priors=spec.phase_priors)
+
+
 def _variants(n=1000, seed=1, K=3):
     full = W.xrd_phase(seed, n=n, k_min=K, k_max=K)
-    return [full, _known_sigma(full), _no_bg(full)]
+    return [full, _known_sigma(full), _no_bg(full), _gauss_approx(full)]
 
 
-@pytest.mark.parametrize("which", range(3))
+@pytest.mark.parametrize("which", range(4))
 def test_energies_fp64_and_fp32(ctx, which):
     spec = _variants()[which]
     K = spec.k_min
@@ -72,7 +80,7 @@ def test_energies_fp64_and_fp32(ctx, which):
         assert abs(e32 - e_or) <= 2e-5 * (abs(e_or) + spec.n)
 
 
-@pytest.mark.parametrize("which,beta", [(0, 1e-3), (1, 1e-2), (2, 1e-3)])
+@pytest.mark.parametrize("which,beta", [(0, 1e-3), (1, 1e-2), (2, 1e-3), (3, 1e-3)])
 def test_mh_stage_replay_and_tracking(ctx, which, beta):
     spec = _variants(n=300, seed=2, K=2)[which]
     K = 2
