@@ -869,7 +869,10 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             c.prof.rcp_ops += 0.5 * (double)jd.var_ops;
             if (jd.family == SMC_GAUSS) c.prof.ex2_ops += (double)jd.sfu_ops;
             else if (jd.family == SMC_LORENTZ) c.prof.rcp_ops += (double)jd.sfu_ops;
-            else {
+            else if (jd.family == SMC_XRD_PHASE) {
+                c.prof.ex2_ops += (double)jd.ex2_part;
+                c.prof.rcp_ops += (double)(jd.sfu_ops - jd.ex2_part);
+            } else {
                 c.prof.ex2_ops += 0.5 * (double)jd.sfu_ops;
                 c.prof.rcp_ops += 0.5 * (double)jd.sfu_ops;
             }

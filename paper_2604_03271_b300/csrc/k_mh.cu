@@ -40,13 +40,13 @@ static mh_fn pick(int family, int J, int G)
 
 bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
 
-// Dynamic shared memory of the phase kernel's profile cache: kcap profiles of
-// every point of the block (threads x J points), if at most 96 KB
+// Dynamic shared memory of the phase kernel's profile cache: the two parts of
+// kcap profiles at every point of the block (threads x J points), if at most 96 KB
 static size_t mh_smem(int family, int J, int G, int kcap)
 {
     if ((family & (MH_COUPLED - 1)) != FAM_XRD || kcap < 1) return 0;
     const int threads = cluster_of(family, G) > 1 ? 256 : block_threads(G);
-    const size_t b = (size_t)kcap * threads * J * sizeof(float);
+    const size_t b = 2 * (size_t)kcap * threads * J * sizeof(float);
     return b <= 96 * 1024 ? b : 0;
 }
 
@@ -72,8 +72,8 @@ int mh_resident_grid(int family, int J, int G, int kcap)
     if (!f) return 0;
     const int C = cluster_of(family, G);
     const size_t smem = mh_smem(family, J, G, kcap);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // static plus dynamic shared memory may pass 48 KB: opt in for every size
+    if (smem > 0) cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (C > 1) {
         // clusters of C CTAs resident at once (every CTA of a cluster runs the
         // same chain, so the grid holds whole clusters)

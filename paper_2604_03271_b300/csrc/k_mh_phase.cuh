@@ -34,29 +34,37 @@
 
 namespace smc {
 
-// Unit profile (A = 1) of one phase at the lane's J points, from the phase's
-// natural components (A, d2theta, alpha, r, u, v, w, s, t); iam1 = 1/alpha - 1.
-// Per point: K1 = -4 / S^2 (S^2 = u T^2 - v T + w) and K2 = 4 / W^2 (0 where
-// the width is not positive); per reflection (R = centred position, I,
-// log2 I) and point: dx = x - (R.x + d2theta), q = dx scaled by 1/alpha right
-// of the reflection, I G = 2^(K1 q^2 + log2 I), L = 1 / (1 + K2 q^2):
-// one EX2 and one RCP, eight ALU operations.  The reflections are read once per
-// lane (a uniform address), outside the loop over the lane's points.
-template <int J>
-__device__ __forceinline__ void mhp_profile(float (&U)[J], const float *__restrict__ gx,
-                                            const float *__restrict__ gt, const float *__restrict__ gs,
-                                            float shift, float iam1, float r, float u, float v, float w,
-                                            float s, float t, const float4 *__restrict__ rtab, int j0, int j1)
+// The two parts of one phase's unit profile (A = 1) at the lane's J points,
+// from the phase's natural components (d2theta, alpha, u, v, w, s, t);
+// iam1 = 1/alpha - 1:  Gs = sum_j I_j G_j and Ls = sum_j I_j L_j, each 0 where
+// its width is not positive, so that the profile is (1 - r) Gs + r Ls.
+// MODE bit 1: Gs, bit 2: Ls (the other output is left alone).
+// Per point: K1 = -4 / S^2 (S^2 = u T^2 - v T + w), K2 = 4 / W^2; per
+// reflection (R = centred position, I, log2 I) and point: dx = x - (R.x +
+// d2theta), q = dx scaled by 1/alpha right of the reflection, I G =
+// 2^(K1 q^2 + log2 I) (one EX2), L = 1 / (1 + K2 q^2) (one RCP), with six ALU
+// operations for one part and eight for both.  The reflections are read once
+// per lane (a uniform address), outside the loop over the lane's points.
+template <int J, int MODE>
+__device__ __forceinline__ void mhp_sums(float (&Gs)[J], float (&Ls)[J], const float *__restrict__ gx,
+                                         const float *__restrict__ gt, const float *__restrict__ gs,
+                                         float shift, float iam1, float u, float v, float w, float s, float t,
+                                         const float4 *__restrict__ rtab, int j0, int j1)
 {
+    constexpr bool DG = (MODE & 1) != 0, DL = (MODE & 2) != 0;
     float xs[J], K1[J], K2[J], Ug[J], Ul[J];
 #pragma unroll
     for (int jj = 0; jj < J; ++jj) {
-        const float tn = __ldg(gt + jj), sc = __ldg(gs + jj);
-        const float rad = fmaf(u * tn, tn, fmaf(-v, tn, w));
-        const float W0 = fmaf(s, sc, t * tn);
+        const float tn = __ldg(gt + jj);
         // clamped so that q = 0 never meets an infinite factor
-        K1[jj] = rad > 0.0f ? fmaxf(-4.0f * rcp_approx(rad), -3.0e38f) : 0.0f;
-        K2[jj] = W0 > 0.0f ? fminf(4.0f * rcp_approx(W0 * W0), 3.0e38f) : 0.0f;
+        if (DG) {
+            const float rad = fmaf(u * tn, tn, fmaf(-v, tn, w));
+            K1[jj] = rad > 0.0f ? fmaxf(-4.0f * rcp_approx(rad), -3.0e38f) : 0.0f;
+        }
+        if (DL) {
+            const float W0 = fmaf(s, __ldg(gs + jj), t * tn);
+            K2[jj] = W0 > 0.0f ? fminf(4.0f * rcp_approx(W0 * W0), 3.0e38f) : 0.0f;
+        }
         xs[jj] = __ldg(gx + jj) - shift;
         Ug[jj] = 0.0f;
         Ul[jj] = 0.0f;
@@ -68,14 +76,14 @@ __device__ __forceinline__ void mhp_profile(float (&U)[J], const float *__restri
             const float dx = xs[jj] - R.x;
             const float q = fmaf(fmaxf(dx, 0.0f), iam1, dx);
             const float q2 = q * q;
-            Ug[jj] += ex2_approx(fmaf(q2, K1[jj], R.z));
-            Ul[jj] = fmaf(R.y, rcp_approx(fmaf(q2, K2[jj], 1.0f)), Ul[jj]);
+            if (DG) Ug[jj] += ex2_approx(fmaf(q2, K1[jj], R.z));
+            if (DL) Ul[jj] = fmaf(R.y, rcp_approx(fmaf(q2, K2[jj], 1.0f)), Ul[jj]);
         }
     }
 #pragma unroll
     for (int jj = 0; jj < J; ++jj) {
-        const float cg = K1[jj] < 0.0f ? 1.0f - r : 0.0f, cl = K2[jj] > 0.0f ? r : 0.0f;
-        U[jj] = fmaf(cg, Ug[jj], cl * Ul[jj]);
+        if (DG) Gs[jj] = K1[jj] < 0.0f ? Ug[jj] : 0.0f;
+        if (DL) Ls[jj] = K2[jj] > 0.0f ? Ul[jj] : 0.0f;
     }
 }
 
@@ -154,8 +162,9 @@ __device__ __forceinline__ float mhp_cl_sum(float (*xch)[MHP_MAX_CL * G], int &c
     return s;
 }
 
-// Per-phase unit profiles of the lane's J points, kept in dynamic shared
-// memory across sweeps ([K][32 G J] per group, the lane's J points contiguous)
+// Per-phase profile parts of the lane's J points, kept in dynamic shared
+// memory across sweeps ([K][2][32 G J] per group: Gs, Ls; the lane's J points
+// contiguous)
 template <int J>
 __device__ __forceinline__ void mhp_cache_store(float *uc, const float (&U)[J])
 {
@@ -245,11 +254,11 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
     g.red = &red_sh[g.grp][0][0];
     const int lane = g.lane;
     WarpComp &cs = comp_sh[warp];
-    // profile cache: as many phases as the launch's dynamic shared memory holds
+    // profile-part cache: as many phases as the launch's dynamic shared memory holds
     extern __shared__ __align__(16) float ucache_sh[];
     constexpr int GP = 32 * G * J;  // points of a group (of a CTA with clusters)
-    const int kcache = (int)(mhp_dyn_smem_bytes() / (4u * (unsigned)(ngroups * GP)));
-    float *ucg = ucache_sh + (size_t)g.grp * kcache * GP + (g.gw * 32 + lane) * J;
+    const int kcache = (int)(mhp_dyn_smem_bytes() / (8u * (unsigned)(ngroups * GP)));
+    float *ucg = ucache_sh + (size_t)g.grp * kcache * 2 * GP + (g.gw * 32 + lane) * J;
 
     int li = 0;
     for (;;) {
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
         __syncwarp();
 
         const float *gx = jb.xc + i0, *gt = jb.ts + i0, *gs = jb.sec2 + i0;
-        float y[J], w[J], f[J], e[J], U[J], Un[J], en[J], Bv[J];
+        float y[J], w[J], f[J], e[J], U[J], Gn[J], Ln[J], en[J], Bv[J];
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) {
             y[jj] = __ldg(jb.y + i0 + jj);
@@ -326,11 +335,14 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
         const bool cached = K <= kcache;
         for (int k = 0; k < K; ++k) {
             const float *q = cs.nat + P * k;
-            mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8], rtab,
+            mhp_sums<J, 3>(Gn, Ln, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[4], q[5], q[6], q[7], q[8], rtab,
                            roff[k], roff[k + 1]);
-            if (cached) mhp_cache_store<J>(ucg + k * GP, U);
+            if (cached) {
+                mhp_cache_store<J>(ucg + (2 * k) * GP, Gn);
+                mhp_cache_store<J>(ucg + (2 * k + 1) * GP, Ln);
+            }
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(q[0], U[jj], f[jj]);
+            for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(q[0], fmaf(q[3], Ln[jj] - Gn[jj], Gn[jj]), f[jj]);
         }
         float ba = 0.0f, bs = 0.0f, br = 0.0f, bb = 0.0f;
         if (nbg > 0) {
@@ -347,7 +359,8 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
         }
 
         unsigned n_eval = 0;
-        unsigned long long n_shape_ref = 0;  // reflections over the shape proposals
+        // reflections whose Gaussian (EX2) / Lorentzian (RCP) parts the shape proposals evaluated
+        unsigned long long n_ex2_ref = 0, n_rcp_ref = 0;
         for (int sw = 0; sw < n; ++sw) {
             PropTable &tb = prop_sh[g.grp][sw & 1];
             if (g.gw == 0)
@@ -374,12 +387,16 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
             for (int k = 0; k < K; ++k) {
                 const int jc0 = P * k, j0 = roff[k], j1 = roff[k + 1];
                 const float *q = cs.nat + jc0;
-                if (cached)
-                    mhp_cache_load<J>(ucg + k * GP, U);
-                else
-                    mhp_profile<J>(U, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[3], q[4], q[5], q[6], q[7], q[8],
-                                   rtab, j0, j1);
-                bool changed = false;
+                float *ucG = ucg + (2 * k) * GP, *ucL = ucg + (2 * k + 1) * GP;
+                if (cached) {
+                    mhp_cache_load<J>(ucG, Gn);
+                    mhp_cache_load<J>(ucL, Ln);
+                } else {
+                    mhp_sums<J, 3>(Gn, Ln, gx, gt, gs, q[1], 1.0f / q[2] - 1.0f, q[4], q[5], q[6], q[7], q[8], rtab,
+                                   j0, j1);
+                }
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj) U[jj] = fmaf(q[3], Ln[jj] - Gn[jj], Gn[jj]);
 #pragma unroll 1
                 for (int c = 0; c < P; ++c) {
                     const int j = jc0 + c;
@@ -390,6 +407,10 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                     const float A = q[0];
                     ++n_eval;
                     float p0 = 0.0f, p1 = 0.0f;
+                    // parts a shape proposal rebuilds: r none (the cached parts
+                    // remix), u, v, w the Gaussian part, s, t the Lorentzian
+                    // part, d2theta and alpha both (both always without a cache)
+                    const int mode = !cached ? 3 : c == 3 ? 0 : c >= 7 ? 2 : c >= 4 ? 1 : 3;
                     if (c == 0) {
                         const float dA = v - A;
 #pragma unroll
@@ -401,15 +422,31 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                                 p0 += en[jj] - e[jj];
                         }
                     } else {
-                        n_shape_ref += (unsigned long long)(j1 - j0);
                         // the phase's components with component c replaced by v
                         const float sh = c == 1 ? v : q[1], al = c == 2 ? v : q[2], r = c == 3 ? v : q[3];
                         const float cu = c == 4 ? v : q[4], cv = c == 5 ? v : q[5], cw = c == 6 ? v : q[6];
                         const float cs_ = c == 7 ? v : q[7], ct = c == 8 ? v : q[8];
-                        mhp_profile<J>(Un, gx, gt, gs, sh, 1.0f / al - 1.0f, r, cu, cv, cw, cs_, ct, rtab, j0, j1);
+                        const float iam1 = 1.0f / al - 1.0f;
+                        if (mode == 0) {
+                            mhp_cache_load<J>(ucG, Gn);
+                            mhp_cache_load<J>(ucL, Ln);
+                        } else if (mode == 1) {
+                            mhp_sums<J, 1>(Gn, Ln, gx, gt, gs, sh, iam1, cu, cv, cw, cs_, ct, rtab, j0, j1);
+                            mhp_cache_load<J>(ucL, Ln);
+                            n_ex2_ref += (unsigned long long)(j1 - j0);
+                        } else if (mode == 2) {
+                            mhp_sums<J, 2>(Gn, Ln, gx, gt, gs, sh, iam1, cu, cv, cw, cs_, ct, rtab, j0, j1);
+                            mhp_cache_load<J>(ucG, Gn);
+                            n_rcp_ref += (unsigned long long)(j1 - j0);
+                        } else {
+                            mhp_sums<J, 3>(Gn, Ln, gx, gt, gs, sh, iam1, cu, cv, cw, cs_, ct, rtab, j0, j1);
+                            n_ex2_ref += (unsigned long long)(j1 - j0);
+                            n_rcp_ref += (unsigned long long)(j1 - j0);
+                        }
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) {
-                            en[jj] = mhf_eterm(noise, fmaf(A, Un[jj] - U[jj], f[jj]), y[jj], w[jj], nv0, nv1, nv2);
+                            const float Un = fmaf(r, Ln[jj] - Gn[jj], Gn[jj]);
+                            en[jj] = mhf_eterm(noise, fmaf(A, Un - U[jj], f[jj]), y[jj], w[jj], nv0, nv1, nv2);
                             if (jj & 1)
                                 p1 += en[jj] - e[jj];
                             else
@@ -423,12 +460,15 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
 #pragma unroll
                             for (int jj = 0; jj < J; ++jj) f[jj] = fmaf(dA, U[jj], f[jj]);
                         } else {
+                            const float r = c == 3 ? v : q[3];
 #pragma unroll
                             for (int jj = 0; jj < J; ++jj) {
-                                f[jj] = fmaf(A, Un[jj] - U[jj], f[jj]);
-                                U[jj] = Un[jj];
+                                const float Un = fmaf(r, Ln[jj] - Gn[jj], Gn[jj]);
+                                f[jj] = fmaf(A, Un - U[jj], f[jj]);
+                                U[jj] = Un;
                             }
-                            changed = true;
+                            if (cached && (mode & 1)) mhp_cache_store<J>(ucG, Gn);
+                            if (cached && (mode & 2)) mhp_cache_store<J>(ucL, Ln);
                         }
 #pragma unroll
                         for (int jj = 0; jj < J; ++jj) e[jj] = en[jj];
@@ -441,7 +481,6 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                         __syncwarp();
                     }
                 }
-                if (cached && changed) mhp_cache_store<J>(ucg + k * GP, U);
             }
             // ---- background (a, s_bg, r_bg, b)
             for (int qb = 0; qb < nbg; ++qb) {
@@ -460,8 +499,8 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                     } else if (qb == 3) {
                         fn = f[jj] + (v - bb);
                     } else {
-                        Un[jj] = mhp_bg_unit(__ldg(gx + jj) + xref, qb == 1 ? v : bs, qb == 2 ? v : br);
-                        fn = fmaf(ba, Un[jj] - Bv[jj], f[jj]);
+                        Gn[jj] = mhp_bg_unit(__ldg(gx + jj) + xref, qb == 1 ? v : bs, qb == 2 ? v : br);
+                        fn = fmaf(ba, Gn[jj] - Bv[jj], f[jj]);
                     }
                     en[jj] = mhf_eterm(noise, fn, y[jj], w[jj], nv0, nv1, nv2);
                     if (jj & 1)
@@ -478,8 +517,8 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                         } else if (qb == 3) {
                             f[jj] += v - bb;
                         } else {
-                            f[jj] = fmaf(ba, Un[jj] - Bv[jj], f[jj]);
-                            Bv[jj] = Un[jj];
+                            f[jj] = fmaf(ba, Gn[jj] - Bv[jj], f[jj]);
+                            Bv[jj] = Gn[jj];
                         }
                         e[jj] = en[jj];
                     }
@@ -524,10 +563,11 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
             if (lane == 0) {
                 const unsigned long long npts = (unsigned long long)jb.n;
                 atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
-                // SFU work of the proposals' profile rebuilds: an EX2 and an
-                // RCP per reflection and point (the two per-point reciprocals
-                // and the rebuild of the current profile are not counted)
-                atomicAdd(&jobs[slot].sfu_ops, 2ull * n_shape_ref * npts);
+                // SFU work of the proposals' profile rebuilds: an EX2 per
+                // reflection and point of a Gaussian part, an RCP of a
+                // Lorentzian part (the per-point reciprocals are not counted)
+                atomicAdd(&jobs[slot].sfu_ops, (n_ex2_ref + n_rcp_ref) * npts);
+                atomicAdd(&jobs[slot].ex2_part, n_ex2_ref * npts);
                 if (noise == NZ_MODEL) atomicAdd(&jobs[slot].var_ops, (unsigned long long)n_eval * npts * 2ull);
             }
         }

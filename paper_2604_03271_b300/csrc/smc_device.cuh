@@ -82,6 +82,7 @@ struct JobDev {
     // evaluations of in-support proposals, and SFU operations of the
     // shape-changing (centre, width) proposals among them
     unsigned long long point_evals, sfu_ops, var_ops;  // var_ops: LG2 + RCP of the model variance
+    unsigned long long ex2_part;  // the EX2 share of sfu_ops (App. D phase kernel)
 };
 
 // ---------------------------------------------------------------------------

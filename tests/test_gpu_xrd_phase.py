@@ -228,3 +228,27 @@ def test_paper_grid_sizes_sampled(ctx, n):
     e64 = np.array([oracle.energy_spec(spec, 3, v) for v in smp[idx]])
     e32 = ctx.energy(spec, 3, opts, smp[idx], precision=0)
     assert np.all(np.abs(e32 - e64) <= 2e-5 * (np.abs(e64) + spec.n))
+
+
+def test_thirteen_phases_without_the_profile_cache(ctx):
+    """13 phases (121 parameters, near the 128-component limit) of 5
+    reflections each: the profile parts of 13 phases exceed the kernel's
+    shared-memory cache, so every shape proposal rebuilds both parts.  One
+    FP32 stage against the oracle's on the same streams."""
+    rng = np.random.default_rng(21)
+    base = W.xrd_phase(6, n=600, k_min=13, k_max=13)
+    refs = [(sorted(rng.uniform(22.0, 78.0, 5).tolist()), rng.uniform(0.1, 1.0, 5).tolist()) for _ in range(13)]
+    spec = W.Spectrum(base.x, base.y, base.sigma, W.XRD_PHASE, 13, 13, W.BG_XRD_PV, 0, base.priors,
+                      truth={}, name="xrd-13", noise=W.NOISE_POISSON, refs=refs, phase_priors=base.phase_priors)
+    K = 13
+    opts = W.Options(particles=32, sweeps=2, seed=5)
+    u, E = oracle.init_particles(spec, K, opts, 32)
+    ok = np.isfinite(E)
+    u, E = u[ok], E[ok]
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, 1e-4, 3)
+    nat32, E32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u, E, step, 1e-4, 3, precision=0)
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
