@@ -182,6 +182,10 @@ def reference_arm(args, world: int, rank: int):
     # particle-point evaluations per spectrum of this workload (measured on the
     # GPU arm; stated constant so the reference arm needs no GPU)
     per_spec = UNITS_PER_SPECTRUM.get(name)
+    if per_spec is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no measured particle-point evaluations per "
+                                                              f"spectrum for workload {name}"}), flush=True)
+        return
     step_s = []
     rates = []
     for k in range(args.warmup + args.steps):
@@ -203,7 +207,8 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 9.7e11,
+UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 1.0e12,
+                      "xrd_phase_5000": 2.2e12, "xrd_phase_10000": 1.7e12,
                       "deconv3": 3.6e10, "deconv10": 8.2e11, "deconv30": 4.8e13}
 
 
