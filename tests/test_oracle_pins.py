@@ -572,6 +572,44 @@ def test_xrd_phase_reduces_to_gaussian_peak():
     assert oracle.xrd_phase(q, [mu], [1.0], mu - fwhm / 2) == pytest.approx(A / 2, rel=1e-12)
 
 
+def test_xrd_widths_at_ninety_degrees():
+    # at 2 theta = 90 degrees tan(x/2) = 1 and 1/cos(x/2) = sqrt(2), so the
+    # Caglioti width is S = sqrt(u - v + w) and the Lorentzian width W =
+    # s sqrt(2) + t (Eqs. of App. D written out by hand); one reflection just
+    # below 90 (x right of it: both widths scaled by alpha) and one just above
+    A, sh, al, r, u, v, w, sw, tw = 2.5, 0.01, 1.3, 0.4, 0.3, 0.1, 0.05, 0.2, 0.07
+    q = [A, sh, al, r, u, v, w, sw, tw]
+    S, Wl = math.sqrt(u - v + w), sw * math.sqrt(2.0) + tw
+
+    def pv(dx, a):
+        return (1 - r) * math.exp(-4 * math.log(2) * (dx / (a * S)) ** 2) + r / (1 + 4 * (dx / (a * Wl)) ** 2)
+
+    for ref, I in ((89.7, 0.8), (90.25, 1.7)):
+        mu = ref + sh
+        dx = 90.0 - mu
+        expect = A * I * pv(dx, al if dx >= 0 else 1.0)
+        assert oracle.xrd_phase(q, [ref], [I], 90.0) == pytest.approx(expect, rel=1e-13)
+    # a radicand below zero removes the Gaussian part only; a negative
+    # Lorentzian width removes the Lorentzian part only
+    q2 = list(q)
+    q2[5] = u + w + 0.2  # v: u - v + w < 0
+    dx = 90.0 - (89.7 + sh)
+    assert oracle.xrd_phase(q2, [89.7], [1.0], 90.0) == pytest.approx(
+        A * r / (1 + 4 * (dx / (al * Wl)) ** 2), rel=1e-13)
+    q3 = list(q)
+    q3[7], q3[8] = -0.2, 0.0
+    assert oracle.xrd_phase(q3, [89.7], [1.0], 90.0) == pytest.approx(
+        A * (1 - r) * math.exp(-4 * math.log(2) * (dx / (al * S)) ** 2), rel=1e-13)
+
+
+def test_xrd_background_closed_form():
+    # a V(x; 0, s, s, r) + b with the App. D pseudo-Voigt, at a few angles
+    a, sb, rb, b = 700.0, 8.0, 0.35, 40.0
+    for x in (0.0, 10.0, 33.3, 80.0):
+        v = (1 - rb) * math.exp(-4 * math.log(2) * (x / sb) ** 2) + rb / (1 + 4 * (x / sb) ** 2)
+        assert oracle.xrd_background([a, sb, rb, b], x) == pytest.approx(a * v + b, rel=1e-14)
+
+
 def test_xrd_poisson_log_z_of_fixed_background_is_exact():
     # no phase (K = 0) and every background parameter fixed: one stage, and
     # log Z = sum_i log Poisson(y_i; f_i) exactly
