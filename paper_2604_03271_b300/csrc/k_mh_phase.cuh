@@ -11,15 +11,18 @@
 // J consecutive grid points and keeps per point y, w, the model value f, the
 // energy term e, the current phase's unit profile U (A = 1) and the
 // background's unit PV; the centred angle, tan(x/2) and 1/cos(x/2) are re-read
-// (L1-resident) whenever a profile is rebuilt.  A proposal of the phase's
-// amplitude changes f by dA U; any other phase component rebuilds the unit
-// profile U' (per reflection and point one EX2 and one RCP, per point two
-// reciprocals) and changes f by A (U' - U).  Every proposal
-// recomputes the energy term at every point; dE is one group reduction.
-// Phases are not exchangeable and are never reordered.  When the launch
-// gives dynamic shared memory for K profiles per group, each phase's unit
-// profile is kept there across sweeps (rewritten when a shape proposal of
-// the phase is accepted), so a phase's block starts from it without a rebuild.
+// (L1-resident) whenever a profile is rebuilt.  The profile is (1 - r) Gs + r Ls
+// with Gs, Ls the intensity-weighted sums of the Gaussian and Lorentzian parts
+// over the phase's reflections.  A proposal of the phase's amplitude changes f
+// by dA U; any other phase component forms U' and changes f by A (U' - U).
+// When the launch gives dynamic shared memory for the two parts of K phases
+// per group, the parts are kept there across sweeps (rewritten when a shape
+// proposal that changed them is accepted): a phase's block starts without a
+// rebuild, r proposals remix the cached parts, u/v/w proposals rebuild Gs only
+// (one EX2 per reflection and point), s/t proposals Ls only (one RCP), d2theta
+// and alpha both; without that memory every shape proposal rebuilds both.
+// Every proposal recomputes the energy term at every point; dE is one group
+// reduction.  Phases are not exchangeable and are never reordered.
 //
 // Grids longer than one block's tile (32 G J points) run with CL = true: a
 // chain spans a thread-block cluster of C CTAs of G = 8 warps (C = 2..16, the
@@ -96,10 +99,6 @@ __device__ __forceinline__ float mhp_bg_unit(float xabs, float sbg, float rbg)
     return fmaf(rbg, l - g, g);
 }
 
-// Register budget (resident blocks per SM): the phase kernel holds eight
-// values per point plus a phase's nine components, so J = 4 gets up to 80
-// registers and J = 8 up to 128 (no spills with the groups of four or more
-// warps that grids of about a thousand points take).
 constexpr int MHP_MAX_CL = 16;  // CTAs per cluster at most (non-portable above 8)
 constexpr int MHP_CL_WARPS = 8;
 
@@ -216,6 +215,10 @@ __device__ __forceinline__ float mhp_chain_energy(GroupCtx<G> &g, const float (&
         return E;
 }
 
+// Register budget (resident blocks per SM): the phase kernel holds about nine
+// values per point plus a phase's nine components, so J = 4 gets up to 80
+// registers and J = 8 up to 128 (no spills with the groups of four or more
+// warps that grids of about a thousand points take).
 template <int J, int G, bool CL>
 struct MhpBounds {
     static constexpr int NT = CL ? 32 * G : MhThreads<G>::NT;
