@@ -59,3 +59,18 @@ def test_autotune_candidates_cover_every_bucket():
             c = A.candidates(fam, n)
             assert c and all(32 * G * J >= n for J, G in c)
             assert all(not (G == 16 and J > 8) for J, G in c)
+
+
+def test_phase_kernel_tiles_reach_the_paper_grids():
+    # the App. D phase kernel: single-block tiles up to 4096 points, then
+    # chains spread over clusters of 8-warp CTAs (G = 8 C, C <= 16) up to the
+    # paper's N = 10000 and beyond; every candidate covers its bucket
+    from paper_2604_03271_b300 import autotune as A
+    from paper_2604_03271_b300 import workloads as W
+    fam = W.XRD_PHASE | A.COUPLED
+    for n in A.BUCKETS_XRD + (1000, 5000, 10000, 16384):
+        c = A.candidates(fam, n)
+        assert c and all(32 * G * J >= n for J, G in c)
+        assert all(G <= 16 or (G % 8 == 0 and G // 8 <= 16) for J, G in c)
+        assert all(J in (4, 8) for J, G in c)
+    assert max(32 * 128 * J for J in (4, 8)) >= 32768
