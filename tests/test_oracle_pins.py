@@ -623,6 +623,20 @@ def test_xrd_poisson_log_z_of_fixed_background_is_exact():
     assert r["log_z"] == pytest.approx(exact, rel=1e-12)
 
 
+def test_xrd_poisson_zero_counts():
+    # points with y = 0 contribute log Poisson(0; f) = -f: the same exact
+    # fixed-background evidence with a tenth of the counts set to zero
+    spec = W.xrd_phase(7, n=120, k_min=0, k_max=0)
+    spec.y = spec.y.copy()
+    spec.y[::10] = 0.0
+    bg = [450.0, 9.0, 0.6, 30.0]
+    spec.comp_priors = [W.Prior(W.FIXED, v) for v in bg]
+    f = np.array([oracle.xrd_background(bg, xi) for xi in spec.x])
+    exact = float(np.sum(stats.poisson.logpmf(spec.y, f)))
+    r = oracle.run_job(spec, 0, W.Options(particles=16, sweeps=1, seed=1))
+    assert r["log_z"] == pytest.approx(exact, rel=1e-12)
+
+
 def test_xrd_evidence_k1_quadrature_amplitude():
     # rutile only, every parameter fixed but the intensity A ~ Gamma(4, rate):
     # Z = int Ga(A) p(D | A) dA by adaptive quadrature
