@@ -252,3 +252,25 @@ def test_thirteen_phases_without_the_profile_cache(ctx):
     assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
     E_true = oracle.energies(spec, K, opts, nat32)
     assert np.all(np.abs(E32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+def test_zero_counts(ctx):
+    """Poisson points with y = 0 (term f): FP64 and FP32 energies against the
+    oracle, and one FP32 Metropolis stage on the same streams."""
+    spec = W.xrd_phase(8, n=400, k_min=2, k_max=2)
+    spec.y = spec.y.copy()
+    spec.y[::7] = 0.0
+    K = 2
+    opts = W.Options(particles=64, sweeps=2, seed=3)
+    u, E_or = oracle.init_particles(spec, K, opts, 64)
+    nat64, E64 = ctx.prior(spec, K, opts, 64, precision=1)
+    np.testing.assert_allclose(E64, E_or, rtol=1e-12)
+    E32 = ctx.energy(spec, K, opts, u, precision=0)
+    assert np.all(np.abs(E32 - E_or) <= 2e-5 * (np.abs(E_or) + spec.n))
+    step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+    u_or, Es_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u[:32], E_or[:32], step, 1e-3, 2)
+    nat32, Es32, acc32, prop32 = ctx.mh_stage(spec, K, opts, u[:32], E_or[:32], step, 1e-3, 2, precision=0)
+    np.testing.assert_array_equal(prop32, prop_or)
+    assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, nat32)
+    assert np.all(np.abs(Es32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
