@@ -274,3 +274,33 @@ def test_zero_counts(ctx):
     assert np.abs(acc32 - acc_or).sum() <= 0.03 * prop_or.sum() + 3
     E_true = oracle.energies(spec, K, opts, nat32)
     assert np.all(np.abs(Es32 - E_true) <= 2e-5 * (np.abs(E_true) + spec.n))
+
+
+@pytest.mark.parametrize("bad", ["negative_intensity", "too_many_reflections", "empty_phase", "shirley_background",
+                                 "poisson_negative_count"])
+def test_invalid_phase_requests_are_rejected(ctx, bad):
+    from paper_2604_03271_b300 import api
+    spec = W.xrd_phase(4, n=200, k_min=1, k_max=2)
+    refs = [(list(p), list(i)) for p, i in spec.refs]
+    if bad == "negative_intensity":
+        refs[0][1][0] = -0.5
+    elif bad == "too_many_reflections":
+        refs[1] = (list(np.linspace(21.0, 79.0, 65)), [1.0] * 65)
+    elif bad == "empty_phase":
+        refs[0] = ([], [])
+    elif bad == "shirley_background":
+        spec.bg = W.BG_SHIRLEY
+    else:
+        spec.y = spec.y.copy()
+        spec.y[3] = -1.0
+    spec.refs = refs
+    if bad == "poisson_negative_count":
+        # the counts are checked on the device by the spectrum preparation:
+        # the request completes with every job marked invalid
+        r = ctx.run(spec, W.Options(particles=64, sweeps=2, seed=1))
+        assert r["status"] != api.SMC_OK
+        if r["job_status"] is not None:
+            assert np.all(r["job_status"] == api.SMC_EINVAL)
+        return
+    with pytest.raises(api.SmcError):
+        ctx.run(spec, W.Options(particles=64, sweeps=2, seed=1))
