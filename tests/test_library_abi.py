@@ -74,3 +74,35 @@ def test_phase_kernel_tiles_reach_the_paper_grids():
         assert all(G <= 16 or (G % 8 == 0 and G // 8 <= 16) for J, G in c)
         assert all(J in (4, 8) for J, G in c)
     assert max(32 * 128 * J for J in (4, 8)) >= 32768
+
+
+def test_binding_structs_match_the_headers(tmp_path):
+    # the ctypes mirrors of the C structs: same field names, offsets and sizes
+    # as a C compiler lays them out from include/*.h (gcc on the host)
+    import shutil
+    import subprocess
+    import ctypes as C
+    from paper_2604_03271_b300 import api
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no host C compiler")
+    pairs = [(api.Prior, "smc_prior"), (api.Priors, "smc_priors"), (api.CreateOpts, "smc_create_opts"),
+             (api.Options, "smc_options"), (api.Request, "smc_request"), (api.ResultView, "smc_result_view"),
+             (api.Profile, "smc_profile")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "smc.h"', '#include "smc_kernels.h"',
+             'int main(void) {']
+    expect = []
+    for cls, cname in pairs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(C.sizeof(cls))
+        for f in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            expect.append(getattr(cls, f[0]).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
