@@ -659,3 +659,17 @@ def test_xrd_evidence_k1_quadrature_amplitude():
     vals = [oracle.run_job(spec, 1, W.Options(particles=2000, sweeps=6, seed=s))["log_z"] for s in range(1, 6)]
     se = np.std(vals, ddof=1) / math.sqrt(len(vals))
     assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
+
+
+def test_generators_use_the_paper_true_parameters():
+    # the synthetic App. C and App. D inputs are built from the paper's printed
+    # true parameters (tests/golden/paper_true_parameters.txt)
+    rows = load_golden("paper_true_parameters.txt")
+    for K in (3, 10, 30):
+        tab = [tuple(float(v) for v in r[2:]) for r in rows if r[0] == f"deconv{K}"]
+        assert [int(r[1]) for r in rows if r[0] == f"deconv{K}"] == list(range(1, K + 1))
+        np.testing.assert_array_equal(np.array(tab), np.array(W.DECONV_TRUTH[K]))
+    ph = [tuple(float(v) for v in r[2:]) for r in rows if r[0] == "xrd_phase"]
+    np.testing.assert_array_equal(np.array(ph), np.array(W.XRD_TRUTH))
+    bg = [tuple(float(v) for v in r[1:]) for r in rows if r[0] == "xrd_bg"]
+    np.testing.assert_array_equal(np.array(bg[0]), np.array(W.XRD_BG_TRUTH))
