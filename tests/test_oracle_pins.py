@@ -673,3 +673,8 @@ def test_generators_use_the_paper_true_parameters():
     np.testing.assert_array_equal(np.array(ph), np.array(W.XRD_TRUTH))
     bg = [tuple(float(v) for v in r[1:]) for r in rows if r[0] == "xrd_bg"]
     np.testing.assert_array_equal(np.array(bg[0]), np.array(W.XRD_BG_TRUTH))
+    for r in (r for r in rows if r[0] == "deconv_grid"):
+        K, N, L, sd = int(r[1]), int(r[2]), float(r[3]), float(r[4])
+        assert W.DECONV_GRID[K] == (N, L, sd)
+        s = W.gaussian_deconvolution(K, 0)
+        assert s.n == N and s.x[0] == 0.0 and s.x[-1] == L and np.all(s.sigma == sd)
