@@ -678,3 +678,23 @@ def test_generators_use_the_paper_true_parameters():
         assert W.DECONV_GRID[K] == (N, L, sd)
         s = W.gaussian_deconvolution(K, 0)
         assert s.n == N and s.x[0] == 0.0 and s.x[-1] == L and np.all(s.sigma == sd)
+
+
+def test_xrd_priors_are_the_paper_table():
+    rows = {r[0]: r[1:] for r in load_golden("xrd_priors.txt")}
+    kinds = {"normal": W.NORMAL, "gamma": W.GAMMA, "uniform": W.UNIFORM}
+    spec = W.xrd_phase(2, n=500)
+    ph = spec.phase_priors  # (A, d2theta, alpha, r, u, v, w, s, t)
+    names = ["d2theta", "alpha", "r", "u", "v", "w", "s", "t"]
+    for name, p in zip(names, ph[1:]):
+        kind, p1, p2 = rows[name]
+        assert (p.kind, p.p1, p.p2) == (kinds[kind], float(p1), float(p2)), name
+    ymin, ymax = float(spec.y.min()), float(spec.y.max())
+    assert (ph[0].kind, ph[0].p1) == (W.GAMMA, 4.0) and ph[0].p2 == pytest.approx(4.0 / (ymax - ymin), rel=1e-15)
+    a, sbg, rbg, b = spec.priors.bg[:4]
+    assert (a.kind, a.p1) == (W.GAMMA, 2.0) and a.p2 == pytest.approx(1.0 / ymax, rel=1e-15)
+    for name, p in (("sigma_bg", sbg), ("r_bg", rbg)):
+        kind, p1, p2 = rows[name]
+        assert (p.kind, p.p1, p.p2) == (kinds[kind], float(p1), float(p2)), name
+    assert b.kind == W.UNIFORM
+    assert (b.p1, b.p2) == pytest.approx((ymin - math.sqrt(ymin), ymin + math.sqrt(ymin)), rel=1e-15)
