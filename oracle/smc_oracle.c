@@ -41,7 +41,10 @@
  *
  * Parity status: every function here is pinned by tests (closed forms,
  * brute force, published Philox answers, the linear-Gaussian evidence and
- * K = 1 quadrature).
+ * K = 1 quadrature).  The step-size rule and the waste-free branch are pinned
+ * against weighted moments computed independently (row replication, numpy's
+ * analytic-weight covariance), replays of standard stages, and the closed-form
+ * and quadrature evidences run in waste-free mode.
  */
 #include <math.h>
 #include <stdint.h>
