@@ -123,10 +123,22 @@ typedef struct {
     smc_prior phase[9];  /* SMC_XRD_PHASE: shared priors of the nine phase components */
 } smc_priors;
 
+/* How a batched FP32 run is launched (smc_create_opts.graph_mode).  Results
+ * are identical in every mode. */
+#define SMC_GRAPH_WHILE 0    /* one CUDA graph launch per run: a conditional while
+                                node over the tempering stages (the default)     */
+#define SMC_GRAPH_CHUNKED 1  /* host-replayed graphs of four stages each          */
+#define SMC_GRAPH_NONE 2     /* every kernel launched on the stream, no graphs:
+                                for kernel profilers and launch tracers, which do
+                                not see kernels inside conditional graph nodes   */
+
 typedef struct {
     int32_t device;           /* CUDA device ordinal                                 */
     size_t mem_budget_bytes;  /* device bytes the context may hold (0 = 80% of free) */
     void *cuda_stream;        /* cudaStream_t to run on (NULL = a private stream)    */
+    int32_t graph_mode;       /* SMC_GRAPH_WHILE / _CHUNKED / _NONE (else SMC_EINVAL);
+                                 the environment variable SMC_GRAPH_CHUNKED=1 at
+                                 creation selects SMC_GRAPH_CHUNKED as well        */
 } smc_create_opts;
 
 typedef struct {
@@ -134,10 +146,21 @@ typedef struct {
     double ess_target;    /* rho: next beta keeps ESS >= rho T (0 < rho < 1)       */
     int32_t sweeps;       /* n, Metropolis sweeps per stage                        */
     int32_t waste_free;   /* 1: resample ceil(T/n) chains, keep every sweep (Sec. II B 3) */
-    int32_t energy_fp64;  /* 1: plain FP64 path, one job per launch sequence       */
+    int32_t energy_fp64;  /* 0: FP32 energies, the batched fused kernels;
+                             1: the plain FP64 path, one job per launch sequence
+                                (thread-per-chain Metropolis, full FP64 energy per
+                                proposal);
+                             2: the same FP64 kernels with every FP64 job of the
+                                call in the same launches                        */
     uint64_t seed;        /* Philox key                                            */
     int32_t max_stages;   /* cap on tempering stages (SMC_EMAXSTAGES beyond)       */
     int32_t keep_samples; /* 1: copy the final particle set to the host            */
+    int32_t step_rule;    /* Metropolis step sizes (Sec. II B 4): 0 = lambda_j x the
+                             weighted population SD, lambda_j adapted from the last
+                             acceptance rate; 1 = predicted from the histories of
+                             beta and of the acceptance rates (1-D Gaussian
+                             acceptance model, weighted log-log regression of the
+                             implied target SD on beta, acceptance 0.44 aimed at) */
 } smc_options;
 
 /* One spectrum and its candidate range, for smc_run_batch / smc_submit. */
@@ -174,37 +197,65 @@ typedef struct {
     const float *samples;         /* [nK][n_samples][dim_max] natural values, or NULL  */
     int64_t n_samples;            /* particles per K in the final set                  */
     double latency_ms;            /* submit (or run start) to completion, host clock   */
+    int32_t selected_k;           /* the K of largest log Z among jobs with status
+                                     SMC_OK (smallest F(K), Sec. II A); log Z values
+                                     within 1e-12 of each other tie and the lower K
+                                     wins; -1 if no job succeeded                     */
 } smc_result_view;
 
-/* Create / destroy a context bound to one device.  A batched run is one CUDA
- * graph launch (a conditional while node over the tempering stages); with the
- * environment variable SMC_GRAPH_CHUNKED=1 at creation the context replays
- * four-stage graphs from the host instead (same results; for kernel profilers,
- * which cannot replay kernels inside conditional graphs). */
+/* Create / destroy a context bound to one device.  By default a batched run
+ * is one CUDA graph launch (a conditional while node over the tempering
+ * stages); opts->graph_mode selects host-replayed four-stage graphs or plain
+ * stream launches instead (same results).  opts may be NULL (device 0,
+ * defaults).  smc_destroy cancels queued requests, waits for the running ones
+ * and frees everything the context holds. */
 int smc_create(smc_ctx **out, const smc_create_opts *opts);
 int smc_destroy(smc_ctx *ctx);
 
-/* Blocking run of one spectrum over K = k_min..k_max.  x, y, sigma are host
- * arrays of n doubles, copied at call time.  *out receives a job handle whose
- * result is read with smc_result and freed with smc_release. */
+/* Blocking run of one spectrum over K = k_min..k_max: for every K, the
+ * tempered sequence of Eq. (9) from the prior (beta = 0) to the posterior
+ * (beta = 1) with the incremental weights of Eq. (10), the evidence of
+ * Eq. (11) and Metropolis moves (Sec. II B 4); then F(K) = -log Z (Eq. (3))
+ * and P(K|D) (Eq. (2)).  x, y, sigma are host arrays of n doubles (the grid,
+ * the data and the known per-point noise SD of the Gaussian likelihood),
+ * copied at call time; priors and opts are read at call time.  *out receives
+ * a job handle whose result is read with smc_result and freed with
+ * smc_release.  Returns SMC_EINVAL for invalid sizes or priors, SMC_ENOMEM if
+ * the request does not fit the context's budget. */
 int smc_run(smc_ctx *ctx, const double *x, const double *y, const double *sigma, int64_t n,
             int32_t k_min, int32_t k_max, int32_t family, int32_t bg, int32_t bg_degree,
             const smc_priors *priors, const smc_options *opts, smc_job *out);
 
-/* Blocking run of several spectra in one batched launch sequence (every
- * (spectrum, K) job advances in the same kernels).  If inputs_on_device is 1,
- * the x/y/sigma pointers are device pointers on the context's device.
- * out[i] receives the handle of reqs[i]. */
+/* Blocking run of several spectra (the computation of smc_run for each) in
+ * one batched launch sequence: every (spectrum, K) job advances in the same
+ * kernels.  If inputs_on_device is 1, the x/y/sigma pointers are device
+ * pointers on the context's device (checked by the preparation kernel).
+ * out[i] receives the handle of reqs[i].  On error no handle is returned. */
 int smc_run_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, int32_t inputs_on_device,
                   smc_job *out);
 
 /* Serving: enqueue a request (host arrays, copied at call time) and return at
- * once.  Requests are admitted by the memory budget and run with continuous
- * batching; their particle state stays on the device until retirement. */
+ * once.  Requests are admitted in arrival order as the memory budget and job
+ * slots free up, and run with continuous batching (requests admitted while
+ * others run join their launches); their particle state stays on the device
+ * until retirement.  A request larger than the whole budget finishes with
+ * status SMC_ENOMEM; one that does not fit yet waits. */
 int smc_submit(smc_ctx *ctx, const smc_request *req, smc_job *out);
-int smc_poll(smc_ctx *ctx, smc_job job, int32_t *done);
-int smc_wait(smc_ctx *ctx, smc_job job, double timeout_s);
+/* Enqueue `count` requests at once, in order (as count calls of smc_submit
+ * that no admission pass can separate).  On error none is enqueued. */
+int smc_submit_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, smc_job *out);
+int smc_poll(smc_ctx *ctx, smc_job job, int32_t *done);   /* *done = 1 once finished     */
+int smc_wait(smc_ctx *ctx, smc_job job, double timeout_s); /* < 0: no limit; SMC_ETIMEOUT */
 
+/* Device bytes a request would hold in this context while it runs (its
+ * spectrum, per-K particle state and results, with the context's tiles): the
+ * quantity admitted against mem_budget_bytes.  SMC_EINVAL for an invalid
+ * request. */
+int smc_request_bytes(smc_ctx *ctx, const smc_request *req, size_t *bytes);
+
+/* Result of a finished job: log Z per K (Eq. (11)), P(K|D) (Eq. (2)), the
+ * selected K, posterior summaries and (if keep_samples) the final particles.
+ * SMC_ENOTREADY while it runs. */
 int smc_result(smc_ctx *ctx, smc_job job, smc_result_view *out);
 int smc_release(smc_ctx *ctx, smc_job job);
 

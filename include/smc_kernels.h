@@ -52,9 +52,11 @@ int smc_k_reweight(smc_ctx *ctx, const double *E, int64_t T, double beta, double
  * most SMC_STATIC_MAX_PARTICLES particles (about 8 MiB, held by every GPU that
  * loads the library until exit).  Runs on the current device and cuda_stream
  * (NULL = default stream) and returns after the stream has finished the step.
- * T above the maximum returns SMC_EINVAL.  The first call on each device looks
- * up the scratch address (cudaGetSymbolAddress); make it before any stream
- * capture.  Calls share the scratch: calls that overlap on the GPU race. */
+ * T above the maximum returns SMC_EINVAL.  Each call outside a stream capture
+ * looks up the scratch address (cudaGetSymbolAddress) on the current device,
+ * so calls stay valid after a device reset; a call inside a capture reuses the
+ * last address found on that device, so make one call on each device before
+ * any capture.  Calls share the scratch: calls that overlap on the GPU race. */
 #define SMC_STATIC_MAX_PARTICLES (1 << 20)
 int smc_k_reweight_static(const void *E_dev, int64_t T, double beta, double rho,
                           int32_t precision, uint64_t *q_dev, double *delta, double *logz_inc,
@@ -106,7 +108,10 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
  *                point of every evaluated proposal (not part of sfu_ops);
  *   gather_bytes bytes the particle copy must move (read + write), per stage;
  *   resample_bytes bytes the resampler must move (q read, ancestors written);
- *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied. */
+ *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied;
+ *   max_batch_requests  the most requests (spectra) whose jobs advanced in
+ *                the same launches: > 1 shows that batched or served
+ *                requests shared kernels on the device. */
 typedef struct {
     int64_t launches[5];
     double ms[5];
@@ -114,6 +119,7 @@ typedef struct {
     double h2d_bytes, d2h_bytes;
     int64_t stages, jobs;
     double ex2_ops, rcp_ops, lg2_ops;
+    int64_t max_batch_requests;
 } smc_profile;
 
 int smc_profile_reset(smc_ctx *ctx, int32_t enable_events);

@@ -55,7 +55,7 @@ class Job(C.Structure):
                 ("noise", C.c_int32), ("noise_par", C.c_double * 3),
                 ("ref_pos", C.POINTER(C.c_double)), ("ref_int", C.POINTER(C.c_double)),
                 ("ref_off", C.POINTER(C.c_int32)), ("n_phase", C.c_int32),
-                ("phase", Prior * 9)]
+                ("phase", Prior * 9), ("step_rule", C.c_int32)]
 
 
 class Out(C.Structure):
@@ -104,6 +104,8 @@ def lib():
         _lib.orc_mh_stage.argtypes = [P(Job), P(d), P(d), i64, P(d), d, u32, P(d), P(d),
                                       P(C.c_int64), P(C.c_int64)]
         _lib.orc_step_sizes.argtypes = [P(Job), P(d), P(d), i64, P(d), P(d), P(d)]
+        _lib.orc_predict_step.argtypes = [P(d), d, d, d, d, d]
+        _lib.orc_predict_step.restype = d
         _lib.orc_run_job.argtypes = [P(Job), P(Out)]
         _lib.orc_run_job.restype = i32
     return _lib
@@ -262,6 +264,7 @@ class _JobHolder:
         j.particles, j.ess_target = opts.particles, opts.ess_target
         j.sweeps, j.waste_free = opts.sweeps, opts.waste_free
         j.seed, j.max_stages = opts.seed, opts.max_stages
+        j.step_rule = int(getattr(opts, "step_rule", 0))
         j.noise = getattr(spec, "noise", 0)
         for i, v in enumerate(getattr(spec, "noise_par", (0.0, 0.0, 0.0))):
             j.noise_par[i] = v
@@ -318,6 +321,16 @@ def step_sizes(spec, K: int, opts, u, w, acc_rate, lam):
     lib().orc_step_sizes(C.byref(h.job), _dp(u), _dp(w), u.shape[0],
                          None if rate is None else _dp(rate), _dp(lam), _dp(step))
     return step, lam
+
+
+def predict_step(hist, s_prev: float, acc: float, beta_prev: float, beta_next: float,
+                 sd_pop: float):
+    """The history step-size predictor for one component: returns the new step
+    and the updated history sums (W, X, Y, XX, XY)."""
+    h = _f64(hist).copy()
+    assert h.shape == (5,)
+    st = lib().orc_predict_step(_dp(h), s_prev, acc, beta_prev, beta_next, sd_pop)
+    return st, h
 
 
 def run_job(spec, K: int, opts, comp_priors=None, traces: bool = True) -> dict:

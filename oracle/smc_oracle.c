@@ -35,7 +35,8 @@
  *   - tempering: next beta by bisection on the effective sample size;
  *   - resampling: systematic, on integer-quantised weights (exact);
  *   - step sizes: lambda_j * weighted population SD, lambda_j adapted from
- *     the previous stage's acceptance rate;
+ *     the previous stage's acceptance rate; or (step_rule 1) predicted from
+ *     the histories of beta and of the acceptance rates (orc_predict_step);
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) with
  *     key = seed and counter = (draw, particle, stage, K).
  *
@@ -86,6 +87,7 @@ typedef struct {
     const int32_t *ref_off;
     int32_t n_phase;
     orc_prior phase[9]; /* shared priors of (A, d2theta, alpha, r, u, v, w, s, t) */
+    int32_t step_rule;  /* 0: lambda x weighted SD; 1: the history predictor */
 } orc_job;
 
 typedef struct {
@@ -677,12 +679,60 @@ int orc_mh_stage(const orc_job *job, const double *u_start, const double *E_star
     return ORC_OK;
 }
 
-/* Step sizes of the adaptive rule: lambda_j <- clamp(lambda_j exp(acc_j - 0.44),
- * 0.01, 10) when an acceptance rate is available, step_j = lambda_j *
- * max(weighted SD_j, 1e-9 (1 + |weighted mean_j|)).  Weights w need not be
- * normalised.  FIXED components get step 0. */
-void orc_step_sizes(const orc_job *job, const double *u, const double *w, int64_t T,
-                    const double *acc_rate, double *lam, double *step)
+/* Step-size predictor from the histories of the inverse temperatures and of
+ * a component's acceptance rates (Sec. II B 4 names such a predictor and
+ * cites it without printing it; the model below is the reading taken).
+ *   - For a one-dimensional Gaussian target of SD sigma and a Gaussian
+ *     random-walk proposal of SD s the acceptance rate is
+ *     (2/pi) atan(2 sigma / s); the rate a observed at step s (clamped to
+ *     [0.02, 0.98]) therefore estimates sigma = s tan(pi a / 2) / 2.
+ *   - log sigma is regressed on log beta over the stages run so far, each
+ *     older stage at half the weight of the next (h holds the weighted sums
+ *     W, X, Y, XX, XY and is updated in place); the slope is clamped to
+ *     [-1, 0], and is -1/2 (a likelihood-dominated posterior) while only
+ *     one stage has been seen.
+ *   - The fit is extrapolated to beta_next and the step is the one whose
+ *     acceptance rate there is 0.44: 2 sigma / tan(0.22 pi), kept within
+ *     [0.01, 10] x the weighted population SD sd_pop. */
+double orc_predict_step(double h[5], double s_prev, double acc, double beta_prev, double beta_next,
+                        double sd_pop)
+{
+    double a = acc;
+    if (a < 0.02) a = 0.02;
+    if (a > 0.98) a = 0.98;
+    double sig = s_prev * tan(M_PI * a / 2.0) / 2.0;
+    double x = log(beta_prev), y = log(sig);
+    for (int k = 0; k < 5; ++k) h[k] *= 0.5;
+    h[0] += 1.0;
+    h[1] += x;
+    h[2] += y;
+    h[3] += x * x;
+    h[4] += x * y;
+    double xm = h[1] / h[0], ym = h[2] / h[0];
+    double sxx = h[3] / h[0] - xm * xm, sxy = h[4] / h[0] - xm * ym;
+    double b = -0.5;
+    if (h[0] > 1.25 && sxx > 1e-12) {
+        b = sxy / sxx;
+        if (b < -1.0) b = -1.0;
+        if (b > 0.0) b = 0.0;
+    }
+    double st = 2.0 * exp(ym + b * (log(beta_next) - xm)) / tan(M_PI * 0.44 / 2.0);
+    if (st < 0.01 * sd_pop) st = 0.01 * sd_pop;
+    if (st > 10.0 * sd_pop) st = 10.0 * sd_pop;
+    return st;
+}
+
+/* Step sizes for the next Metropolis stage, from the population u[T][d] under
+ * the stage's incremental weights w (need not be normalised): sd_j = max(
+ * weighted SD_j, 1e-9 (1 + |weighted mean_j|)).  Without acceptance rates
+ * (the first stage), and always under step_rule 0: lambda_j <-
+ * clamp(lambda_j exp(acc_j - 0.44), 0.01, 10) when rates are given, step_j =
+ * lambda_j sd_j.  Under step_rule 1 with rates, history h[5 d] and the
+ * previous steps in step[]: step_j = orc_predict_step(h + 5 j, step_j,
+ * acc_j, beta_prev, beta_next, sd_j).  FIXED components get step 0. */
+void orc_step_sizes_ex(const orc_job *job, const double *u, const double *w, int64_t T,
+                       const double *acc_rate, double *lam, double *step, double *hist,
+                       double beta_prev, double beta_next)
 {
     ctx_t c;
     if (setup_ctx(&c, job) != ORC_OK) return;
@@ -706,6 +756,10 @@ void orc_step_sizes(const orc_job *job, const double *u, const double *w, int64_
         double sd = sqrt(v);
         double floor_sd = 1e-9 * (1.0 + fabs(m1));
         if (sd < floor_sd) sd = floor_sd;
+        if (acc_rate && job->step_rule == 1 && hist) {
+            step[j] = orc_predict_step(hist + 5 * j, step[j], acc_rate[j], beta_prev, beta_next, sd);
+            continue;
+        }
         if (acc_rate) {
             lam[j] *= exp(acc_rate[j] - 0.44);
             if (lam[j] < 0.01) lam[j] = 0.01;
@@ -715,6 +769,12 @@ void orc_step_sizes(const orc_job *job, const double *u, const double *w, int64_
     }
     free(c.pri);
     free(c.nat);
+}
+
+void orc_step_sizes(const orc_job *job, const double *u, const double *w, int64_t T,
+                    const double *acc_rate, double *lam, double *step)
+{
+    orc_step_sizes_ex(job, u, w, T, acc_rate, lam, step, NULL, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -766,13 +826,14 @@ int orc_run_job(const orc_job *job, orc_out *out)
     uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * Tc);
     int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * S);
     double *lam = (double *)malloc(sizeof(double) * dd);
+    double *hist = (double *)calloc(5 * dd, sizeof(double));
     double *step = (double *)malloc(sizeof(double) * dd);
     double *rate = (double *)malloc(sizeof(double) * dd);
     int64_t *acc = (int64_t *)calloc(dd, sizeof(int64_t));
     int64_t *prop = (int64_t *)calloc(dd, sizeof(int64_t));
     double *cur = (double *)malloc(sizeof(double) * dd);
     if (!u || !un || !us || !E || !En || !Es || !e || !w || !q || !anc || !lam || !step ||
-        !rate || !acc || !prop || !cur) {
+        !rate || !acc || !prop || !cur || !hist) {
         out->status = ORC_ENOMEM;
         goto done;
     }
@@ -826,12 +887,13 @@ int orc_run_job(const orc_job *job, orc_out *out)
         }
         /* -- evidence increment: log of the mean unnormalised weight (Eq. (11)) */
         logz += -delta * emin + log(sw / (double)Tc);
+        const double beta_prev = beta;
         beta = final_step ? 1.0 : beta + delta;
 
         /* -- step sizes from the reweighted population and last acceptance */
         if (stage > 1)
             for (int j = 0; j < d; ++j) rate[j] = prop[j] ? (double)acc[j] / (double)prop[j] : 0.44;
-        orc_step_sizes(job, u, w, Tc, stage > 1 ? rate : NULL, lam, step);
+        orc_step_sizes_ex(job, u, w, Tc, stage > 1 ? rate : NULL, lam, step, hist, beta_prev, beta);
         if (out->step_trace)
             for (int j = 0; j < d; ++j) out->step_trace[(size_t)stage * d + j] = step[j];
 
@@ -872,6 +934,6 @@ int orc_run_job(const orc_job *job, orc_out *out)
 done:
     free(c.pri); free(c.nat); free(u); free(un); free(us); free(E); free(En); free(Es);
     free(e); free(w); free(q); free(anc); free(lam); free(step); free(rate); free(acc);
-    free(prop); free(cur);
+    free(prop); free(cur); free(hist);
     return out->status;
 }

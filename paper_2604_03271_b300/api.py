@@ -38,14 +38,18 @@ class Priors(C.Structure):
                 ("phase", Prior * 9)]
 
 
+GRAPH_WHILE, GRAPH_CHUNKED, GRAPH_NONE = 0, 1, 2
+
+
 class CreateOpts(C.Structure):
-    _fields_ = [("device", C.c_int32), ("mem_budget_bytes", C.c_size_t), ("cuda_stream", C.c_void_p)]
+    _fields_ = [("device", C.c_int32), ("mem_budget_bytes", C.c_size_t), ("cuda_stream", C.c_void_p),
+                ("graph_mode", C.c_int32)]
 
 
 class Options(C.Structure):
     _fields_ = [("particles", C.c_int64), ("ess_target", C.c_double), ("sweeps", C.c_int32),
                 ("waste_free", C.c_int32), ("energy_fp64", C.c_int32), ("seed", C.c_uint64),
-                ("max_stages", C.c_int32), ("keep_samples", C.c_int32)]
+                ("max_stages", C.c_int32), ("keep_samples", C.c_int32), ("step_rule", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -63,7 +67,8 @@ class Profile(C.Structure):
                 ("sfu_ops", C.c_double), ("gather_bytes", C.c_double), ("resample_bytes", C.c_double),
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
                 ("stages", C.c_int64), ("jobs", C.c_int64),
-                ("ex2_ops", C.c_double), ("rcp_ops", C.c_double), ("lg2_ops", C.c_double)]
+                ("ex2_ops", C.c_double), ("rcp_ops", C.c_double), ("lg2_ops", C.c_double),
+                ("max_batch_requests", C.c_int64)]
 
 
 KERNEL_CLASSES = ("reweight", "resample", "gather", "metropolis", "stage_end")
@@ -75,7 +80,7 @@ class ResultView(C.Structure):
                 ("p_k", C.POINTER(C.c_double)), ("n_stages", C.POINTER(C.c_int32)),
                 ("job_status", C.POINTER(C.c_int32)), ("post_mean", C.POINTER(C.c_double)),
                 ("post_sd", C.POINTER(C.c_double)), ("samples", C.POINTER(C.c_float)),
-                ("n_samples", C.c_int64), ("latency_ms", C.c_double)]
+                ("n_samples", C.c_int64), ("latency_ms", C.c_double), ("selected_k", C.c_int32)]
 
 
 _lib = None
@@ -99,6 +104,8 @@ def lib():
     L.smc_run.argtypes = [vp, vp, vp, vp, i64, i32, i32, i32, i32, i32, P(Priors), P(Options), P(u64)]
     L.smc_run_batch.argtypes = [vp, P(Request), i32, i32, P(u64)]
     L.smc_submit.argtypes = [vp, P(Request), P(u64)]
+    L.smc_submit_batch.argtypes = [vp, P(Request), i32, P(u64)]
+    L.smc_request_bytes.argtypes = [vp, P(Request), P(C.c_size_t)]
     L.smc_poll.argtypes = [vp, u64, P(i32)]
     L.smc_wait.argtypes = [vp, u64, dbl]
     L.smc_result.argtypes = [vp, u64, P(ResultView)]
@@ -114,7 +121,8 @@ def lib():
     L.smc_profile_reset.argtypes = [vp, i32]
     L.smc_profile_read.argtypes = [vp, P(Profile)]
     L.smc_k_mufu_rate.argtypes = [i32, P(dbl), P(dbl), P(dbl), vp]
-    for f in ("smc_k_mufu_rate", "smc_profile_reset", "smc_profile_read", "smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_poll",
+    for f in ("smc_k_mufu_rate", "smc_profile_reset", "smc_profile_read", "smc_create", "smc_destroy", "smc_run", "smc_run_batch", "smc_submit", "smc_submit_batch",
+              "smc_request_bytes", "smc_poll",
               "smc_wait", "smc_result", "smc_release", "smc_k_philox", "smc_k_energy",
               "smc_k_prior", "smc_k_reweight", "smc_k_resample", "smc_k_mh_stage"):
         getattr(L, f).restype = C.c_int
@@ -164,7 +172,7 @@ class _Marshalled:
             self.pri.n_comp = len(spec.comp_priors)
         self.opts = Options(int(opts.particles), float(opts.ess_target), int(opts.sweeps),
                             int(opts.waste_free), int(opts.energy_fp64), int(opts.seed),
-                            int(opts.max_stages), int(keep_samples))
+                            int(opts.max_stages), int(keep_samples), int(getattr(opts, "step_rule", 0)))
         if device_arrays is None:
             self.x, self.y, self.s = _f64(spec.x), _f64(spec.y), _f64(spec.sigma)
             xp, yp, sp = self.x.ctypes.data, self.y.ctypes.data, self.s.ctypes.data
@@ -192,10 +200,11 @@ def _dim(family: int, K: int, bg: int, bg_degree: int) -> int:
 class Context:
     """One device context (smc_create / smc_destroy)."""
 
-    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: Optional[int] = None):
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: Optional[int] = None,
+                 graph_mode: int = GRAPH_WHILE):
         self._L = lib()
         h = C.c_void_p()
-        o = CreateOpts(device, mem_budget_bytes, stream)
+        o = CreateOpts(device, mem_budget_bytes, stream, graph_mode)
         _check(self._L.smc_create(C.byref(h), C.byref(o)), "smc_create")
         self.h = h
 
@@ -222,7 +231,8 @@ class Context:
         _check(self._L.smc_result(self.h, C.c_uint64(job), C.byref(v)), "smc_result")
         nK = v.k_max - v.k_min + 1
         ks = list(range(v.k_min, v.k_max + 1))
-        out = {"K": ks, "status": v.status, "latency_ms": v.latency_ms, "n_samples": v.n_samples}
+        out = {"K": ks, "status": v.status, "latency_ms": v.latency_ms, "n_samples": v.n_samples,
+               "argmax_k": v.selected_k if v.selected_k >= 0 else None}
         if not v.log_z:  # the request failed before producing results
             out.update({"log_z": None, "p_k": None, "n_stages": None, "job_status": None,
                         "post_mean": None, "post_sd": None, "argmax_k": None})
@@ -241,8 +251,6 @@ class Context:
         if v.samples:
             smp = np.ctypeslib.as_array(v.samples, (nK, v.n_samples, dm))
             out["samples"] = [smp[a, :, :dims[a]].copy() for a in range(nK)]
-        ok = [a for a in range(nK) if out["job_status"][a] == 0]
-        out["argmax_k"] = ks[max(ok, key=lambda a: log_z[a])] if ok else None
         return out
 
     def release(self, job: int):
@@ -250,7 +258,19 @@ class Context:
 
     # -- blocking runs -----------------------------------------------------
     def run(self, spec: W.Spectrum, opts: W.Options, keep_samples: bool = True) -> dict:
-        return self.run_batch([(spec, opts)], keep_samples=keep_samples)[0]
+        """One spectrum, blocking.  Known-sigma spectra go through smc_run (host
+        arrays); spectra that need smc_request's extra fields (model variance,
+        Poisson counts, App. D reflections) through smc_run_batch."""
+        if int(getattr(spec, "noise", 0)) != 0 or getattr(spec, "refs", None):
+            return self.run_batch([(spec, opts)], keep_samples=keep_samples)[0]
+        m = _Marshalled(spec, opts, None, 1 if keep_samples else 0)
+        job = C.c_uint64()
+        _check(self._L.smc_run(self.h, _ptr(m.x), _ptr(m.y), _ptr(m.s), spec.n, spec.k_min,
+                               spec.k_max, spec.family, spec.bg, spec.bg_degree, C.pointer(m.pri),
+                               C.pointer(m.opts), C.byref(job)), "smc_run")
+        out = self.result(int(job.value), spec)
+        self.release(int(job.value))
+        return out
 
     def run_batch(self, items: Sequence[tuple], keep_samples: bool = True,
                   device_arrays: Optional[Sequence] = None) -> List[dict]:
@@ -277,6 +297,21 @@ class Context:
         job = C.c_uint64()
         _check(self._L.smc_submit(self.h, C.byref(m.req), C.byref(job)), "smc_submit")
         return int(job.value)
+
+    def submit_batch(self, items: Sequence[tuple], keep_samples: bool = False) -> List[int]:
+        """Enqueue several (spectrum, options) pairs at once (smc_submit_batch)."""
+        ms = [_Marshalled(s, o, None, 1 if keep_samples else 0) for s, o in items]
+        reqs = (Request * len(ms))(*[m.req for m in ms])
+        jobs = (C.c_uint64 * len(ms))()
+        _check(self._L.smc_submit_batch(self.h, reqs, len(ms), jobs), "smc_submit_batch")
+        return [int(j) for j in jobs]
+
+    def request_bytes(self, spec: W.Spectrum, opts: W.Options, keep_samples: bool = False) -> int:
+        """Device bytes the request would hold while running (smc_request_bytes)."""
+        m = _Marshalled(spec, opts, None, 1 if keep_samples else 0)
+        b = C.c_size_t()
+        _check(self._L.smc_request_bytes(self.h, C.byref(m.req), C.byref(b)), "smc_request_bytes")
+        return int(b.value)
 
     def poll(self, job: int) -> bool:
         d = C.c_int32()
@@ -306,7 +341,7 @@ class Context:
                 "gather_bytes": p.gather_bytes, "resample_bytes": p.resample_bytes,
                 "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes,
                 "stages": p.stages, "jobs": p.jobs, "ex2_ops": p.ex2_ops, "rcp_ops": p.rcp_ops,
-                "lg2_ops": p.lg2_ops}
+                "lg2_ops": p.lg2_ops, "max_batch_requests": p.max_batch_requests}
 
     def mufu_rate(self, op: int, stream=None) -> dict:
         """Measured SFU throughput of EX2 (op 0), RCP (op 1) or LG2 (op 2) on this

@@ -41,6 +41,15 @@ void serve_loop(Ctx *cp)
 {
     Ctx &c = *cp;
     for (;;) {
+        // capacity as the engine sees it (c.used and the free slots change
+        // under c.mu only); admission below adds up everything it admits in
+        // one pass against this snapshot
+        size_t used_now = 0, slots_now = 0;
+        {
+            std::lock_guard<std::recursive_mutex> g(c.mu);
+            used_now = c.used;
+            slots_now = c.free_slots.size();
+        }
         std::vector<Request *> admitted;
         {
             std::unique_lock<std::mutex> lk(c.qmu);
@@ -48,25 +57,48 @@ void serve_loop(Ctx *cp)
                 c.qcv.wait(lk, [&] { return c.stop || !c.queue.empty(); });
             }
             if (c.stop && c.queue.empty() && c.running.empty()) return;
+            size_t pending = 0, pending_slots = 0;
             while (!c.queue.empty()) {
                 Request *r = c.queue.front();
                 const size_t need = request_bytes(*r);
-                if (need > c.budget) {
+                const size_t nK = (size_t)(r->k_max - r->k_min + 1);
+                if (need > c.budget || nK > (size_t)MAX_SLOTS) {
                     c.queue.pop_front();
                     finish_failed(c, r, SMC_ENOMEM);
                     c.done_cv.notify_all();
                     continue;
                 }
-                if (c.used + need > c.budget) break;
+                if (used_now + pending + need > c.budget || pending_slots + nK > slots_now) break;
                 c.queue.pop_front();
                 admitted.push_back(r);
+                pending += need;
+                pending_slots += nK;
+            }
+            if (admitted.empty() && c.running.empty() && !c.queue.empty()) {
+                // nothing of this loop holds memory, yet the head request does
+                // not fit: memory held outside the serving loop must be
+                // released first (smc_release); wait for a new event
+                c.qcv.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
             }
         }
         std::vector<Request *> finished;
+        bool requeued = false;
         {
             std::lock_guard<std::recursive_mutex> g(c.mu);
-            for (Request *r : admitted) {
+            for (size_t i = 0; i < admitted.size(); ++i) {
+                Request *r = admitted[i];
                 int st = setup_request(c, *r);
+                if (st == ST_NO_ROOM) {
+                    // budget or job slots taken meanwhile (by calls outside the
+                    // serving loop): this request and the later admitted ones
+                    // go back to the head of the queue, in order, and wait
+                    free_request_device(c, *r);
+                    std::lock_guard<std::mutex> lk(c.qmu);
+                    for (size_t k = admitted.size(); k-- > i;) c.queue.push_front(admitted[k]);
+                    requeued = true;
+                    break;
+                }
                 if (st != SMC_OK) {
                     free_request_device(c, *r);
                     std::lock_guard<std::mutex> lk(c.qmu);
@@ -121,6 +153,11 @@ void serve_loop(Ctx *cp)
             std::lock_guard<std::mutex> lk(c.qmu);
             c.done_cv.notify_all();
         }
+        if (requeued && c.running.empty()) {
+            // nothing of this loop runs to free memory: wait for a new event
+            std::unique_lock<std::mutex> lk(c.qmu);
+            c.qcv.wait_for(lk, std::chrono::milliseconds(20));
+        }
     }
 }
 
@@ -151,6 +188,8 @@ int smc_create(smc_ctx **out, const smc_create_opts *opts)
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return SMC_ECUDA;
     const int dev = opts ? opts->device : 0;
     if (dev < 0 || dev >= ndev) return SMC_EINVAL;
+    if (opts && (opts->graph_mode < SMC_GRAPH_WHILE || opts->graph_mode > SMC_GRAPH_NONE))
+        return SMC_EINVAL;
     CKS(cudaSetDevice(dev));
     smc_ctx *ctx = new smc_ctx();
     Ctx &c = ctx->c;
@@ -167,9 +206,12 @@ int smc_create(smc_ctx **out, const smc_create_opts *opts)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c.budget = (opts && opts->mem_budget_bytes) ? opts->mem_budget_bytes : (size_t)(0.8 * fr);
-    // SMC_GRAPH_CHUNKED=1: replay four-stage graphs instead of one graph with a
-    // conditional while node (kernel profilers cannot replay kernels of the latter)
-    if (const char *g = getenv("SMC_GRAPH_CHUNKED")) c.no_while_graph = g[0] == '1';
+    c.graph_mode = opts ? opts->graph_mode : SMC_GRAPH_WHILE;
+    // SMC_GRAPH_CHUNKED=1 in the environment: replay four-stage graphs instead of
+    // one graph with a conditional while node (kernel profilers cannot replay
+    // kernels of the latter)
+    if (const char *g = getenv("SMC_GRAPH_CHUNKED"))
+        if (g[0] == '1' && c.graph_mode == SMC_GRAPH_WHILE) c.graph_mode = SMC_GRAPH_CHUNKED;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -248,7 +290,7 @@ int smc_run_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, int32_t 
         r->t_submit = t0;
         rs.push_back(r);
         st = setup_request(c, *r);
-        if (st != SMC_OK) return cleanup(st);
+        if (st != SMC_OK) return cleanup(st == ST_NO_ROOM ? SMC_ENOMEM : st);
         r->state = 1;
     }
     int st = run_requests(c, rs);
@@ -299,6 +341,61 @@ int smc_submit(smc_ctx *ctx, const smc_request *req, smc_job *out)
     }
     c.qcv.notify_all();
     *out = r->id;
+    return SMC_OK;
+}
+
+int smc_submit_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, smc_job *out)
+{
+    if (!ctx || !reqs || count < 1 || !out) return SMC_EINVAL;
+    Ctx &c = ctx->c;
+    std::vector<Request *> rs;
+    for (int i = 0; i < count; ++i) {
+        Request *r = nullptr;
+        const int st = make_request(c, reqs[i], false, r);
+        if (st != SMC_OK) {
+            for (Request *q : rs) delete q;
+            return st;
+        }
+        rs.push_back(r);
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::recursive_mutex> g(c.mu);
+        {
+            std::lock_guard<std::mutex> lk(c.qmu);
+            for (Request *r : rs) {
+                r->t_submit = t0;
+                r->id = c.next_id++;
+                c.reqs[r->id] = r;
+            }
+        }
+        if (!c.worker_started) {
+            c.worker_started = true;
+            c.worker = std::thread([&c] {
+                cudaSetDevice(c.device);
+                serve_loop(&c);
+            });
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(c.qmu);
+        for (Request *r : rs) c.queue.push_back(r);
+    }
+    c.qcv.notify_all();
+    for (int i = 0; i < count; ++i) out[i] = rs[i]->id;
+    return SMC_OK;
+}
+
+int smc_request_bytes(smc_ctx *ctx, const smc_request *req, size_t *bytes)
+{
+    if (!ctx || !req || !bytes) return SMC_EINVAL;
+    Ctx &c = ctx->c;
+    std::lock_guard<std::recursive_mutex> g(c.mu);  // the tile table
+    Request *r = nullptr;
+    const int st = make_request(c, *req, false, r);
+    if (st != SMC_OK) return st;
+    *bytes = request_bytes(*r);
+    delete r;
     return SMC_OK;
 }
 
@@ -355,6 +452,7 @@ int smc_result(smc_ctx *ctx, smc_job job, smc_result_view *out)
     v.samples = r->samples.empty() ? nullptr : r->samples.data();
     v.n_samples = r->n_samples;
     v.latency_ms = r->latency_ms;
+    v.selected_k = r->selected_k;
     *out = v;
     return SMC_OK;
 }
@@ -409,7 +507,7 @@ static int single_job(smc_ctx *ctx, const smc_request *spec, int32_t K, int32_t 
         delete r;
         r = nullptr;
     }
-    return st;
+    return st == ST_NO_ROOM ? SMC_ENOMEM : st;
 }
 
 // natural value -> sampling coordinate of component j (centres shifted for FP32 jobs)

@@ -159,6 +159,8 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     if (rq.k_min < 0 || rq.k_min > rq.k_max || rq.k_max > SMC_MAX_K) return SMC_EINVAL;
     if (job_dim(rq.family, rq.k_max, rq.bg, rq.bg_degree) > SMC_MAX_DIM) return SMC_EINVAL;
     if (o.particles < 2 || o.particles > (1 << 24) || o.sweeps < 1 || o.sweeps > 100000) return SMC_EINVAL;
+    if (o.energy_fp64 < 0 || o.energy_fp64 > 2) return SMC_EINVAL;
+    if (o.step_rule < 0 || o.step_rule > 1) return SMC_EINVAL;
     if (!(o.ess_target > 0.0 && o.ess_target < 1.0) || o.max_stages < 1) return SMC_EINVAL;
     if (o.waste_free) {
         const int64_t S = (o.particles + o.sweeps - 1) / o.sweeps;
@@ -286,7 +288,7 @@ static SpecLayout spec_layout(const Request &r, int64_t T_out)
 }
 
 struct JobLayout {
-    size_t th, E, ths, Es, w64, rwpart, q, anc, lam, step, stepf, acc, prop, pri, total;
+    size_t th, E, ths, Es, w64, rwpart, q, anc, lam, step, stepf, acc, prop, pri, hist, total;
 };
 
 static JobLayout job_layout(int d, int64_t T, int64_t S, bool fp64)
@@ -308,6 +310,7 @@ static JobLayout job_layout(int d, int64_t T, int64_t S, bool fp64)
     L.acc = o;  o += al(dd * 8);
     L.prop = o; o += al(dd * 8);
     L.pri = o;  o += al(dd * sizeof(PriorDev));
+    L.hist = o; o += al(5 * dd * 8);
     L.total = o;
     return L;
 }
@@ -387,12 +390,12 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         S = S_override > 0 ? S_override : T_override;
     }
     const int nK = r.k_max - r.k_min + 1;
-    if ((int)c.free_slots.size() < nK) return SMC_ENOMEM;
+    if ((int)c.free_slots.size() < nK) return ST_NO_ROOM;
     const SpecLayout SL = spec_layout(r, T);
     size_t need = SL.total;
     for (int K = r.k_min; K <= r.k_max; ++K)
         need += job_layout(job_dim(r.family, K, r.bg, r.bg_degree), T, S, r.fp64).total;
-    if (c.used + need > c.budget) return SMC_ENOMEM;
+    if (c.used + need > c.budget) return ST_NO_ROOM;
 
     char *sa = nullptr;
     CK(cudaMallocAsync((void **)&sa, SL.total, c.stream));
@@ -460,6 +463,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         CK(cudaMemcpyAsync(ja + JL.lam, lam.data(), 8 * lam.size(), cudaMemcpyHostToDevice, c.stream));
         CK(cudaMemsetAsync(ja + JL.acc, 0, 8 * std::max(d, 1), c.stream));
         CK(cudaMemsetAsync(ja + JL.prop, 0, 8 * std::max(d, 1), c.stream));
+        CK(cudaMemsetAsync(ja + JL.hist, 0, 5 * 8 * std::max(d, 1), c.stream));
         JobDev jb{};
         jb.xc = r.sd.xc;
         jb.wt = r.sd.wt;
@@ -520,6 +524,8 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.acc = (unsigned long long *)(ja + JL.acc);
         jb.prop = (unsigned long long *)(ja + JL.prop);
         jb.pri = (const PriorDev *)(ja + JL.pri);
+        jb.hist = (double *)(ja + JL.hist);
+        jb.step_rule = r.opts.step_rule;
         jb.beta = 0.0;
         jb.rho = r.opts.ess_target;
         jb.stage = 0;
@@ -554,6 +560,7 @@ struct Bucket {
 };
 
 struct Plan {
+    int nreq = 0;  // requests with FP32 jobs in the plan
     std::vector<int> all;
     std::vector<Bucket> buckets;
     std::vector<size_t> boff;
@@ -569,6 +576,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
 {
     for (Request *r : reqs) {
         if (r->fp64) continue;
+        if (!r->slots.empty()) P.nreq += 1;
         for (int sl : r->slots) {
             P.all.push_back(sl);
             const JobDev &jb = c.h_jobs[sl];
@@ -588,6 +596,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
         }
     }
     if (P.all.empty()) return SMC_OK;
+    c.prof.max_batch_requests = std::max<int64_t>(c.prof.max_batch_requests, P.nreq);
     // costliest chains first inside each bucket (dynamic scheduling drains them first)
     for (Bucket &b : P.buckets)
         std::stable_sort(b.slots.begin(), b.slots.end(), [&](int a, int z) {
@@ -711,7 +720,7 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
     int st = build_plan(c, reqs, P);
     if (st != SMC_OK || P.all.empty()) return st;
     // without per-kernel events the whole run is one graph launch
-    if (!c.prof_events && !c.no_while_graph && run_whole_graph(c, P, &st)) return st;
+    if (!c.prof_events && c.graph_mode == SMC_GRAPH_WHILE && run_whole_graph(c, P, &st)) return st;
     // capture CHUNK stages into a CUDA graph and replay it until no job is active
     std::vector<cudaEvent_t> ev;
     if (c.prof_events) {
@@ -720,8 +729,8 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
     }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    bool use_graph = true;
-    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    bool use_graph = c.graph_mode != SMC_GRAPH_NONE;
+    if (use_graph && cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < CHUNK && e == cudaSuccess; ++k)
             e = iteration(c, P, ev.empty() ? nullptr : &ev[6 * k], k);
@@ -779,25 +788,34 @@ static int run_fp32(Ctx &c, std::vector<Request *> &reqs)
     return status;
 }
 
-static int run_fp64(Ctx &c, Request &r)
+// FP64 jobs: the plain kernels (thread-per-chain Metropolis with a full FP64
+// energy per proposal), one stage per launch sequence, the host checking
+// completion after every stage.  The plain path passes one job at a time;
+// the batched FP64 mode (energy_fp64 = 2) passes every FP64 job of the batch.
+static int run_fp64_list(Ctx &c, const std::vector<int> &list)
 {
-    // plain path: one job at a time, one launch sequence per stage, the host
-    // checks completion after every stage
-    int *list = c.d_lists;
-    for (int sl : r.slots) {
-        CK(cudaMemcpyAsync(list, &sl, 4, cudaMemcpyHostToDevice, c.stream));
+    if (list.empty()) return SMC_OK;
+    if ((int)list.size() > LIST_AREA) return SMC_ENOMEM;
+    int64_t max_T = 0, max_elems = 0, max_S = 0;
+    int max_stages = 1;
+    for (int sl : list) {
         const JobDev &jb = c.h_jobs[sl];
-        const int64_t elems = (int64_t)jb.S * (jb.d + 1);
-        for (int it = 0; it < jb.max_stages + 2; ++it) {
-            CK(launch_reweight(c.d_jobs, list, 1, true, jb.T, c.stream));
-            CK(launch_resample(c.d_jobs, list, 1, c.stream));
-            CK(launch_gather(c.d_jobs, list, 1, elems, true, c.stream));
-            CK(launch_mh_plain(c.d_jobs, list, 1, jb.S, c.stream));
-            CK(launch_stage_end(c.d_jobs, list, 1, c.d_nactive, c.h_nactive_dev, c.stream));
-            CK(cudaStreamSynchronize(c.stream));
-            c.prof.stages += 1;
-            if (*(volatile int *)c.h_nactive == 0) break;
-        }
+        max_T = std::max<int64_t>(max_T, jb.T);
+        max_S = std::max<int64_t>(max_S, jb.S);
+        max_elems = std::max<int64_t>(max_elems, (int64_t)jb.S * (jb.d + 1));
+        max_stages = std::max(max_stages, jb.max_stages);
+    }
+    const int n = (int)list.size();
+    CK(cudaMemcpyAsync(c.d_lists, list.data(), 4 * list.size(), cudaMemcpyHostToDevice, c.stream));
+    for (int it = 0; it < max_stages + 2; ++it) {
+        CK(launch_reweight(c.d_jobs, c.d_lists, n, true, max_T, c.stream));
+        CK(launch_resample(c.d_jobs, c.d_lists, n, c.stream));
+        CK(launch_gather(c.d_jobs, c.d_lists, n, max_elems, true, c.stream));
+        CK(launch_mh_plain(c.d_jobs, c.d_lists, n, (int)max_S, c.stream));
+        CK(launch_stage_end(c.d_jobs, c.d_lists, n, c.d_nactive, c.h_nactive_dev, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+        c.prof.stages += 1;
+        if (*(volatile int *)c.h_nactive == 0) break;
     }
     return SMC_OK;
 }
@@ -806,11 +824,20 @@ int run_requests(Ctx &c, std::vector<Request *> &reqs)
 {
     int st = run_fp32(c, reqs);
     if (st != SMC_OK) return st;
-    for (Request *r : reqs)
-        if (r->fp64) {
-            st = run_fp64(c, *r);
+    std::vector<int> batched;
+    for (Request *r : reqs) {
+        if (!r->fp64) continue;
+        if (r->opts.energy_fp64 == 2) {
+            batched.insert(batched.end(), r->slots.begin(), r->slots.end());
+            continue;
+        }
+        for (int sl : r->slots) {  // the plain path: one job per launch sequence
+            st = run_fp64_list(c, std::vector<int>{sl});
             if (st != SMC_OK) return st;
         }
+    }
+    st = run_fp64_list(c, batched);
+    if (st != SMC_OK) return st;
     return finalize_requests(c, reqs);
 }
 
@@ -883,6 +910,18 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             r->n_stages[a] = jobs[a].stage;
             r->job_status[a] = jobs[a].status;
             if (jobs[a].status != 0 && r->status == SMC_OK) r->status = jobs[a].status;
+        }
+        // model selection: the K of smallest free energy F = -log Z (Sec. II A);
+        // scanning K upwards and moving only on a gain beyond 1e-12 keeps the
+        // lower K on ties
+        r->selected_k = -1;
+        double best = 0.0;
+        for (int a = 0; a < nK; ++a) {
+            if (r->job_status[a] != SMC_OK || !std::isfinite(r->log_z[a])) continue;
+            if (r->selected_k < 0 || r->log_z[a] > best + 1e-12) {
+                r->selected_k = r->k_min + a;
+                best = r->log_z[a];
+            }
         }
         free_request_device(c, *r);
         r->state = 2;

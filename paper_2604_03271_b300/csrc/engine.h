@@ -29,6 +29,10 @@ constexpr int MAX_SLOTS = 4096;
 constexpr int LIST_AREA = 24 * MAX_SLOTS;  // ints of the device slot-list area
 constexpr int CHUNK = 4;                   // stages per CUDA-graph launch
 constexpr int NACTIVE_SLOTS = 64;
+// internal status of setup_request: the context's memory budget or its job
+// slots are taken for now (the serving loop retries later; the blocking entry
+// points report SMC_ENOMEM)
+constexpr int ST_NO_ROOM = 1000;
 
 struct Tile {
     int J, G;
@@ -65,6 +69,7 @@ struct Request {
     int64_t n_samples = 0;
     std::vector<double> log_z, p_k, mean, sdv;
     std::vector<int32_t> n_stages, job_status;
+    int32_t selected_k = -1;      // argmax of log Z over successful jobs, ties to the lower K
     std::vector<float> samples;
     std::chrono::steady_clock::time_point t_submit, t_done;
     double latency_ms = 0.0;
@@ -88,7 +93,7 @@ struct Ctx {
     // profiling (per-kernel events need the chunked graph: conditional bodies
     // take no event nodes)
     bool prof_events = false;
-    bool no_while_graph = false;
+    int graph_mode = SMC_GRAPH_WHILE;  // smc_create_opts.graph_mode
     smc_profile prof{};
     std::map<smc_job, Request *> reqs;
     uint64_t next_id = 1;

@@ -10,7 +10,11 @@
 // which is E(theta') - E(theta) of the Gaussian energy (App. C Eq. (C2)).  The
 // lanes keep h_i = w_i / 2 and R_i = -w_i r_i instead of w_i and r_i, so a point
 // costs two FMAs, dE = sum_i D_i (h_i D_i + R_i), and an accepted change D
-// updates R_i += 2 h_i D_i.
+// updates R_i += 2 h_i D_i.  A lane's points are held and updated in pairs by
+// the packed FP32 instructions (f32x2: two results per issue slot), because
+// the kernel is bound by instruction issue; each half of a packed operation
+// is the scalar IEEE operation, and the two halves are the even and odd
+// points of the lane's split accumulation.
 // Within a peak's block of components the unit-amplitude shapes of the peak
 // (the Gaussian and Lorentzian parts) are cached per point, so amplitude and
 // mixing-ratio proposals need no transcendental at all and centre / width
@@ -24,6 +28,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "f32x2.cuh"
 #include "kernels.h"
 
 namespace smc {
@@ -193,10 +198,52 @@ struct MhBounds {
                       : 2;
 };
 
+// Packed form of shape() for two grid points: the argument in f32x2
+// arithmetic, one MUFU operation per point and transcendental.  Each half is
+// bit-identical to shape() of that point.
+template <int FAM>
+__device__ __forceinline__ void shape2(f2 x, f2 sc, f2 nmsc, f2 &S0, f2 &S1)
+{
+    const f2 t = fma2(x, sc, nmsc);
+    const f2 t2 = mul2(t, t);
+    if (FAM == FAM_GAUSS) {
+        S0 = mk2(ex2_approx(-lo2(t2)), ex2_approx(-hi2(t2)));
+    } else {
+        const f2 q = add2(t2, splat2(1.0f));
+        const f2 L = mk2(rcp_approx(lo2(q)), rcp_approx(hi2(q)));
+        if (FAM == FAM_LORENTZ) {
+            S0 = L;
+        } else {
+            S0 = sub2(mk2(ex2_approx(-lo2(t2)), ex2_approx(-hi2(t2))), L);  // G - L
+            S1 = L;
+        }
+    }
+}
+
+__device__ __forceinline__ f2 neg2(f2 a) { return mul2(a, splat2(-1.0f)); }
+
+// group_energy() on packed points (pair p holds points 2p and 2p + 1; the
+// compensated sum runs over them in that order)
+template <int JP, int G>
+__device__ __forceinline__ float group_energy2(GroupCtx<G> &g, const f2 *w2, const f2 *r2)
+{
+    float w[2 * JP], r[2 * JP];
+#pragma unroll
+    for (int p = 0; p < JP; ++p) {
+        w[2 * p] = lo2(w2[p]);
+        w[2 * p + 1] = hi2(w2[p]);
+        r[2 * p] = lo2(r2[p]);
+        r[2 * p + 1] = hi2(r2[p]);
+    }
+    return group_energy<2 * JP, G>(g, w, r);
+}
+
 template <int FAM, int J, int G>
 __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
     k_mh(JobDev *__restrict__ jobs, const int *__restrict__ slots, int nslots)
 {
+    static_assert(J % 2 == 0, "a lane's points are processed in packed pairs");
+    constexpr int JP = J / 2;
     constexpr int NT = MhThreads<G>::NT;
     __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
@@ -267,50 +314,53 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
         }
         __syncwarp();
 
-        // ---- grid points of this lane and the residual r = y - f(theta)
-        float x[J], w[J], r[J], S0[J], S1[J], N0[J], N1[J];
+        // ---- grid points of this lane, in pairs (points 2p and 2p + 1 of the
+        // lane), and the residual r = y - f(theta)
+        f2 x[JP], w[JP], r[JP], S0[JP], S1[JP], N0[JP], N1[JP];
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-            const int i = base + jj * stride;
-            x[jj] = __ldg(jb.xc + i);
-            w[jj] = __ldg(jb.wt + i);
-            r[jj] = __ldg(jb.y + i);
+        for (int p = 0; p < JP; ++p) {
+            const int i0 = base + 2 * p * stride, i1 = i0 + stride;
+            x[p] = mk2(__ldg(jb.xc + i0), __ldg(jb.xc + i1));
+            w[p] = mk2(__ldg(jb.wt + i0), __ldg(jb.wt + i1));
+            r[p] = mk2(__ldg(jb.y + i0), __ldg(jb.y + i1));
         }
         for (int k = 0; k < K; ++k) {
             const int j0 = k * P;
             const float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
             const float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
             const float sc = sc2_of<FAM>(wd, wprec);
+            const f2 scv = splat2(sc), nmsc = splat2(-mu * sc), nA = splat2(-A), et = splat2(eta);
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) {
-                float a0, a1 = 0.0f;
-                shape<FAM>(x[jj], mu, sc, a0, a1);
-                r[jj] -= A * unit_of<FAM>(a0, a1, eta);
+            for (int p = 0; p < JP; ++p) {
+                f2 a0, a1 = splat2(0.0f);
+                shape2<FAM>(x[p], scv, nmsc, a0, a1);
+                r[p] = fma2(nA, FAM == FAM_PV ? fma2(et, a0, a1) : a0, r[p]);
             }
         }
         if (nbg > 0) {
             // Chebyshev terms by the three-term recurrence, carried across q
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) {
-                N0[jj] = __ldg(jb.ts + base + jj * stride);  // t
-                S0[jj] = 1.0f;                               // T_{q-1}
-                S1[jj] = N0[jj];                             // T_q (q = 1)
+            for (int p = 0; p < JP; ++p) {
+                const int i0 = base + 2 * p * stride;
+                N0[p] = mk2(__ldg(jb.ts + i0), __ldg(jb.ts + i0 + stride));  // t
+                S0[p] = splat2(1.0f);                                         // T_{q-1}
+                S1[p] = N0[p];                                                // T_q (q = 1)
             }
             for (int q = 0; q < nbg; ++q) {
-                const float cq = cs.nat[K * P + q];
+                const f2 ncq = splat2(-cs.nat[K * P + q]);
 #pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    float tq;
+                for (int p = 0; p < JP; ++p) {
+                    f2 tq;
                     if (q == 0) {
-                        tq = 1.0f;
+                        tq = splat2(1.0f);
                     } else if (q == 1) {
-                        tq = N0[jj];
+                        tq = N0[p];
                     } else {
-                        tq = fmaf(2.0f * N0[jj], S1[jj], -S0[jj]);
-                        S0[jj] = S1[jj];
-                        S1[jj] = tq;
+                        tq = fma2(add2(N0[p], N0[p]), S1[p], neg2(S0[p]));
+                        S0[p] = S1[p];
+                        S1[p] = tq;
                     }
-                    r[jj] = fmaf(-cq, tq, r[jj]);
+                    r[p] = fma2(ncq, tq, r[p]);
                 }
             }
         }
@@ -319,9 +369,9 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
         // dE = 1/2 sum w D (D - 2 r) = sum D (h D + R) and, on acceptance,
         // r -> r - D is R -> R + 2 h D
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-            r[jj] = -w[jj] * r[jj];
-            w[jj] = 0.5f * w[jj];
+        for (int p = 0; p < JP; ++p) {
+            r[p] = mul2(neg2(w[p]), r[p]);
+            w[p] = mul2(splat2(0.5f), w[p]);
         }
         unsigned n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
         for (int sw = 0; sw < n; ++sw) {
@@ -353,11 +403,14 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                 float A = cs.nat[j0], mu = cs.nat[j0 + 1], wd = cs.nat[j0 + 2];
                 float eta = (FAM == FAM_PV) ? cs.nat[j0 + 3] : 0.0f;
                 float sc = sc2_of<FAM>(wd, wprec);
+                {
+                    const f2 scv = splat2(sc), nmsc = splat2(-mu * sc), et = splat2(eta);
 #pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    float l = 0.0f;
-                    shape<FAM>(x[jj], mu, sc, S0[jj], l);
-                    if (FAM == FAM_PV) S1[jj] = fmaf(eta, S0[jj], l);  // U
+                    for (int p = 0; p < JP; ++p) {
+                        f2 l = splat2(0.0f);
+                        shape2<FAM>(x[p], scv, nmsc, S0[p], l);
+                        if (FAM == FAM_PV) S1[p] = fma2(et, S0[p], l);  // U
+                    }
                 }
                 float tq[P], vq[P];
 #pragma unroll
@@ -373,70 +426,67 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
                     const float v = vq[c];
                     ++n_eval;
-                    // two independent accumulators shorten the FMA dependency chain
-                    float p0 = 0.0f, p1 = 0.0f;
+                    // lanes of the packed accumulator: even and odd points
+                    f2 acc2 = splat2(0.0f);
                     if (c == 0) {  // amplitude: D = (A' - A) U
-                        const float dA = v - A;
+                        const f2 dA = splat2(v - A);
 #pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            const float D = dA * (FAM == FAM_PV ? S1[jj] : S0[jj]);
-                            if (jj & 1)
-                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
-                            else
-                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
+                        for (int p = 0; p < JP; ++p) {
+                            const f2 D = mul2(dA, FAM == FAM_PV ? S1[p] : S0[p]);
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
                     } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
-                        const float dd = A * (v - eta);
+                        const f2 dd = splat2(A * (v - eta));
 #pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            const float D = dd * S0[jj];
-                            if (jj & 1)
-                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
-                            else
-                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
+                        for (int p = 0; p < JP; ++p) {
+                            const f2 D = mul2(dd, S0[p]);
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
                     } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
                         const float mu2 = (c == 1) ? v : mu;
-                        const float sc2 = (c == 2) ? sc2_of<FAM>(v, wprec) : sc;
+                        const float scn = (c == 2) ? sc2_of<FAM>(v, wprec) : sc;
+                        const f2 scv = splat2(scn), nmsc = splat2(-mu2 * scn), et = splat2(eta),
+                                 Av = splat2(A);
 #pragma unroll
-                        for (int jj = 0; jj < J; ++jj) {
-                            float l = 0.0f;
-                            shape<FAM>(x[jj], mu2, sc2, N0[jj], l);
-                            if (FAM == FAM_PV) N1[jj] = fmaf(eta, N0[jj], l);
-                            const float D = A * (FAM == FAM_PV ? N1[jj] - S1[jj] : N0[jj] - S0[jj]);
-                            if (jj & 1)
-                                p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
-                            else
-                                p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
+                        for (int p = 0; p < JP; ++p) {
+                            f2 l = splat2(0.0f);
+                            shape2<FAM>(x[p], scv, nmsc, N0[p], l);
+                            if (FAM == FAM_PV) N1[p] = fma2(et, N0[p], l);
+                            const f2 D = mul2(Av, FAM == FAM_PV ? sub2(N1[p], S1[p]) : sub2(N0[p], S0[p]));
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
                     }
-                    const float dE = group_sum(g, p0 + p1);
+                    const float dE = group_sum(g, lo2(acc2) + hi2(acc2));
                     if (tj < -beta * dE) {
                         if (c == 0) {
                             const float dA = v - A;
+                            const f2 d2 = splat2(dA + dA);
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(w[jj], (dA + dA) * (FAM == FAM_PV ? S1[jj] : S0[jj]), r[jj]);
+                            for (int p = 0; p < JP; ++p)
+                                r[p] = fma2(w[p], mul2(d2, FAM == FAM_PV ? S1[p] : S0[p]), r[p]);
                             A = v;
                         } else if (c == 3) {
                             const float de = v - eta;
                             const float dd = A * de;
+                            const f2 dd2 = splat2(dd + dd), de2 = splat2(de);
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) {
-                                r[jj] = fmaf(w[jj], (dd + dd) * S0[jj], r[jj]);
-                                S1[jj] = fmaf(de, S0[jj], S1[jj]);
+                            for (int p = 0; p < JP; ++p) {
+                                r[p] = fma2(w[p], mul2(dd2, S0[p]), r[p]);
+                                S1[p] = fma2(de2, S0[p], S1[p]);
                             }
                             eta = v;
                         } else {
+                            const f2 AA = splat2(A + A);
 #pragma unroll
-                            for (int jj = 0; jj < J; ++jj) {
+                            for (int p = 0; p < JP; ++p) {
                                 if (FAM == FAM_PV) {
-                                    r[jj] = fmaf(w[jj], (A + A) * (N1[jj] - S1[jj]), r[jj]);
-                                    S1[jj] = N1[jj];
+                                    r[p] = fma2(w[p], mul2(AA, sub2(N1[p], S1[p])), r[p]);
+                                    S1[p] = N1[p];
                                 } else {
-                                    r[jj] = fmaf(w[jj], (A + A) * (N0[jj] - S0[jj]), r[jj]);
+                                    r[p] = fma2(w[p], mul2(AA, sub2(N0[p], S0[p])), r[p]);
                                 }
-                                S0[jj] = N0[jj];
+                                S0[p] = N0[p];
                             }
                             if (c == 1) {
                                 mu = v;
@@ -458,25 +508,26 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
             // terms by the recurrence carried across q (N1: t, S0/S1: T_{q-1}, T_q)
             if (nbg > 0) {
 #pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    N1[jj] = __ldg(jb.ts + base + jj * stride);
-                    S0[jj] = 1.0f;
-                    S1[jj] = N1[jj];
+                for (int p = 0; p < JP; ++p) {
+                    const int i0 = base + 2 * p * stride;
+                    N1[p] = mk2(__ldg(jb.ts + i0), __ldg(jb.ts + i0 + stride));
+                    S0[p] = splat2(1.0f);
+                    S1[p] = N1[p];
                 }
             }
             for (int q = 0; q < nbg; ++q) {
                 const int j = K * P + q;
                 // advance the recurrence to T_q for every q, proposed or not
 #pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
+                for (int p = 0; p < JP; ++p) {
                     if (q == 0) {
-                        N0[jj] = 1.0f;
+                        N0[p] = splat2(1.0f);
                     } else if (q == 1) {
-                        N0[jj] = N1[jj];
+                        N0[p] = N1[p];
                     } else {
-                        N0[jj] = fmaf(2.0f * N1[jj], S1[jj], -S0[jj]);
-                        S0[jj] = S1[jj];
-                        S1[jj] = N0[jj];
+                        N0[p] = fma2(add2(N1[p], N1[p]), S1[p], neg2(S0[p]));
+                        S0[p] = S1[p];
+                        S1[p] = N0[p];
                     }
                 }
                 const float2 q2 = tb.tv[j];
@@ -485,19 +536,18 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                 const float v = q2.y;
                 const float dc = v - cs.nat[j];
                 ++n_eval;
-                float p0 = 0.0f, p1 = 0.0f;
+                f2 acc2 = splat2(0.0f);
+                const f2 dcv = splat2(dc);
 #pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    const float D = dc * N0[jj];
-                    if (jj & 1)
-                        p1 = fmaf(D, fmaf(w[jj], D, r[jj]), p1);
-                    else
-                        p0 = fmaf(D, fmaf(w[jj], D, r[jj]), p0);
+                for (int p = 0; p < JP; ++p) {
+                    const f2 D = mul2(dcv, N0[p]);
+                    acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                 }
-                const float dE = group_sum(g, p0 + p1);
+                const float dE = group_sum(g, lo2(acc2) + hi2(acc2));
                 if (tj < -beta * dE) {
+                    const f2 d2 = splat2(dc + dc);
 #pragma unroll
-                    for (int jj = 0; jj < J; ++jj) r[jj] = fmaf(w[jj], (dc + dc) * N0[jj], r[jj]);
+                    for (int p = 0; p < JP; ++p) r[p] = fma2(w[p], mul2(d2, N0[p]), r[p]);
                     if (lane == 0) {
                         cs.th[j] = tb.un[j];
                         cs.nat[j] = v;
@@ -507,7 +557,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
                 }
             }
             if (wf) {
-                const float E = group_energy<J, G>(g, w, r);
+                const float E = group_energy2<JP, G>(g, w, r);
                 const size_t o = (size_t)m * n + sw;
                 if (g.gw == 0) {
                     for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
@@ -516,7 +566,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhBounds<FAM, J, G>::MINB))
             }
         }
         if (!wf) {
-            const float E = group_energy<J, G>(g, w, r);
+            const float E = group_energy2<JP, G>(g, w, r);
             if (g.gw == 0) {
                 for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
                 if (lane == 0) jb.E[m] = E;

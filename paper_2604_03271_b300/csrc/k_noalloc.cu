@@ -9,11 +9,14 @@
 // in a fixed file-scope device array that every GPU loading this library
 // holds until the process exits.
 //
-// The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (once per device, with that device current); make that
-// first call before any stream capture.  All calls share the one array and it
-// keeps the last call's contents; each call rewrites every scratch field it
-// reads.  Calls whose kernels overlap on the GPU race on the array.
+// Every call made outside a stream capture looks up the array's device
+// address with cudaGetSymbolAddress (with the call's device current), so the
+// address stays right after a device reset re-creates the context; a call
+// made while its stream is capturing reuses the address found by the last
+// uncaptured call on that device, so make one call on each device before any
+// capture.  All calls share the one array and it keeps the last call's
+// contents; each call rewrites every scratch field it reads.  Calls whose
+// kernels overlap on the GPU race on the array.
 #include <mutex>
 
 #include "../../include/smc_kernels.h"
@@ -36,15 +39,22 @@ static __device__ __align__(256) StaticScratch g_scratch;
 static std::mutex g_mu;
 static StaticScratch *g_addr[STATIC_MAX_DEVICES];
 
-// device address of g_scratch on the current device (looked up once per device)
-static cudaError_t scratch_address(int dev, StaticScratch **out)
+// device address of g_scratch on the current device: looked up again on every
+// call outside a stream capture (a device reset gives the array a new
+// address), the last address found on this device inside one
+static cudaError_t scratch_address(int dev, cudaStream_t s, StaticScratch **out)
 {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = (StaticScratch *)p;
+    } else if (!g_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -68,9 +78,9 @@ extern "C" int smc_k_reweight_static(const void *E_dev, int64_t T, double beta, 
     if (!(beta >= 0.0 && beta < 1.0) || !(rho > 0.0 && rho < 1.0)) return SMC_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES) return SMC_ECUDA;
-    StaticScratch *sc = nullptr;
-    if (scratch_address(dev, &sc) != cudaSuccess) return SMC_ECUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    StaticScratch *sc = nullptr;
+    if (scratch_address(dev, s, &sc) != cudaSuccess) return SMC_ECUDA;
 
     // a fresh descriptor every call: zero-dimensional job, weights in scratch
     JobDev jb{};

@@ -223,7 +223,8 @@ __global__ void __cluster_dims__(RW_CL, 1, 1) __launch_bounds__(RW_THREADS)
     // -- job scalars (rank 0): step sizes from the previous stage's acceptance,
     //    evidence increment, new temperature
     if (rank == 0) {
-        for (int j = (int)threadIdx.x; j < d; j += RW_THREADS) update_step(jb, j, sh.mean[j], var[j] / sw);
+        for (int j = (int)threadIdx.x; j < d; j += RW_THREADS)
+            update_step(jb, j, sh.mean[j], var[j] / sw, beta, final_step ? 1.0 : beta + delta);
         if (threadIdx.x == 0) {
             jb.logz += -delta * emin + log(sw / (double)T);
             jb.beta = final_step ? 1.0 : beta + delta;

@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(FN_THREADS) k_finish32(JobDev *jobs, const int
     if (jb.state != JOB_ACTIVE || jb.status != 0) return;
     const int T = jb.T, d = jb.d, split = rw_split_of(T), ld = 1 + 2 * d;
     const double *part = jb.rwpart;
+    const double beta_prev = jb.beta, beta_next = jb.final_step ? 1.0 : jb.beta + jb.delta;
     double sw = 0.0;
     for (int sp = 0; sp < split; ++sp) sw += part[(size_t)sp * ld];
     for (int j = threadIdx.x; j < d; j += FN_THREADS) {
@@ -536,8 +537,9 @@ __global__ void __launch_bounds__(FN_THREADS) k_finish32(JobDev *jobs, const int
             s2 += part[(size_t)sp * ld + 2 + 2 * j];
         }
         const double c = (double)jb.th[(size_t)j * T], m1 = s1 / sw;
-        update_step(jb, j, c + m1, s2 / sw - m1 * m1);
+        update_step(jb, j, c + m1, s2 / sw - m1 * m1, beta_prev, beta_next);
     }
+    __syncthreads();  // every thread has read beta before it moves on
     if (threadIdx.x == 0) {
         const double delta = jb.delta;
         jb.logz += -delta * jb.emin + log(sw / (double)T);

@@ -70,6 +70,8 @@ struct JobDev {
     int *anc;
     double *lam, *step;
     float *stepf;
+    int step_rule;   // 0: lambda x population SD; 1: history predictor
+    double *hist;    // step_rule 1: per component (W, X, Y, XX, XY) regression sums
     unsigned long long *acc, *prop;
     const PriorDev *pri;
     // tempering state
@@ -176,6 +178,7 @@ __device__ __forceinline__ float poisson_term_f(float f, float y)
 
 // 1 / sqrt(2 ln 2): exp(-v^2/2) = 2^(-(v / sqrt(2 ln 2))^2)
 #define SMC_INV_SQRT_2LN2 0.84932180028801904272150283410289f
+#define SMC_PI 3.14159265358979323846
 
 // ---------------------------------------------------------------------------
 // Prior helpers (sampling coordinates)

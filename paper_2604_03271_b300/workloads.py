@@ -61,6 +61,7 @@ class Options:
     energy_fp64: int = 0
     seed: int = 1
     max_stages: int = 10000
+    step_rule: int = 0  # 0: lambda x weighted population SD; 1: history predictor
 
 
 @dataclasses.dataclass

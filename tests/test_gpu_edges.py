@@ -40,6 +40,26 @@ def test_all_fixed_parameters_give_exact_likelihood(ctx):
         assert abs(r["log_z"][0] - exact) <= (1e-9 if fp64 else 2e-5 * abs(exact))
 
 
+def test_equal_evidence_selects_the_lower_k(ctx):
+    # every peak FIXED at zero amplitude and the constant background FIXED:
+    # each candidate K has the same likelihood, so log Z is the same for every
+    # K (one stage, all weights equal) and the selection's tie rule must give
+    # the lowest K (|delta log Z| < 1e-12 counts as a tie)
+    spec = W.gaussian_small(1)
+    spec.k_min, spec.k_max = 1, 3
+    spec.bg = W.BG_CONST
+    spec.priors = W.Priors(amp=W.Prior(W.FIXED, 0.0), centre=W.Prior(W.FIXED, 5.0),
+                           width=W.Prior(W.FIXED, 0.5), bg=[W.Prior(W.FIXED, 0.3)])
+    f = np.full_like(spec.x, 0.3)
+    exact = float(np.sum(-0.5 * ((spec.y - f) / spec.sigma) ** 2)) + _lognorm(spec)
+    for fp64 in (0, 1):
+        r = ctx.run(spec, W.Options(particles=64, sweeps=1, seed=2, energy_fp64=fp64))
+        assert r["status"] == 0 and np.all(r["n_stages"] == 1)
+        assert np.ptp(r["log_z"]) <= 1e-12 * abs(exact)
+        assert abs(r["log_z"][0] - exact) <= (1e-9 if fp64 else 2e-5 * abs(exact))
+        assert r["argmax_k"] == 1
+
+
 @pytest.mark.parametrize("n,T", [(2, 2), (33, 7), (5, 64)])
 def test_minimal_sizes_replay(ctx, n, T):
     rng = np.random.default_rng(n)

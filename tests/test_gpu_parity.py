@@ -399,3 +399,104 @@ def test_whole_run_graph_equals_chunked_replay(ctx):
     ctx.profile_reset(events=False)
     np.testing.assert_array_equal(a["log_z"], b["log_z"])
     np.testing.assert_array_equal(a["n_stages"], b["n_stages"])
+
+
+# --------------------------------------------------------------------------
+# The boundary itself: smc_run with host arrays, model selection in C,
+# launch modes
+# --------------------------------------------------------------------------
+
+def _smc_run_raw(ctx, spec, opts):
+    """smc_run called through ctypes with plain host arrays (no binding helper)."""
+    import ctypes as C
+    from paper_2604_03271_b300 import api
+    m = api._Marshalled(spec, opts, None, 0)
+    x, y, s = (np.ascontiguousarray(a, dtype=np.float64) for a in (spec.x, spec.y, spec.sigma))
+    job = C.c_uint64()
+    st = api.lib().smc_run(ctx.h, x.ctypes.data, y.ctypes.data, s.ctypes.data, len(x), spec.k_min,
+                           spec.k_max, spec.family, spec.bg, spec.bg_degree, C.pointer(m.pri),
+                           C.pointer(m.opts), C.byref(job))
+    assert st == 0
+    v = api.ResultView()
+    assert api.lib().smc_result(ctx.h, job, C.byref(v)) == 0
+    nK = v.k_max - v.k_min + 1
+    out = {"log_z": np.ctypeslib.as_array(v.log_z, (nK,)).copy(), "selected_k": v.selected_k,
+           "p_k": np.ctypeslib.as_array(v.p_k, (nK,)).copy()}
+    assert api.lib().smc_release(ctx.h, job) == 0
+    return out
+
+
+def test_smc_run_entry_point_host_arrays(ctx):
+    # smc_run (Sec. II: log Z per K by Eq. (11), P(K|D) by Eq. (2), the K of
+    # smallest F = -log Z) against the oracle on the FP64 path, and the FP32
+    # path bit-identical to the same spectrum through smc_run_batch
+    spec = W.gaussian_small(1)
+    o64 = W.Options(particles=384, sweeps=4, seed=5, energy_fp64=1)
+    ref = oracle.run(spec, W.Options(particles=384, sweeps=4, seed=5))
+    r64 = _smc_run_raw(ctx, spec, o64)
+    np.testing.assert_allclose(r64["log_z"], ref["log_z"], atol=1e-7, rtol=0)
+    np.testing.assert_allclose(r64["p_k"], ref["p_k"], rtol=1e-6, atol=1e-12)
+    assert r64["selected_k"] == ref["argmax_k"] == 2
+    o32 = W.Options(particles=2048, sweeps=4, seed=5)
+    r32 = _smc_run_raw(ctx, spec, o32)
+    b32 = ctx.run_batch([(spec, o32)], keep_samples=False)[0]
+    np.testing.assert_array_equal(r32["log_z"], b32["log_z"])
+    assert r32["selected_k"] == b32["argmax_k"] == 2
+    lz = r32["log_z"]
+    assert r32["selected_k"] == spec.k_min + int(np.argmax(lz))
+
+
+def test_launch_modes_give_identical_results():
+    # one graph launch with a conditional while node, host-replayed four-stage
+    # graphs, and plain stream launches: the same kernels in the same order
+    from paper_2604_03271_b300 import api
+    spec = W.xps_like(3, n=600, k_true=2, k_max=3)
+    opts = W.Options(particles=2048, sweeps=3, seed=8)
+    res = []
+    for mode in (api.GRAPH_WHILE, api.GRAPH_CHUNKED, api.GRAPH_NONE):
+        with api.Context(0, graph_mode=mode) as c:
+            res.append(c.run(spec, opts, keep_samples=False))
+    for r in res[1:]:
+        np.testing.assert_array_equal(res[0]["log_z"], r["log_z"])
+        np.testing.assert_array_equal(res[0]["n_stages"], r["n_stages"])
+        for a, b in zip(res[0]["post_mean"], r["post_mean"]):
+            np.testing.assert_array_equal(a, b)
+    with pytest.raises(api.SmcError) as e:
+        api.Context(0, graph_mode=7)
+    assert e.value.status == api.SMC_EINVAL
+
+
+# --------------------------------------------------------------------------
+# Step sizes predicted from the histories of beta and of the acceptance
+# rates (step_rule 1, Sec. II B 4)
+# --------------------------------------------------------------------------
+
+def test_history_step_rule_fp64_replays_oracle(ctx):
+    spec = W.gaussian_small(1)
+    opts = W.Options(particles=384, sweeps=4, seed=5, step_rule=1)
+    ref = oracle.run(spec, opts)
+    r = ctx.run(spec, W.Options(particles=384, sweeps=4, seed=5, energy_fp64=1, step_rule=1))
+    np.testing.assert_allclose(r["log_z"], ref["log_z"], atol=1e-7, rtol=0)
+    np.testing.assert_array_equal(r["n_stages"], [j["n_stages"] for j in ref["jobs"]])
+    # the rule changes the trajectory: it is not the default rule
+    r0 = ctx.run(spec, W.Options(particles=384, sweeps=4, seed=5, energy_fp64=1))
+    assert np.max(np.abs(r0["log_z"] - r["log_z"])) > 1e-6
+
+
+def test_history_step_rule_fp32_estimator(ctx):
+    # FP32 batched path with the history rule against the FP64 path with it,
+    # as estimators over seeds (0.05 nat, 3 SE <= 0.05), same selected K
+    spec = W.gaussian_small(1)
+    seeds = range(1, 129)
+    a = ctx.run_batch([(spec, W.Options(particles=4096, sweeps=5, seed=s, step_rule=1)) for s in seeds],
+                      keep_samples=False)
+    b = ctx.run_batch([(spec, W.Options(particles=4096, sweeps=5, seed=s, step_rule=1, energy_fp64=2))
+                       for s in seeds], keep_samples=False)
+    lz32 = np.array([r["log_z"] for r in a])
+    lz64 = np.array([r["log_z"] for r in b])
+    se = np.sqrt(lz32.var(axis=0, ddof=1) / len(seeds) + lz64.var(axis=0, ddof=1) / len(seeds))
+    diff = np.abs(lz32.mean(0) - lz64.mean(0))
+    print("history rule: |mean FP32 - mean FP64| per K", diff, "SE", se)
+    assert np.all(3 * se <= 0.05), se
+    assert np.all(diff <= 0.05), (diff, se)
+    assert all(r["argmax_k"] == 2 for r in a + b)

@@ -271,3 +271,92 @@ def test_waste_free_evidence_k1_gamma_amplitude_quadrature():
     print("waste-free log Z: mean", vals.mean(), "exact", exact, "SE", se)
     assert se < 0.015
     assert abs(vals.mean() - exact) < 0.05, (vals.mean(), exact, se)
+
+
+# --------------------------------------------------------------------------
+# the history step-size predictor (step_rule 1; Sec. II B 4 names a predictor
+# from the histories of beta and of the acceptance rates)
+# --------------------------------------------------------------------------
+
+def _rw_acceptance_numeric(s, sigma):
+    """Acceptance rate of a Gaussian random walk of SD s on N(0, sigma^2), by
+    2-D quadrature of E[min(1, pi(x + s z) / pi(x))] over x and z."""
+    f = lambda z, x: (stats.norm.pdf(x, scale=sigma) * stats.norm.pdf(z)
+                      * min(1.0, math.exp(-((x + s * z) ** 2 - x * x) / (2 * sigma * sigma))))
+    val, _ = integrate.dblquad(f, -10 * sigma, 10 * sigma, -10, 10, epsabs=1e-10, epsrel=1e-10)
+    return val
+
+
+def _rw_acceptance(s, sigma):
+    return 2.0 / math.pi * math.atan(2.0 * sigma / s)
+
+
+@pytest.mark.parametrize("ratio", [0.3, 1.0, 2.42, 6.0])
+def test_random_walk_acceptance_closed_form(ratio):
+    # the relation the predictor inverts, checked by direct quadrature
+    assert _rw_acceptance_numeric(ratio, 1.0) == pytest.approx(_rw_acceptance(ratio, 1.0), abs=1e-7)
+
+
+@pytest.mark.parametrize("gamma", [0.5, 0.3, 0.9])
+def test_predictor_hits_target_rate_on_a_power_law(gamma):
+    # tempered posteriors whose SD follows sigma(beta) = 2 beta^-gamma; rates
+    # observed at arbitrary steps; after two or more stages the fitted slope is
+    # -gamma and the predicted step gives acceptance 0.44 at the next beta
+    # exactly (with one stage the slope is -1/2, exact for gamma = 1/2)
+    sig = lambda b: 2.0 * b ** -gamma
+    betas = [1e-4 * 3.0 ** k for k in range(8)]
+    h = np.zeros(5)
+    rng = np.random.default_rng(3)
+    s = 0.7 * sig(betas[0])
+    for k in range(len(betas) - 1):
+        a = _rw_acceptance(s, sig(betas[k]))
+        assert 0.02 < a < 0.98  # inside the clamp of the observed rate
+        s_new, h = oracle.predict_step(h, s, a, betas[k], betas[k + 1], sd_pop=sig(betas[k + 1]))
+        if k >= 1 or gamma == 0.5:
+            assert _rw_acceptance(s_new, sig(betas[k + 1])) == pytest.approx(0.44, abs=1e-9)
+        # the next observation is made at an unrelated step
+        s = s_new * rng.uniform(0.3, 3.0)
+
+
+def test_predictor_history_weights_and_bounds():
+    # the regression sums: each older stage counts half as much as the next
+    h = np.zeros(5)
+    obs = [(1e-3, 0.5, 0.8), (1e-2, 0.3, 0.5), (1e-1, 0.6, 0.2)]
+    wts, xs, ys = [], [], []
+    for k, (b, a, s) in enumerate(obs):
+        _, h = oracle.predict_step(h, s, a, b, 2 * b, sd_pop=1.0)
+        wts = [0.5 * q for q in wts] + [1.0]
+        xs.append(math.log(b))
+        ys.append(math.log(s * math.tan(math.pi * a / 2) / 2))
+    wts, xs, ys = np.array(wts), np.array(xs), np.array(ys)
+    np.testing.assert_allclose(h, [wts.sum(), wts @ xs, wts @ ys, wts @ xs ** 2, wts @ (xs * ys)],
+                               rtol=1e-13)
+    # observed rates are clamped to [0.02, 0.98]: 0.999 counts as 0.98
+    a1, _ = oracle.predict_step(np.zeros(5), 1.0, 0.999, 1e-3, 1e-2, sd_pop=1e9)
+    a2, _ = oracle.predict_step(np.zeros(5), 1.0, 0.98, 1e-3, 1e-2, sd_pop=1e9)
+    assert a1 == a2
+    # the step stays within [0.01, 10] x the population SD
+    st, _ = oracle.predict_step(np.zeros(5), 1.0, 0.98, 1e-3, 1e-2, sd_pop=1e-3)
+    assert st == pytest.approx(1e-2, rel=1e-14)
+    st, _ = oracle.predict_step(np.zeros(5), 1.0, 0.02, 1e-3, 1e-2, sd_pop=1e3)
+    assert st == pytest.approx(10.0, rel=1e-14)
+
+
+def test_predictor_rule_in_runs_evidence_and_rates():
+    # the sampler with the history predictor: closed-form evidence of the
+    # linear-Gaussian case, and the amplitudes' acceptance rates near 0.44 at
+    # the later stages (their tempered posteriors are Gaussian)
+    spec = W.linear_gaussian_case(3)
+    exact = _lin_gauss_exact(spec)
+    vals, late = [], []
+    for seed in range(1, 13):
+        r = oracle.run_job(spec, 2, W.Options(particles=8000, sweeps=8, seed=seed, step_rule=1))
+        assert r["status"] == 0
+        vals.append(r["log_z"])
+        late.append(r["acc"][-3:, [0, 3]].ravel())
+    vals = np.array(vals)
+    se = vals.std(ddof=1) / math.sqrt(len(vals))
+    print("history predictor log Z: mean", vals.mean(), "exact", exact, "SE", se)
+    assert se < 0.015
+    assert abs(vals.mean() - exact) < 0.05
+    assert abs(np.mean(late) - 0.44) < 0.08

@@ -4,9 +4,10 @@ It serves callers that cannot allocate device memory themselves through the
 library (a host framework that owns every device allocation, or a service
 that must not grow device memory once running): they pass their own device
 arrays, and the kernel's scratch is a fixed static array inside the library.
-This file is collected last on purpose.  Two calls in a row (different sizes
-and precisions, so the shared scratch is reused) must match the ordinary
-smc_k_reweight entry point within the tolerances of the other reweight tests.
+This file is collected last on purpose.  Three calls in a row (different sizes
+and precisions, the last at the largest accepted size, so the shared scratch
+is reused and filled) must match the ordinary smc_k_reweight entry point
+within the tolerances of the other reweight tests.
 """
 import ctypes as C
 
@@ -40,12 +41,15 @@ def _call_static(f, E, beta, rho, precision):
     return dl.value, lz.value, bool(fin.value), q
 
 
-def test_static_reweight_matches_ordinary_entry_point_twice():
+def test_static_reweight_matches_ordinary_entry_point_in_a_row():
     from paper_2604_03271_b300 import api
     f = _static_fn()
     rng = np.random.default_rng(42)
     cases = [(rng.gamma(2.0, 3e3, 65536) + 50.0, 0.01, 1),      # FP64 energies, large T
-             (rng.gamma(2.0, 40.0, 5000) + 7.0, 0.4, 0)]        # FP32 energies, smaller T
+             (rng.gamma(2.0, 40.0, 5000) + 7.0, 0.4, 0),        # FP32 energies, smaller T
+             # FP32 energies at the largest accepted T: the top of the weight
+             # buffer and every per-CTA partial row of the scratch in use
+             (rng.gamma(2.0, 200.0, 1 << 20) + 1000.0, 0.0, 0)]
     with api.Context(0) as ctx:
         for E, beta, prec in cases:
             if prec == 0:
