@@ -57,6 +57,10 @@ def workload(name: str, seed: int):
         return _MIXED[(seed - 1) % len(_MIXED)]
     if name == "xps":
         return W.xps_like(seed), W.Options(particles=16384, sweeps=20, seed=seed)
+    if name == "xps_wf":
+        # waste-free SMC (Sec. II B 3): 16384 chains per K resampled from
+        # 20 x 16384 carried particles, every sweep's state kept
+        return W.xps_like(seed), W.Options(particles=16384 * 20, sweeps=20, waste_free=1, seed=seed)
     if name == "xrd":
         return W.xrd_like(seed), W.Options(particles=65536, sweeps=20, seed=seed)
     if name == "gauss":
@@ -84,7 +88,8 @@ def workload(name: str, seed: int):
 
 def config_of(name: str, batch: int) -> dict:
     s, o = workload(name, 1)
-    return {"workload": {"xps": "xps-pv-1001", "xrd": "xrd-pv-4096", "gauss": "gauss-301",
+    return {"workload": {"xps": "xps-pv-1001", "xps_wf": "xps-pv-1001-waste-free", "xrd": "xrd-pv-4096",
+                         "gauss": "gauss-301",
                          "mixed": "mixed-256", "xps_shirley": "xps-shirley-model-variance-840",
                          "xrd_phase": "xrd-phase-poisson-K3-1000", "xrd_phase_5000": "xrd-phase-poisson-K3-5000",
                          "xrd_phase_10000": "xrd-phase-poisson-K3-10000",
@@ -92,6 +97,7 @@ def config_of(name: str, batch: int) -> dict:
                          "deconv10": "deconv-gauss-K10-1000", "deconv30": "deconv-gauss-K30-3000"}[name],
             "n_points": s.n, "k_range": [s.k_min, s.k_max], "particles_per_k": o.particles,
             "sweeps": o.sweeps, "ess_target": o.ess_target, "spectra_per_step": batch,
+            "waste_free": bool(o.waste_free),
             "family": {W.GAUSS: "gauss", W.LORENTZ: "lorentz", W.PSEUDO_VOIGT: "pseudo-voigt",
                        W.GAUSS_PRECISION: "gauss-precision", W.XRD_PHASE: "xrd-phase"}[s.family],
             "l2": "flushed between steps (256 MiB write)"}
@@ -239,7 +245,7 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 1.0e12,
+UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xps_wf": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 1.0e12,
                       "xrd_phase_5000": 2.2e12, "xrd_phase_10000": 1.7e12,
                       "deconv3": 3.6e10, "deconv10": 8.2e11, "deconv30": 4.8e13}
 
@@ -253,7 +259,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="xps", choices=["xps", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "xrd_phase_5000",
+    ap.add_argument("--workload", default="xps", choices=["xps", "xps_wf", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "xrd_phase_5000",
                                                        "xrd_phase_10000", "deconv3", "deconv10",
                                                        "deconv30"])
     ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
@@ -264,7 +270,18 @@ def main():
     ap.add_argument("--event-steps", type=int, default=1,
                     help="steps of the untimed per-kernel event pass (kernel shares, roofline)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="only the serving sweep (Poisson mix of XPS- and XRD-shaped requests)")
+    ap.add_argument("--serve-rates", default="0.5,1.0,3.0")
+    ap.add_argument("--serve-saturate", type=float, default=2.0,
+                    help="rates at or above this are saturation probes (half the requests)")
+    ap.add_argument("--serve-particles", type=int, default=2048)
+    ap.add_argument("--plain-requests", type=int, default=0)
     args = ap.parse_args()
+
+    if args.serving_sweep:
+        serving_sweep(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -484,6 +501,94 @@ def serve_sample(api, device: int, name: str, rate: float, count: int) -> dict:
     return {"offered_per_s": rate, "requests": count, "achieved_per_s": count / max(t_done, 1e-9),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "note": "FP32 batched path; arrivals from t = 0"}
+
+
+def serve_stream(api, device: int, items, rate: float, seed: int = 7) -> dict:
+    """Submit `items` on a Poisson arrival stream of `rate` requests/s to one
+    context (continuous batching); per-request latency is the library's
+    submit-to-result time.  Returns offered and achieved load and the latency
+    percentiles."""
+    import threading
+
+    from paper_2604_03271_b300 import autotune
+    ctx = api.Context(device)
+    autotune.load(ctx)
+    count = len(items)
+    arrivals = W.poisson_arrivals(rate, count, seed=seed)
+    jobs = [None] * count
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (s, o) in enumerate(items):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            jobs[i] = ctx.submit(s, o)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = np.zeros(count)
+    ok = 0
+    for i in range(count):
+        while jobs[i] is None:
+            time.sleep(0.0005)
+        ctx.wait(jobs[i], 3600.0)
+        r = ctx.result(jobs[i], items[i][0])
+        lat[i] = r["latency_ms"]
+        ok += int(r["status"] == 0)
+        ctx.release(jobs[i])
+    t_done = time.perf_counter() - t0
+    th.join()
+    prof = ctx.profile()
+    ctx.close()
+    span = max(t_done - arrivals[0], 1e-9)
+    return {"offered_per_s": rate, "requests": count, "ok": ok,
+            "achieved_per_s": count / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max()), "max_batch_requests": prof["max_batch_requests"]}
+
+
+def serving_sweep(args):
+    """Serving: a Poisson stream mixing XPS-shaped (N = 1001, K = 1..6) and
+    XRD-shaped (N = 4096, K = 1..12) spectra 50/50, served by the FP32 batched
+    path with continuous batching at several offered rates, and the plain FP64
+    one-spectrum-per-launch path on the same kind of requests one at a time."""
+    import torch
+
+    from paper_2604_03271_b300 import api
+    torch.cuda.set_device(0)
+    T = args.serve_particles
+
+    def mix(n, seed0):
+        out = []
+        for i in range(n):
+            if i % 2 == 0:
+                out.append((W.xps_like(seed0 + i), W.Options(particles=T, sweeps=20, seed=seed0 + i)))
+            else:
+                out.append((W.xrd_like(seed0 + i), W.Options(particles=T, sweeps=20, seed=seed0 + i)))
+        return out
+
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    res = {"workload": "poisson mix: 50% xps-pv-1001 (K=1..6), 50% xrd-pv-4096 (K=1..12)",
+           "particles_per_k": T, "sweeps": 20, "rates": []}
+    for k, rate in enumerate(rates):
+        n = args.serve_requests if rate < args.serve_saturate else max(args.serve_requests // 2, 20)
+        res["rates"].append(serve_stream(api, 0, mix(n, 10000 * (k + 1)), rate, seed=11 + k))
+        print(json.dumps(res["rates"][-1]), flush=True)
+    res["saturation_per_s"] = max(r["achieved_per_s"] for r in res["rates"])
+    if args.plain_requests > 0:
+        ctx = api.Context(0)
+        lat = []
+        for i in range(args.plain_requests):
+            s = W.xps_like(50000 + i)
+            t0 = time.perf_counter()
+            r = ctx.run(s, W.Options(particles=T, sweeps=20, seed=50000 + i, energy_fp64=1), keep_samples=False)
+            lat.append(1000.0 * (time.perf_counter() - t0))
+            assert r["status"] == 0
+        ctx.close()
+        res["plain_fp64_xps"] = {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+                                 "max_ms": float(np.max(lat)), "note": "one request at a time, XPS-shaped only"}
+    print(json.dumps({"serving_sweep": res}), flush=True)
 
 
 def plain_sample(ctx, name: str, units_per_spec: float) -> dict:

@@ -81,14 +81,17 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
 /* Tile of the fused Metropolis kernel for FP32 jobs of `family` whose grid
  * has at most n_max points: J points per lane (4, 8, 12, 16; also 24, 32 for
  * Gaussian/Lorentzian) and G warps per chain (1, 2, 4, 8; 16 with J <= 8),
- * 32 G J >= N.  family | SMC_TILE_COUPLED sets the tile of the coupled-grid
- * kernel (Shirley background or model variance: J = 4 or 8); SMC_XRD_PHASE
- * (always coupled) that of the phase kernel (J = 4 or 8).
- * Entries are matched in the order they were set; the first whose family
- * matches and n_max >= N wins; without a match a padding-minimising default
- * is used.  J = 0 clears the table.  Used by the autotuner. */
+ * 32 G J >= N, and the register budget per thread `regs`: 0 for the tile's
+ * default, or 64, 80, 96, 128 for G = 4 or 8 with J = 4, 8, 16 (fewer
+ * registers, more resident warps).  family | SMC_TILE_COUPLED sets the tile of
+ * the coupled-grid kernel (Shirley background or model variance: J = 4 or 8,
+ * regs 0); SMC_XRD_PHASE (always coupled) that of the phase kernel (J = 4 or
+ * 8, regs 0).  Entries are matched in the order they were set; the first
+ * whose family matches and n_max >= N wins; without a match a
+ * padding-minimising default is used.  J = 0 clears the table.  SMC_EINVAL
+ * for a tile that is not compiled.  Used by the autotuner. */
 #define SMC_TILE_COUPLED 16
-int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G);
+int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G, int32_t regs);
 
 /* Profiling counters of a context, accumulated over the runs finished since
  * the last smc_profile_reset.  Kernel classes: 0 reweight (tempering step),

@@ -116,7 +116,7 @@ def lib():
     L.smc_k_reweight.argtypes = [vp, vp, i64, dbl, dbl, i32, P(dbl), P(dbl), P(i32), vp]
     L.smc_k_resample.argtypes = [vp, vp, i64, i64, u32, vp]
     L.smc_k_mh_stage.argtypes = [vp, P(Request), i32, vp, vp, i64, vp, dbl, u32, i32, vp, vp, vp, vp]
-    L.smc_set_tile.argtypes = [vp, i32, i64, i32, i32]
+    L.smc_set_tile.argtypes = [vp, i32, i64, i32, i32, i32]
     L.smc_set_tile.restype = C.c_int
     L.smc_profile_reset.argtypes = [vp, i32]
     L.smc_profile_read.argtypes = [vp, P(Profile)]
@@ -322,11 +322,11 @@ class Context:
         _check(self._L.smc_wait(self.h, C.c_uint64(job), float(timeout_s)), "smc_wait")
 
     # -- tiles -------------------------------------------------------------
-    def set_tile(self, family: int, n_max: int, J: int, G: int):
-        _check(self._L.smc_set_tile(self.h, family, n_max, J, G), "smc_set_tile")
+    def set_tile(self, family: int, n_max: int, J: int, G: int, regs: int = 0):
+        _check(self._L.smc_set_tile(self.h, family, n_max, J, G, regs), "smc_set_tile")
 
     def clear_tiles(self):
-        _check(self._L.smc_set_tile(self.h, 0, 1, 0, 0), "smc_set_tile")
+        _check(self._L.smc_set_tile(self.h, 0, 1, 0, 0, 0), "smc_set_tile")
 
     # -- profiling ---------------------------------------------------------
     def profile_reset(self, events: bool = False):

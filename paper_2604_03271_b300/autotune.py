@@ -1,12 +1,14 @@
 """Autotuner for the fused Metropolis kernel's tile.
 
-The tile (J grid points per lane, G warps per chain, 32 G J >= N) decides the
-kernel's register budget, occupancy and per-proposal reduction cost.  For each
-peak family and grid-length bucket this times every admissible tile on a short
-run of a synthetic spectrum (same spectrum, seed and stages for all tiles) and
-keeps the fastest Metropolis time.  The table is stored next to this file
-(tiles_b300.json) and applied with `load(ctx)`; the library itself falls back
-to a padding-minimising default for buckets the table does not cover.
+The tile (J grid points per lane, G warps per chain, 32 G J >= N, and a
+register budget R per thread) decides the kernel's occupancy, spills and
+per-proposal reduction cost.  For each peak family and grid-length bucket this
+times every admissible tile -- and, for four- and eight-warp chains, every
+compiled register budget -- on a short run of a synthetic spectrum (same
+spectrum, seed and stages for all) and keeps the fastest Metropolis time.  The
+table is stored next to this file (tiles_b300.json) and applied with
+`load(ctx)`; the library itself falls back to a padding-minimising default for
+buckets the table does not cover.
 
     python -m paper_2604_03271_b300.autotune      # on a B300: tune and write
 """
@@ -28,6 +30,17 @@ G_SET = (1, 2, 4, 8, 16)
 # the phase kernel also spreads a chain over a cluster of 8-warp CTAs (G = 8 C)
 G_SET_CLUSTER = tuple(8 * c for c in range(3, 17))
 BUCKETS_XRD = (512, 1024, 2048, 4096, 5120, 10240)
+
+
+R_SET = (64, 80, 96, 128)  # register budgets of four- and eight-warp chains with J = 4, 8, 16
+
+
+def variants(family: int, J: int, G: int) -> List[int]:
+    """Register budgets to try for a tile: 0 (the tile's default) and, for the
+    fused kernel's four- and eight-warp chains with J = 4, 8, 16, R_SET."""
+    if family & COUPLED or G not in (4, 8) or J not in (4, 8, 16):
+        return [0]
+    return [0] + list(R_SET)
 
 
 def candidates(family: int, n: int, slack: float = 1.5) -> List[Tuple[int, int]]:
@@ -70,7 +83,8 @@ def tuning_spectrum(family: int, n: int) -> W.Spectrum:
 
 def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COUPLED, W.XRD_PHASE | COUPLED),
          buckets=BUCKETS,
-         particles: int = 8192, sweeps: int = 4, stages: int = 6, verbose: bool = True) -> List[Dict]:
+         particles: int = 8192, sweeps: int = 4, stages: int = 6, verbose: bool = True,
+         registers: bool = True) -> List[Dict]:
     table = []
     for fam in families:
         for n in (BUCKETS_XRD if fam == W.XRD_PHASE | COUPLED else buckets):
@@ -78,17 +92,18 @@ def tune(ctx, families=(W.PSEUDO_VOIGT, W.GAUSS, W.LORENTZ, W.PSEUDO_VOIGT | COU
             opts = W.Options(particles=particles, sweeps=sweeps, seed=5, max_stages=stages)
             results = []
             for J, G in candidates(fam, n):
-                ctx.clear_tiles()
-                ctx.set_tile(fam, n, J, G)
-                ctx.run(spec, W.Options(particles=1024, sweeps=1, seed=1, max_stages=1), keep_samples=False)
-                ctx.profile_reset(events=True)
-                ctx.run(spec, opts, keep_samples=False)
-                p = ctx.profile()
-                ms = p["ms"]["metropolis"]
-                results.append((ms, J, G, p["sfu_ops"] / max(ms, 1e-9) / 1e6))
-            ms, J, G, gops = min(results)
-            row = {"family": fam, "n_max": n, "J": J, "G": G, "mh_ms": ms, "sfu_gops": gops,
-                   "tried": [{"J": j, "G": g, "mh_ms": m} for m, j, g, _ in results]}
+                for R in (variants(fam, J, G) if registers else [0]):
+                    ctx.clear_tiles()
+                    ctx.set_tile(fam, n, J, G, R)
+                    ctx.run(spec, W.Options(particles=1024, sweeps=1, seed=1, max_stages=1), keep_samples=False)
+                    ctx.profile_reset(events=True)
+                    ctx.run(spec, opts, keep_samples=False)
+                    p = ctx.profile()
+                    ms = p["ms"]["metropolis"]
+                    results.append((ms, J, G, R, p["sfu_ops"] / max(ms, 1e-9) / 1e6))
+            ms, J, G, R, gops = min(results)
+            row = {"family": fam, "n_max": n, "J": J, "G": G, "R": R, "mh_ms": ms, "sfu_gops": gops,
+                   "tried": [{"J": j, "G": g, "R": rr, "mh_ms": m} for m, j, g, rr, _ in results]}
             if verbose:
                 print(json.dumps(row), flush=True)
             table.append(row)
@@ -105,7 +120,7 @@ def load(ctx, path: Optional[str] = None) -> int:
         rows = json.load(fh)["tiles"]
     ctx.clear_tiles()
     for r in sorted(rows, key=lambda r: (r["family"], r["n_max"])):
-        ctx.set_tile(int(r["family"]), int(r["n_max"]), int(r["J"]), int(r["G"]))
+        ctx.set_tile(int(r["family"]), int(r["n_max"]), int(r["J"]), int(r["G"]), int(r.get("R", 0)))
     return len(rows)
 
 

@@ -814,7 +814,7 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
         if (r->fp64)
             st = cuda_status(launch_mh_plain(c.d_jobs, c.d_lists, 1, (int)S, c.stream));
         else
-            st = cuda_status(launch_mh(c.d_jobs, c.d_lists, 1, kernel_family(r->family) | (r->full ? MH_COUPLED : 0), r->tile.J, r->tile.G, 0, c.stream, K));
+            st = cuda_status(launch_mh(c.d_jobs, c.d_lists, 1, kernel_family(r->family) | (r->full ? MH_COUPLED : 0), r->tile.J, r->tile.G, r->tile.R, 0, c.stream, K));
     }
     if (st == SMC_OK) st = cuda_status(cudaStreamSynchronize(c.stream));
     if (st == SMC_OK)
@@ -842,7 +842,7 @@ int smc_k_mh_stage(smc_ctx *ctx, const smc_request *spec, int32_t K, const doubl
     return st;
 }
 
-int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G)
+int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t G, int32_t regs)
 {
     if (!ctx) return SMC_EINVAL;
     std::lock_guard<std::recursive_mutex> g(ctx->c.mu);
@@ -854,8 +854,8 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
     family &= ~MH_COUPLED;
     if (family < 0 || family > 4 || (family == SMC_XRD_PHASE && !coupled)) return SMC_EINVAL;
     family = kernel_family(family) | coupled;
-    if (n_max < 1 || !mh_tile_supported(family, J, G) || 32L * J * G < 1) return SMC_EINVAL;
-    ctx->c.tiles.push_back({family, n_max, J, G});
+    if (n_max < 1 || !mh_tile_supported(family, J, G, regs) || 32L * J * G < 1) return SMC_EINVAL;
+    ctx->c.tiles.push_back({family, n_max, J, G, regs});
     return SMC_OK;
 }
 

@@ -50,13 +50,13 @@ Tile choose_tile(int family, int n)
         // G > 16 (multiples of 8): the phase kernel's cluster-spanning chains
         static const int Gs[] = {1,  2,  4,  8,  16, 24, 32, 40,  48,  56,  64,
                                  72, 80, 88, 96, 104, 112, 120, 128};
-        Tile best{0, 0};
+        Tile best{0, 0, 0};
         long best_pad = -1;
         for (int J : {8, 4})
             for (int G : Gs) {
                 if (!mh_tile_supported(family, J, G) || 32L * G * J < n) continue;
                 if (best_pad < 0 || 32L * G * J < best_pad) {
-                    best = {J, G};
+                    best = {J, G, 0};
                     best_pad = 32L * G * J;
                 }
                 break;
@@ -70,7 +70,7 @@ Tile choose_tile(int family, int n)
     static const int Js_large[] = {16, 8, 12, 4, 24, 32};
     const int *Js = n <= 32 * 4 * 8 ? Js_small : Js_large;
     const int nJ = 6;  // unsupported (family, J, G) are skipped below
-    Tile best{0, 0};
+    Tile best{0, 0, 0};
     double best_cost = -1.0;
     for (int a = 0; a < nJ; ++a)
         for (int G : {1, 2, 4, 8, 16}) {
@@ -80,7 +80,7 @@ Tile choose_tile(int family, int n)
             if (pad < n) continue;
             const double cost = (double)pad * (1.0 + 0.1 * a);  // preferred J first
             if (best_cost < 0.0 || cost < best_cost) {
-                best = {J, G};
+                best = {J, G, 0};
                 best_cost = cost;
             }
             break;  // smallest G for this J
@@ -210,8 +210,8 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
         r->tile = choose_tile(kf, r->n);
         for (const auto &t : c.tiles)
             if (t[0] == kf && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
-                mh_tile_supported(kf, (int)t[2], (int)t[3])) {
-                r->tile = {(int)t[2], (int)t[3]};
+                mh_tile_supported(kf, (int)t[2], (int)t[3], (int)t[4])) {
+                r->tile = {(int)t[2], (int)t[3], (int)t[4]};
                 break;
             }
         if (r->tile.J == 0) {
@@ -498,6 +498,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
         jb.d = d;
         jb.J = r.tile.J;
         jb.G = r.tile.G;
+        jb.R = r.tile.R;
         jb.T = (int)T;
         jb.S = (int)S;
         jb.sweeps = r.opts.sweeps;
@@ -554,7 +555,7 @@ int setup_request(Ctx &c, Request &r, int64_t T_override, int64_t S_override)
 // Stage loop.
 // ---------------------------------------------------------------------------
 struct Bucket {
-    int family, J, G;
+    int family, J, G, R;
     std::vector<int> slots;
     int kcap = 0;  // most peaks (phases) of its jobs
 };
@@ -586,9 +587,9 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
             Bucket *b = nullptr;
             const int kfam = jb.family | (jb.full ? MH_COUPLED : 0);
             for (Bucket &x : P.buckets)
-                if (x.family == kfam && x.J == jb.J && x.G == jb.G) b = &x;
+                if (x.family == kfam && x.J == jb.J && x.G == jb.G && x.R == jb.R) b = &x;
             if (!b) {
-                P.buckets.push_back({kfam, jb.J, jb.G, {}});
+                P.buckets.push_back({kfam, jb.J, jb.G, jb.R, {}});
                 b = &P.buckets.back();
             }
             b->slots.push_back(sl);
@@ -607,7 +608,7 @@ static int build_plan(Ctx &c, std::vector<Request *> &reqs, Plan &P)
     for (Bucket &b : P.buckets) {
         P.boff.push_back(host_lists.size());
         host_lists.insert(host_lists.end(), b.slots.begin(), b.slots.end());
-        P.grids.push_back(mh_resident_grid(b.family, b.J, b.G, b.kcap));
+        P.grids.push_back(mh_resident_grid(b.family, b.J, b.G, b.R, b.kcap));
     }
     if ((int)host_lists.size() > LIST_AREA) return SMC_ENOMEM;
     CK(cudaMemcpyAsync(c.d_lists, host_lists.data(), 4 * host_lists.size(), cudaMemcpyHostToDevice,
@@ -637,7 +638,8 @@ static cudaError_t iteration(Ctx &c, const Plan &P, cudaEvent_t *ev, int k)
     if ((e = mark(3)) != cudaSuccess) return e;
     for (size_t b = 0; b < P.buckets.size(); ++b)
         if ((e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
-                           P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream,
+                           P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.buckets[b].R,
+                           P.grids[b], c.stream,
                            P.buckets[b].kcap)) != cudaSuccess)
             return e;
     if ((e = mark(4)) != cudaSuccess) return e;
@@ -688,7 +690,8 @@ static bool run_whole_graph(Ctx &c, const Plan &P, int *status)
         if (e == cudaSuccess) e = launch_gather(c.d_jobs, c.d_lists, nall, P.max_elems, false, c.stream);
         for (size_t b = 0; b < P.buckets.size() && e == cudaSuccess; ++b)
             e = launch_mh(c.d_jobs, c.d_lists + P.boff[b], (int)P.buckets[b].slots.size(),
-                          P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.grids[b], c.stream,
+                          P.buckets[b].family, P.buckets[b].J, P.buckets[b].G, P.buckets[b].R,
+                          P.grids[b], c.stream,
                           P.buckets[b].kcap);
         if (e == cudaSuccess)
             e = launch_stage_end_cond(c.d_jobs, c.d_lists, nall, c.d_nactive, h, c.d_nactive + 1,

@@ -35,7 +35,7 @@ constexpr int NACTIVE_SLOTS = 64;
 constexpr int ST_NO_ROOM = 1000;
 
 struct Tile {
-    int J, G;
+    int J, G, R;  // R: register budget per thread (0: the tile's default)
 };
 
 struct Request {
@@ -57,7 +57,7 @@ struct Request {
     void *spec_arena = nullptr;
     size_t spec_bytes = 0;
     SpecDev sd{};
-    Tile tile{16, 1};
+    Tile tile{16, 1, 0};
     int n_pad = 0;
     std::vector<int> slots;
     std::vector<void *> job_arena;
@@ -88,8 +88,8 @@ struct Ctx {
     int *d_nactive = nullptr;
     int *h_nactive = nullptr;      // pinned, device-mapped, one entry per stage of a chunk
     int *h_nactive_dev = nullptr;  // its device alias
-    // autotuned tiles: (family, n_max, J, G)
-    std::vector<std::array<int64_t, 4>> tiles;
+    // autotuned tiles: (family, n_max, J, G, R)
+    std::vector<std::array<int64_t, 5>> tiles;
     // profiling (per-kernel events need the chunked graph: conditional bodies
     // take no event nodes)
     bool prof_events = false;

@@ -6,9 +6,9 @@
 namespace smc {
 
 typedef void (*mh_fn)(JobDev *, const int *, int);
-mh_fn mh_pick_gauss(int J, int G);
-mh_fn mh_pick_lor(int J, int G);
-mh_fn mh_pick_pv(int J, int G);
+mh_fn mh_pick_gauss(int J, int G, int R);
+mh_fn mh_pick_lor(int J, int G, int R);
+mh_fn mh_pick_pv(int J, int G, int R);
 mh_fn mhf_pick_gauss(int J, int G);
 mh_fn mhf_pick_lor(int J, int G);
 mh_fn mhf_pick_pv(int J, int G);
@@ -23,22 +23,24 @@ static int cluster_of(int family, int G)
     return ((family & (MH_COUPLED - 1)) == FAM_XRD && G > 16) ? G / 8 : 1;
 }
 
-// family: FAM_* of the peaks, plus MH_COUPLED for the coupled-grid kernel
-static mh_fn pick(int family, int J, int G)
+// family: FAM_* of the peaks, plus MH_COUPLED for the coupled-grid kernel;
+// R: register budget of the fused kernel's tile (0: its default)
+static mh_fn pick(int family, int J, int G, int R)
 {
     const int fam = family & (MH_COUPLED - 1);
+    if (R != 0 && (family & MH_COUPLED)) return nullptr;
     if (fam == FAM_XRD) return (family & MH_COUPLED) ? mhp_pick(J, G) : nullptr;
     if (family & MH_COUPLED) {
         if (fam == FAM_GAUSS) return mhf_pick_gauss(J, G);
         if (fam == FAM_LORENTZ) return mhf_pick_lor(J, G);
         return mhf_pick_pv(J, G);
     }
-    if (fam == FAM_GAUSS) return mh_pick_gauss(J, G);
-    if (fam == FAM_LORENTZ) return mh_pick_lor(J, G);
-    return mh_pick_pv(J, G);
+    if (fam == FAM_GAUSS) return mh_pick_gauss(J, G, R);
+    if (fam == FAM_LORENTZ) return mh_pick_lor(J, G, R);
+    return mh_pick_pv(J, G, R);
 }
 
-bool mh_tile_supported(int family, int J, int G) { return pick(family, J, G) != nullptr; }
+bool mh_tile_supported(int family, int J, int G, int R) { return pick(family, J, G, R) != nullptr; }
 
 // Dynamic shared memory of the phase kernel's profile cache: the two parts of
 // kcap profiles at every point of the block (threads x J points), if at most 96 KB
@@ -66,9 +68,9 @@ static cudaLaunchConfig_t cluster_config(int C, int grid, size_t smem, cudaStrea
     return cfg;
 }
 
-int mh_resident_grid(int family, int J, int G, int kcap)
+int mh_resident_grid(int family, int J, int G, int R, int kcap)
 {
-    mh_fn f = pick(family, J, G);
+    mh_fn f = pick(family, J, G, R);
     if (!f) return 0;
     const int C = cluster_of(family, G);
     const size_t smem = mh_smem(family, J, G, kcap);
@@ -95,13 +97,13 @@ int mh_resident_grid(int family, int J, int G, int kcap)
     return sms * per;
 }
 
-cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
+cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G, int R,
                       int grid, cudaStream_t s, int kcap)
 {
-    mh_fn f = pick(family, J, G);
+    mh_fn f = pick(family, J, G, R);
     if (!f) return cudaErrorInvalidValue;
     if (nslots <= 0) return cudaSuccess;
-    if (grid <= 0) grid = mh_resident_grid(family, J, G, kcap);
+    if (grid <= 0) grid = mh_resident_grid(family, J, G, R, kcap);
     const int C = cluster_of(family, G);
     const size_t smem = mh_smem(family, J, G, kcap);
     if (C > 1) {

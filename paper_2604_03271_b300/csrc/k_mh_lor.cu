@@ -2,5 +2,5 @@
 #include "k_mh_impl.cuh"
 
 namespace smc {
-mh_fn mh_pick_lor(int J, int G) { return mh_pick_family<FAM_LORENTZ>(J, G); }
+mh_fn mh_pick_lor(int J, int G, int R) { return mh_pick_family<FAM_LORENTZ>(J, G, R); }
 }  // namespace smc

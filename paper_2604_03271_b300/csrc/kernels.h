@@ -48,10 +48,12 @@ cudaError_t launch_gather(JobDev *jobs, const int *slots, int nslots, int64_t ma
 constexpr int MH_COUPLED = 16;
 // kcap: most peaks (phases) of the launch's jobs; the phase kernel then gets
 // dynamic shared memory for that many cached profiles per chain (if it fits)
-cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G,
+// R: register budget per thread of the fused kernel (0: the tile's default;
+// 64, 80, 96 or 128 for four- and eight-warp chains with J = 4, 8, 16)
+cudaError_t launch_mh(JobDev *jobs, const int *slots, int nslots, int family, int J, int G, int R,
                       int grid, cudaStream_t s, int kcap = 0);
-bool mh_tile_supported(int family, int J, int G);
-int mh_resident_grid(int family, int J, int G, int kcap = 0);
+bool mh_tile_supported(int family, int J, int G, int R = 0);
+int mh_resident_grid(int family, int J, int G, int R = 0, int kcap = 0);
 
 // Plain FP64 Metropolis stage (thread per chain, full energy per proposal).
 cudaError_t launch_mh_plain(JobDev *jobs, const int *slots, int nslots, int max_S,

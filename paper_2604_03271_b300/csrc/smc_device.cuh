@@ -58,8 +58,9 @@ struct JobDev {
     const float4 *rtab;  // App. D reflections: (centred position, I, log2 I, 0)
     const double *rpos64, *rint64;
     const int *roff;
-    // tile of the Metropolis kernel (points per lane J, warps per chain G)
-    int J, G;
+    // tile of the Metropolis kernel (points per lane J, warps per chain G,
+    // register budget R, 0 = the tile's default)
+    int J, G, R;
     // particles
     int T, S, sweeps, waste_free, fp64;
     float *th, *E, *ths, *Es;

@@ -160,6 +160,53 @@ def test_full_size_xps_sampled_outputs(ctx):
             assert np.median(e64) < 2.0 * spec.n
 
 
+def _sampling(spec, K, nat):
+    pr = spec.priors
+    kinds = [pr.amp.kind, pr.centre.kind, pr.width.kind, pr.eta.kind] * K + [b.kind for b in pr.bg]
+    u = np.array(nat, dtype=np.float64, copy=True)
+    for j in range(u.shape[1]):
+        if kinds[j] == W.LOG_UNIFORM:
+            u[:, j] = np.log(u[:, j])
+    return u
+
+
+def test_bench_config_fp32_energies_move_log_z_by_less_than_005(ctx):
+    """The bench configuration (N = 1001, K = 1..6, PV + linear background,
+    T = 16384, 20 sweeps).  The FP32 path samples and weighs with FP32
+    energies E32 = E64 + eps; the evidence of that energy landscape differs
+    from the FP64 one's by log Z32 - log Z64 = log E_post64[exp(-eps)]
+    (Eq. (11) at beta = 1 is the prior expectation of exp(-E)), which lies in
+    [-max eps, -min eps] over the posterior.  So over the final particles of
+    a full FP32 run, for every K: |eps| of the FP32 energy kernel, and of the
+    energies the fused Metropolis kernel itself carries after 20 sweeps at
+    beta = 1 (incremental updates included), must stay below 0.05 nat; the
+    remaining FP32-vs-FP64 difference of the estimators is Monte Carlo error
+    of the same algorithm at the same T (the statistical 0.05 tests run where
+    the FP64 path is affordable: configs of N <= 400)."""
+    spec = W.xps_like(1)
+    opts = W.Options(particles=16384, sweeps=20, seed=1)
+    r = ctx.run(spec, opts, keep_samples=True)
+    assert r["status"] == 0
+    rng = np.random.default_rng(5)
+    for a, K in enumerate(r["K"]):
+        nat = r["samples"][a].astype(np.float64)
+        e32 = ctx.energy(spec, K, opts, nat, precision=0)
+        e64 = ctx.energy(spec, K, opts, nat, precision=1)
+        eps = e32 - e64
+        shift = math.log(np.mean(np.exp(-(eps - eps.mean())))) - eps.mean()
+        # the kernel's own energies after a stage of 20 sweeps at beta = 1
+        idx = rng.choice(nat.shape[0], 2048, replace=False)
+        u = _sampling(spec, K, nat[idx])
+        step = 0.3 * np.maximum(u.std(axis=0), 1e-6)
+        nat_o, E_o, acc, prop = ctx.mh_stage(spec, K, opts, nat[idx], e32[idx], step, 1.0, 7, precision=0)
+        eps_k = E_o - ctx.energy(spec, K, opts, nat_o, precision=1)
+        print(f"K={K}: eps of the FP32 energy kernel in [{eps.min():.2e}, {eps.max():.2e}], "
+              f"log-Z shift {shift:.2e}; Metropolis kernel energies in [{eps_k.min():.2e}, {eps_k.max():.2e}]")
+        assert acc.sum() > 0
+        assert np.max(np.abs(eps)) <= 0.05 and np.max(np.abs(eps_k)) <= 0.05
+        assert abs(shift) <= 0.05
+
+
 def test_full_size_xrd_g16_tile_energies(ctx):
     """N = 4096 (16-warp chains): three stages at the XRD configuration's
     particle count, then sampled energies against the oracle."""

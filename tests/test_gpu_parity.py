@@ -8,7 +8,14 @@ Tolerances (stated per test) follow from the arithmetic:
   * FP32 energies: each term 1/2 w r^2 carries relative error ~ few ulp of the
     largest of (y, f) over sigma; Kahan keeps the sum's error at that level, so
     |E32 - E64| <= 2e-5 (E64 + N) (measured ~1e-6);
-  * full runs: |delta log Z| <= 0.05 nats and the same argmax K.
+  * full runs (estimators: FP32 trajectories decorrelate from the FP64 ones
+    after a few stages): the means over seeds of log Z from the FP32 path and
+    from the FP64 path (which replays the oracle) within 0.05 nat, with enough
+    seeds that three combined standard errors are within 0.05 too, where the
+    FP64 path's cost allows that (the 301-point Gaussian case); elsewhere within three
+    combined standard errors (printed), and the FP32 energies of the final
+    particles within 0.05 nat of the FP64 ones, which bounds the difference
+    of the two energy landscapes' evidences; the same argmax K.
 """
 import math
 
@@ -16,6 +23,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import diff_and_se, estimator_stats
 from paper_2604_03271_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -273,28 +281,26 @@ def test_full_run_fp64_replays_oracle(ctx):
 
 
 def test_full_run_fp32_matches_oracle_gaussian(ctx):
-    # With FP32 energies the trajectories leave the oracle's after a few
-    # stages (bisection and resampling boundaries move by rounding), so log Z
-    # is compared as an estimator: mean over seeds within max(0.05, 3 SE).
-    # The FP64 path replays the oracle exactly (checked on two seeds here) and
-    # supplies the FP64 replicates.
+    # The 301-point Gaussian case (K = 1..3).  With FP32 energies the
+    # trajectories leave the oracle's after a few stages (bisection and
+    # resampling boundaries move by rounding), so log Z is compared as an
+    # estimator: the mean over 64 seeds of the FP32 batched path against the
+    # mean over the same seeds of the FP64 path, which replays the oracle
+    # (checked on two seeds).  The bar is 0.05 nat absolute for every K, with
+    # enough seeds that three combined standard errors are within 0.05 too
+    # (per-seed SD at T = 4096, n = 10: 0.06-0.09 nat).
     spec = W.gaussian_small(1)
-    seeds = range(1, 17)
-    lz32, lz64 = [], []
-    for s in seeds:
-        o = W.Options(particles=1024, sweeps=10, seed=s)
-        lz32.append(ctx.run(spec, o, keep_samples=False)["log_z"])
-        lz64.append(ctx.run(spec, W.Options(particles=1024, sweeps=10, seed=s, energy_fp64=1),
-                            keep_samples=False)["log_z"])
+    seeds = range(1, 65)
+    lz32, lz64, k32, k64 = estimator_stats(ctx, spec, seeds, particles=4096, sweeps=10)
     for s in (1, 2):
-        ref = oracle.run(spec, W.Options(particles=1024, sweeps=10, seed=s))
+        ref = oracle.run(spec, W.Options(particles=4096, sweeps=10, seed=s))
         np.testing.assert_allclose(lz64[s - 1], ref["log_z"], atol=1e-6)
-    lz32, lz64 = np.array(lz32), np.array(lz64)
-    se = np.sqrt(lz32.var(axis=0, ddof=1) / len(seeds) + lz64.var(axis=0, ddof=1) / len(seeds))
-    diff = np.abs(lz32.mean(0) - lz64.mean(0))
-    assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
+    diff, se = diff_and_se(lz32, lz64)
+    print("gauss-301 |mean log Z FP32 - FP64| per K", diff, "SE", se)
+    assert np.all(3 * se <= 0.05), se
+    assert np.all(diff <= 0.05), (diff, se)
     # model selection: K = 2 (the truth) on every seed, both paths
-    assert np.all(np.argmax(lz32, axis=1) == 1) and np.all(np.argmax(lz64, axis=1) == 1)
+    assert set(k32) == set(k64) == {2}
 
 
 def test_posterior_means_within_two_standard_errors(ctx):
@@ -371,20 +377,29 @@ def test_max_stages_reported(ctx):
 # --------------------------------------------------------------------------
 
 def test_xps_shaped_fp32_vs_fp64_statistical(ctx):
+    # XPS-shaped (pseudo-Voigt + linear background on the 280 eV axis) at
+    # N = 301, K = 1..3, T = 2048: the FP32 and FP64 estimators over 48 seeds
+    # agree within three combined standard errors (printed; the per-seed SD of
+    # the over-complete K = 3 is above 1 nat here, so 0.05 nat is out of
+    # statistical reach at an affordable FP64 cost), the selected K agrees,
+    # and the FP32 energies of the final particles differ from FP64 ones by
+    # less than 0.05 nat, which bounds the difference of the two energy
+    # landscapes' evidences (log Z32 - log Z64 = log E_post[exp(-(E32 - E64))]).
     spec = W.xps_like(7, n=301, k_true=2, k_max=3)
-    lz32, lz64 = [], []
-    for s in range(1, 9):
-        o32 = W.Options(particles=1024, sweeps=4, seed=s)
-        o64 = W.Options(particles=1024, sweeps=4, seed=s, energy_fp64=1)
-        lz32.append(ctx.run(spec, o32, keep_samples=False)["log_z"])
-        lz64.append(ctx.run(spec, o64, keep_samples=False)["log_z"])
-    ref = oracle.run(spec, W.Options(particles=1024, sweeps=4, seed=1))
+    seeds = range(1, 49)
+    lz32, lz64, k32, k64 = estimator_stats(ctx, spec, seeds, particles=2048, sweeps=4)
+    ref = oracle.run(spec, W.Options(particles=2048, sweeps=4, seed=1))
     np.testing.assert_allclose(lz64[0], ref["log_z"], atol=1e-6)
-    lz32, lz64 = np.array(lz32), np.array(lz64)
-    se = np.sqrt(lz32.var(axis=0, ddof=1) / 8 + lz64.var(axis=0, ddof=1) / 8)
-    diff = np.abs(lz32.mean(0) - lz64.mean(0))
-    assert np.all(diff <= np.maximum(0.05, 3 * se)), (diff, se)
+    diff, se = diff_and_se(lz32, lz64)
+    print("xps-301 |mean log Z FP32 - FP64| per K", diff, "SE", se)
+    assert np.all(diff <= 3 * se), (diff, se)
     assert np.argmax(lz32.mean(0)) == np.argmax(lz64.mean(0))
+    r = ctx.run(spec, W.Options(particles=2048, sweeps=4, seed=1), keep_samples=True)
+    for a, K in enumerate(r["K"]):
+        nat = r["samples"][a].astype(np.float64)
+        eps = ctx.energy(spec, K, W.Options(), nat, precision=0) - ctx.energy(spec, K, W.Options(), nat,
+                                                                               precision=1)
+        assert np.max(np.abs(eps)) <= 0.05
 
 
 def test_whole_run_graph_equals_chunked_replay(ctx):
@@ -485,18 +500,54 @@ def test_history_step_rule_fp64_replays_oracle(ctx):
 
 def test_history_step_rule_fp32_estimator(ctx):
     # FP32 batched path with the history rule against the FP64 path with it,
-    # as estimators over seeds (0.05 nat, 3 SE <= 0.05), same selected K
+    # as estimators over 64 seeds on the 301-point Gaussian case (0.05 nat with 3 SE <= 0.05),
+    # same selected K
     spec = W.gaussian_small(1)
-    seeds = range(1, 129)
-    a = ctx.run_batch([(spec, W.Options(particles=4096, sweeps=5, seed=s, step_rule=1)) for s in seeds],
-                      keep_samples=False)
-    b = ctx.run_batch([(spec, W.Options(particles=4096, sweeps=5, seed=s, step_rule=1, energy_fp64=2))
-                       for s in seeds], keep_samples=False)
-    lz32 = np.array([r["log_z"] for r in a])
-    lz64 = np.array([r["log_z"] for r in b])
-    se = np.sqrt(lz32.var(axis=0, ddof=1) / len(seeds) + lz64.var(axis=0, ddof=1) / len(seeds))
-    diff = np.abs(lz32.mean(0) - lz64.mean(0))
+    lz32, lz64, k32, k64 = estimator_stats(ctx, spec, range(1, 65), particles=4096, sweeps=10,
+                                           step_rule=1)
+    diff, se = diff_and_se(lz32, lz64)
     print("history rule: |mean FP32 - mean FP64| per K", diff, "SE", se)
     assert np.all(3 * se <= 0.05), se
     assert np.all(diff <= 0.05), (diff, se)
-    assert all(r["argmax_k"] == 2 for r in a + b)
+    assert set(k32) == set(k64) == {2}
+
+
+# --------------------------------------------------------------------------
+# Every tile of the shipped table against the oracle in a Metropolis stage
+# --------------------------------------------------------------------------
+
+def _table_rows():
+    import json
+    import os
+    from paper_2604_03271_b300 import autotune
+    if not os.path.exists(autotune.TABLE):
+        return []
+    rows = json.load(open(autotune.TABLE))["tiles"]
+    return [r for r in rows if not r["family"] & autotune.COUPLED]
+
+
+@pytest.mark.parametrize("row", _table_rows(), ids=lambda r: f"fam{r['family']}-n{r['n_max']}-J{r['J']}-G{r['G']}-R{r.get('R', 0)}")
+def test_mh_fp32_tracks_oracle_every_tuned_tile(row):
+    # the fused kernel at the tile (and register budget) the table ships for
+    # this family and grid bucket, on a spectrum of that bucket's length: the
+    # same random streams as the oracle, accept counts equal up to FP32
+    # knife-edge flips, final energies those of the final states
+    from paper_2604_03271_b300 import api
+    fam, n = int(row["family"]), int(row["n_max"])
+    spec = W.xps_like(3, n=n, k_true=2, k_max=3)
+    if fam != W.PSEUDO_VOIGT:
+        spec.family = fam
+        spec.priors = W.Priors(amp=spec.priors.amp, centre=spec.priors.centre,
+                               width=spec.priors.width, bg=spec.priors.bg)
+    K = 3
+    with api.Context(0) as c:
+        c.set_tile(fam, n, int(row["J"]), int(row["G"]), int(row.get("R", 0)))
+        opts = W.Options(particles=192, sweeps=3, seed=17)
+        u, nat, E = _starts(spec, K, opts, 192)
+        step = 0.2 * np.maximum(np.std(u, axis=0), 1e-3)
+        u_or, E_or, acc_or, prop_or = oracle.mh_stage(spec, K, opts, u, E, step, 1e-3, 3)
+        nat_g, E_g, acc_g, prop_g = c.mh_stage(spec, K, opts, nat, E, step, 1e-3, 3, precision=0)
+    np.testing.assert_array_equal(prop_g, prop_or)
+    assert np.abs(acc_g - acc_or).sum() <= 0.02 * prop_or.sum() + 3
+    E_true = oracle.energies(spec, K, opts, _to_sampling(spec, K, nat_g))
+    assert np.all(np.abs(E_g - E_true) <= 2e-5 * (E_true + spec.n))
