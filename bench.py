@@ -1,13 +1,18 @@
 #!/usr/bin/env python
 """Throughput benchmark of the batched FP32-energy SMC sampler.
 
-Workload (default): XPS-shaped spectra -- N = 1001 points on a 20 eV binding
-energy axis at 280 eV, 4 true pseudo-Voigt peaks on a linear background,
-counting-like noise -- fitted with pseudo-Voigt peaks + linear background for
-every K = 1..6 at once, 16384 particles per K, 20 Metropolis sweeps per stage,
+Workload (default): one XRD-shaped spectrum per step -- N = 4096 points on
+2 theta in [10, 90] degrees, 10 sparse Lorentzian / pseudo-Voigt peaks with
+amplitudes over three decades on a cubic background, Gaussian noise of 1 % of
+the maximum -- fitted with pseudo-Voigt peaks + cubic Chebyshev background for
+every K = 1..12 at once, 65536 particles per K, 20 Metropolis sweeps per stage,
 ESS target 0.5 (seeded synthetic data, see paper_2604_03271_b300/workloads.py).
-One step = one full SMC run (prior to beta = 1, every K) over a batch of B
-spectra.  Metric: spectra/s (higher is better).
+`--workload xps` is the XPS-shaped one (N = 1001, K = 1..6, 16384 particles
+per K, two spectra per step).  One step = one full SMC run (prior to beta = 1,
+every K) over a batch of B spectra.  Metric: spectra/s (higher is better).
+The timed region runs the shipped launch path (one CUDA graph launch per
+run); per-kernel event times (kernel shares, the Metropolis kernel's roofline)
+come from a separate untimed pass right after it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,11 +43,11 @@ from paper_2604_03271_b300.sharding import max_over_ranks, shard_seeds  # noqa: 
 
 METRIC = "spectra/s (all candidate K per spectrum, |dlogZ|<=0.05 vs FP64)"
 SM_COUNT = 148
-# DRAM bytes (read + write) of one k_mh launch from an ncu capture of the
-# XPS-shaped workload (one spectrum per step), valid only for the kernel source
-# (k_mh_impl.cuh, by sha1) it was taken on; scaled by the spectra a launch
+# DRAM bytes (read + write) of one k_mh launch per spectrum, from ncu captures
+# of one spectrum per step, per workload; valid only for the kernel source
+# (k_mh_impl.cuh, by sha1) they were taken on; scaled by the spectra a launch
 # processes (the particle state of each spectrum's jobs is its own)
-MH_TRAFFIC = {"sha1": "0dc5128c1393", "bytes_per_spectrum": 6.380e6 + 0.481e6, "workload": "xps"}
+MH_TRAFFIC = {"xps": {"sha1": "0dc5128c1393", "bytes_per_spectrum": 6.380e6 + 0.481e6}}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
@@ -259,17 +264,23 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="xps", choices=["xps", "xps_wf", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "xrd_phase_5000",
+    ap.add_argument("--workload", default="xrd", choices=["xps", "xps_wf", "xrd", "gauss", "mixed", "xps_shirley", "xrd_phase", "xrd_phase_5000",
                                                        "xrd_phase_10000", "deconv3", "deconv10",
                                                        "deconv30"])
-    ap.add_argument("--batch", type=int, default=2, help="spectra per step per GPU")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="spectra per step per GPU (default: 1 for xrd, 2 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain-sample", type=int, default=1, help="time the plain FP64 path on a sample")
-    ap.add_argument("--serve-rate", type=float, default=1.0, help="Poisson arrivals per s (0: skip)")
+    ap.add_argument("--plain-sample", type=int, default=None,
+                    help="time the plain FP64 path on a sample (default: on, except for xrd, where one "
+                         "plain stage of K = 12 takes minutes)")
+    ap.add_argument("--serve-rate", type=float, default=None,
+                    help="Poisson arrivals per s (0: skip; default 1.0, 0 for xrd: its serving is the "
+                         "separate --serving-sweep)")
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--event-steps", type=int, default=1,
                     help="steps of the untimed per-kernel event pass (kernel shares, roofline)")
-    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass")
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end pass (default 3, 1 for xrd)")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the serving sweep (Poisson mix of XPS- and XRD-shaped requests)")
     ap.add_argument("--serve-rates", default="0.5,1.0,3.0")
@@ -282,6 +293,15 @@ def main():
     if args.serving_sweep:
         serving_sweep(args)
         return
+    big = args.workload == "xrd"
+    if args.batch is None:
+        args.batch = 1 if big else 2
+    if args.plain_sample is None:
+        args.plain_sample = 0 if big else 1
+    if args.serve_rate is None:
+        args.serve_rate = 0.0 if big else 1.0
+    if args.e2e_steps is None:
+        args.e2e_steps = 1 if big else 3
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -403,9 +423,11 @@ def main():
     nominal = SM_COUNT * SFU_PER_SM_CLK * 2032e6 / 1e9
     import hashlib
     src = open(os.path.join(ROOT, "paper_2604_03271_b300", "csrc", "k_mh_impl.cuh"), "rb").read()
-    same_kernel = hashlib.sha1(src).hexdigest()[:12] == MH_TRAFFIC["sha1"]
-    traffic = (MH_TRAFFIC["bytes_per_spectrum"] * B / (mh_n / max(1, n_ev * B))
-               if same_kernel and args.workload == MH_TRAFFIC["workload"] else None)
+    tr = MH_TRAFFIC.get(args.workload)
+    same_kernel = tr is not None and hashlib.sha1(src).hexdigest()[:12] == tr["sha1"]
+    # per launch: the bytes of the spectra one launch processes (a launch
+    # advances every spectrum of the step by one stage)
+    traffic = tr["bytes_per_spectrum"] * B if same_kernel else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_mh (fused Metropolis)", "avg_launch_ms": mh_ms / mh_n,

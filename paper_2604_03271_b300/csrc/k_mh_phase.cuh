@@ -137,26 +137,32 @@ __device__ __forceinline__ void mhp_cl_store_i(const void *local, unsigned rank,
 }
 
 // Cluster-wide sum of one value per warp (v: the warp's total, equal in its
-// lanes); every thread of every CTA returns the same sum (CTA order, then warp
-// order).  xch: [2][MHP_MAX_CL * G] in this CTA's shared memory.
+// lanes); every thread of every CTA returns the same sum.  Two levels: the
+// CTA adds its warps' values in warp order (ctab: [2][G] in this CTA's shared
+// memory, one CTA barrier), then its first warp pushes the CTA total into
+// every CTA of the cluster (xch: [2][.] in each CTA's shared memory, one
+// cluster barrier) and each CTA adds the C totals in CTA order, so every CTA
+// takes the same decision from the same bits.
 template <int G>
-__device__ __forceinline__ float mhp_cl_sum(float (*xch)[MHP_MAX_CL * G], int &cpar, unsigned crank,
-                                            unsigned csize, int gw, int lane, float v)
+__device__ __forceinline__ float mhp_cl_sum(float (*xch)[MHP_MAX_CL * G], float (*ctab)[G], int &cpar,
+                                            unsigned crank, unsigned csize, int gw, int lane, float v)
 {
-    if ((unsigned)lane < csize) mhp_cl_store(&xch[cpar][crank * G + gw], (unsigned)lane, v);
+    if (lane == 0) ctab[cpar][gw] = v;
+    __syncthreads();
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < G; w += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(&ctab[cpar][w]);
+        t += q.x;
+        t += q.y;
+        t += q.z;
+        t += q.w;
+    }
+    if (gw == 0 && (unsigned)lane < csize) mhp_cl_store(&xch[cpar][crank], (unsigned)lane, t);
     __syncwarp();
     mhp_cl_sync();
     float s = 0.0f;
-    for (unsigned r = 0; r < csize; ++r) {
-#pragma unroll
-        for (int w = 0; w < G; w += 4) {
-            const float4 q = *reinterpret_cast<const float4 *>(&xch[cpar][r * G + w]);
-            s += q.x;
-            s += q.y;
-            s += q.z;
-            s += q.w;
-        }
-    }
+    for (unsigned r = 0; r < csize; ++r) s += xch[cpar][r];
     cpar ^= 1;
     return s;
 }
@@ -192,11 +198,12 @@ __device__ __forceinline__ unsigned mhp_dyn_smem_bytes()
 
 // A proposal's dE: the group sum, then (clusters) the exchange between CTAs
 template <int G, bool CL>
-__device__ __forceinline__ float mhp_dE(GroupCtx<G> &g, float (*xch)[CL ? MHP_MAX_CL * G : 4], int &cpar,
-                                        unsigned crank, unsigned csize, float v)
+__device__ __forceinline__ float mhp_dE(GroupCtx<G> &g, float (*xch)[CL ? MHP_MAX_CL * G : 4],
+                                        float (*ctab)[G], int &cpar, unsigned crank, unsigned csize,
+                                        float v)
 {
     if constexpr (CL)
-        return mhp_cl_sum<G>(xch, cpar, crank, csize, g.gw, g.lane, warp_sum(v));
+        return mhp_cl_sum<G>(xch, ctab, cpar, crank, csize, g.gw, g.lane, warp_sum(v));
     else
         return group_sum(g, v);
 }
@@ -205,12 +212,13 @@ __device__ __forceinline__ float mhp_dE(GroupCtx<G> &g, float (*xch)[CL ? MHP_MA
 // totals added in CTA order
 template <int J, int G, bool CL>
 __device__ __forceinline__ float mhp_chain_energy(GroupCtx<G> &g, const float (&e)[J],
-                                                  float (*xch)[CL ? MHP_MAX_CL * G : 4], int &cpar,
-                                                  unsigned crank, unsigned csize)
+                                                  float (*xch)[CL ? MHP_MAX_CL * G : 4],
+                                                  float (*ctab)[G], int &cpar, unsigned crank,
+                                                  unsigned csize)
 {
     const float E = mhf_group_energy<J, G>(g, e);
     if constexpr (CL)
-        return mhp_cl_sum<G>(xch, cpar, crank, csize, g.gw, g.lane, g.gw == 0 ? E : 0.0f);
+        return mhp_cl_sum<G>(xch, ctab, cpar, crank, csize, g.gw, g.lane, g.gw == 0 ? E : 0.0f);
     else
         return E;
 }
@@ -237,6 +245,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
     __shared__ WarpComp comp_sh[NT / 32];
     __shared__ PropTable prop_sh[NT / 32 / G][2];
     __shared__ __align__(16) float xch_sh[CL ? 2 : 1][CL ? MHP_MAX_CL * G : 4];
+    __shared__ __align__(16) float ctab_sh[2][G < 4 ? 4 : G];  // a CTA's warp totals (clusters)
     __shared__ int claim_sh[2][2];
     unsigned crank = 0, csize = 1;
     int cpar = 0;
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                                 p0 += en[jj] - e[jj];
                         }
                     }
-                    const float dE = mhp_dE<G, CL>(g, xch_sh, cpar, crank, csize, p0 + p1);
+                    const float dE = mhp_dE<G, CL>(g, xch_sh, (float(*)[G])ctab_sh, cpar, crank, csize, p0 + p1);
                     if (tj < -beta * dE) {
                         if (c == 0) {
                             const float dA = v - A;
@@ -511,7 +520,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                     else
                         p0 += en[jj] - e[jj];
                 }
-                const float dE = mhp_dE<G, CL>(g, xch_sh, cpar, crank, csize, p0 + p1);
+                const float dE = mhp_dE<G, CL>(g, xch_sh, (float(*)[G])ctab_sh, cpar, crank, csize, p0 + p1);
                 if (tj < -beta * dE) {
 #pragma unroll
                     for (int jj = 0; jj < J; ++jj) {
@@ -542,7 +551,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
                 }
             }
             if (wf) {
-                const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, cpar, crank, csize);
+                const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, (float(*)[G])ctab_sh, cpar, crank, csize);
                 const size_t o = (size_t)m * n + sw;
                 if (g.gw == 0 && crank == 0) {
                     for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + o] = cs.th[j];
@@ -551,7 +560,7 @@ __global__ void __launch_bounds__((MhpBounds<J, G, CL>::NT), (MhpBounds<J, G, CL
             }
         }
         if (!wf) {
-            const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, cpar, crank, csize);
+            const float E = mhp_chain_energy<J, G, CL>(g, e, xch_sh, (float(*)[G])ctab_sh, cpar, crank, csize);
             if (g.gw == 0 && crank == 0) {
                 for (int j = lane; j < d; j += 32) jb.th[(size_t)j * T + m] = cs.th[j];
                 if (lane == 0) jb.E[m] = E;
