@@ -202,15 +202,25 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def oracle_rate_all_cores(name: str, seconds: float) -> dict:
-    """oracle_rate on every host core at once: one process per core (started
-    with spawn, so no CUDA state is inherited), each timing its own bounded
-    sample for `seconds`; the rates add up."""
+def oracle_pool():
+    """One process per host core, started with spawn (no CUDA state inherited)."""
     import multiprocessing as mp
+    return mp.get_context("spawn").Pool(os.cpu_count() or 1)
 
+
+def oracle_rate_all_cores(name: str, seconds: float, pool=None) -> dict:
+    """oracle_rate on every host core at once: one process per core, each
+    timing its own bounded sample for `seconds`; the rates add up."""
     procs = os.cpu_count() or 1
-    with mp.get_context("spawn").Pool(procs) as pool:
+    own = pool is None
+    if own:
+        pool = oracle_pool()
+    try:
         res = pool.map(_oracle_worker, [(name, seconds)] * procs)
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     rate = sum(r["units_per_s"] for r in res)
     chains = res[0]["sample"].split(" chains")[0]
     return {"units_per_s": rate, "seconds": max(r["seconds"] for r in res), "cores": procs,
@@ -231,11 +241,14 @@ def reference_arm(args, world: int, rank: int):
         return
     step_s = []
     rates = []
+    pool = oracle_pool()
     for k in range(args.warmup + args.steps):
-        r = oracle_rate_all_cores(name, seconds=max(2.0, 60.0 / (args.warmup + args.steps)))
+        r = oracle_rate_all_cores(name, seconds=max(2.0, 60.0 / (args.warmup + args.steps)), pool=pool)
         if k >= args.warmup:
             step_s.append(r["seconds"])
             rates.append(r["units_per_s"])
+    pool.close()
+    pool.join()
     rate = float(np.mean(rates))
     value = rate / per_spec
     line = {"metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,

@@ -35,6 +35,7 @@ namespace smc {
 
 constexpr int MH_MAX_GROUPS = 16;  // warps per chain at most, and chains per block at most
 
+
 template <int FAM>
 __device__ __forceinline__ void shape(float x, float mu, float sc, float &S0, float &S1)
 {
@@ -63,8 +64,7 @@ __device__ __forceinline__ float unit_of(float S0, float S1, float eta)
 template <int G>
 struct GroupCtx {
     int lane, gw, grp;
-    float *red;   // [2][G] for this group
-    float *red4;  // [2][4][max(G, 4)] for this group (group_sum4)
+    float *red;  // [2][G] for this group
     int par;
 };
 
@@ -101,53 +101,6 @@ __device__ __forceinline__ float group_sum(GroupCtx<G> &g, float v)
     }
     g.par ^= 1;
     return s;
-}
-
-// Four sums over the group at once.  Within a warp the four values are
-// reduced by a transposing butterfly: after the exchange across 16 lanes each
-// lane keeps two of the four partial sums, after the one across 8 lanes one,
-// and three more steps finish it, so lane 8 v (v < 4) ends with the warp's
-// total of value v: 6 shuffles instead of 20.  Across warps one barrier and
-// a fixed-order sum, as in group_sum.
-template <int G>
-__device__ __forceinline__ float4 group_sum4(GroupCtx<G> &g, float a0, float a1, float a2, float a3)
-{
-    const bool b4 = (g.lane & 16) != 0, b3 = (g.lane & 8) != 0;
-    const float k0 = (b4 ? a2 : a0) + __shfl_xor_sync(FULL_MASK, b4 ? a0 : a2, 16);
-    const float k1 = (b4 ? a3 : a1) + __shfl_xor_sync(FULL_MASK, b4 ? a1 : a3, 16);
-    float m = (b3 ? k1 : k0) + __shfl_xor_sync(FULL_MASK, b3 ? k0 : k1, 8);
-    m += __shfl_xor_sync(FULL_MASK, m, 4);
-    m += __shfl_xor_sync(FULL_MASK, m, 2);
-    m += __shfl_xor_sync(FULL_MASK, m, 1);
-    if constexpr (G == 1) {
-        return make_float4(__shfl_sync(FULL_MASK, m, 0), __shfl_sync(FULL_MASK, m, 8),
-                           __shfl_sync(FULL_MASK, m, 16), __shfl_sync(FULL_MASK, m, 24));
-    } else {
-        constexpr int GR = G < 4 ? 4 : G;
-        float *slot = g.red4 + g.par * 4 * GR;
-        if ((g.lane & 7) == 0) slot[(g.lane >> 3) * GR + g.gw] = m;
-        named_barrier(1 + g.grp, 32 * G);
-        float s[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            s[v] = 0.0f;
-            if constexpr (G % 4 == 0) {
-#pragma unroll
-                for (int w = 0; w < G; w += 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(slot + v * GR + w);
-                    s[v] += q.x;
-                    s[v] += q.y;
-                    s[v] += q.z;
-                    s[v] += q.w;
-                }
-            } else {
-#pragma unroll
-                for (int w = 0; w < G; ++w) s[v] += slot[v * GR + w];
-            }
-        }
-        g.par ^= 1;
-        return make_float4(s[0], s[1], s[2], s[3]);
-    }
 }
 
 // Kahan-compensated energy 1/2 sum w r^2 over the group
@@ -256,9 +209,13 @@ struct MhMinBlocks {
                                         : (65536 / (NT * R) > 0 ? 65536 / (NT * R) : 1);
 };
 
+__device__ __forceinline__ f2 neg2(f2 a) { return mul2(a, splat2(-1.0f)); }
+
 // Packed form of shape() for two grid points: the argument in f32x2
 // arithmetic, one MUFU operation per point and transcendental.  Each half is
-// bit-identical to shape() of that point.
+// bit-identical to shape() of that point.  (A Newton-Raphson reciprocal on the
+// FMA pipe in place of the SFU's was measured slower: the kernel is bound by
+// issue and latency, not by the SFU.)
 template <int FAM>
 __device__ __forceinline__ void shape2(f2 x, f2 sc, f2 nmsc, f2 &S0, f2 &S1)
 {
@@ -277,8 +234,6 @@ __device__ __forceinline__ void shape2(f2 x, f2 sc, f2 nmsc, f2 &S0, f2 &S1)
         }
     }
 }
-
-__device__ __forceinline__ f2 neg2(f2 a) { return mul2(a, splat2(-1.0f)); }
 
 // group_energy() on packed points (pair p holds points 2p and 2p + 1; the
 // compensated sum runs over them in that order)
@@ -304,8 +259,6 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
     constexpr int JP = J / 2;
     constexpr int NT = MhThreads<G>::NT;
     __shared__ __align__(16) float red_sh[MH_MAX_GROUPS][2][MH_MAX_GROUPS];
-    constexpr int GR = G < 4 ? 4 : G;
-    __shared__ __align__(16) float red4_sh[NT / 32 / G][2][4][GR];
     __shared__ int work_sh[MH_MAX_GROUPS][2];
     __shared__ WarpComp comp_sh[NT / 32];
     __shared__ PropTable prop_sh[NT / 32 / G][2];  // one double-buffered table per chain
@@ -318,7 +271,6 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
     constexpr int ngroups = (NT / 32) / G;
     if (g.grp >= ngroups) return;
     g.red = &red_sh[g.grp][0][0];
-    g.red4 = &red4_sh[g.grp][0][0][0];
     const int lane = g.lane;
     WarpComp &cs = comp_sh[warp];
     constexpr int P = (FAM == FAM_PV) ? 4 : 3;
@@ -480,191 +432,88 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     tq[c] = q2.x;
                     vq[c] = q2.y;
                 }
-                // ---- amplitude and centre in one pass and one reduction.  The
-                // centre's change is taken at unit amplitude, Dm = U' - U, so
-                // that its dE follows for either outcome of the amplitude
-                // proposal: with A* = A' if that move is accepted (residual
-                // then R + 2 h D_A) and A otherwise,
-                //   dE_mu = A*^2 sum h Dm^2 + A* (sum Dm R + [accepted] 2 sum h Dm D_A),
-                // exactly the sequential order of the sweep.
-                {
-                    const bool pA = tq[0] != INFINITY, pM = tq[1] != INFINITY;
-                    if (pA || pM) {
-                        n_eval += (unsigned)pA + (unsigned)pM;
-                        const f2 dA = splat2(pA ? vq[0] - A : 0.0f);
-                        f2 sA = splat2(0.0f), sMM = sA, sMR = sA, sMA = sA;
-                        if (pM) {
-                            ++n_shape;
-                            const f2 scv = splat2(sc), nmsc = splat2(-vq[1] * sc), et = splat2(eta);
 #pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                f2 l = splat2(0.0f);
-                                shape2<FAM>(x[p], scv, nmsc, N0[p], l);
-                                if (FAM == FAM_PV) N1[p] = fma2(et, N0[p], l);
-                                const f2 U = FAM == FAM_PV ? S1[p] : S0[p];
-                                const f2 DA = mul2(dA, U);
-                                sA = fma2(DA, fma2(w[p], DA, r[p]), sA);
-                                const f2 Dm = sub2(FAM == FAM_PV ? N1[p] : N0[p], U);
-                                const f2 q = mul2(w[p], Dm);
-                                sMM = fma2(q, Dm, sMM);
-                                sMR = fma2(Dm, r[p], sMR);
-                                sMA = fma2(q, DA, sMA);
-                            }
-                        } else {
+                for (int c = 0; c < P; ++c) {
+                    const int j = j0 + c;
+                    const float tj = tq[c];
+                    if (tj == INFINITY) continue;  // fixed or outside the prior's support
+                    const float v = vq[c];
+                    ++n_eval;
+                    // lanes of the packed accumulator: even and odd points
+                    f2 acc2 = splat2(0.0f);
+                    if (c == 0) {  // amplitude: D = (A' - A) U
+                        const f2 dA = splat2(v - A);
 #pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                const f2 DA = mul2(dA, FAM == FAM_PV ? S1[p] : S0[p]);
-                                sA = fma2(DA, fma2(w[p], DA, r[p]), sA);
-                            }
+                        for (int p = 0; p < JP; ++p) {
+                            const f2 D = mul2(dA, FAM == FAM_PV ? S1[p] : S0[p]);
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
-                        const float4 t = group_sum4(g, lo2(sA) + hi2(sA), lo2(sMM) + hi2(sMM),
-                                                    lo2(sMR) + hi2(sMR), lo2(sMA) + hi2(sMA));
-                        const bool accA = pA && tq[0] < -beta * t.x;
-                        const float As = accA ? vq[0] : A;
-                        bool accM = false;
-                        if (pM) {
-                            const float eM = As * As * t.y + As * (t.z + (accA ? 2.0f * t.w : 0.0f));
-                            accM = tq[1] < -beta * eM;
-                        }
-                        if (accA || accM) {
-                            const f2 cA = splat2(accA ? 2.0f * (vq[0] - A) : 0.0f), cM = splat2(As + As);
+                    } else if (c == 3) {  // mixing ratio: D = A (eta' - eta) (G - L)
+                        const f2 dd = splat2(A * (v - eta));
 #pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                const f2 U = FAM == FAM_PV ? S1[p] : S0[p];
-                                f2 tt = mul2(cA, U);
-                                if (accM) {
-                                    tt = fma2(cM, sub2(FAM == FAM_PV ? N1[p] : N0[p], U), tt);
-                                    S0[p] = N0[p];
-                                    if (FAM == FAM_PV) S1[p] = N1[p];
-                                }
-                                r[p] = fma2(w[p], tt, r[p]);
-                            }
-                            if (accM) mu = vq[1];
-                            A = As;
-                            if (lane == 0) {
-                                if (accA) {
-                                    cs.th[j0] = tb.un[j0];
-                                    cs.nat[j0] = vq[0];
-                                    cs.acc[j0] += 1u;
-                                }
-                                if (accM) {
-                                    cs.th[j0 + 1] = tb.un[j0 + 1];
-                                    cs.nat[j0 + 1] = vq[1];
-                                    cs.acc[j0 + 1] += 1u;
-                                }
-                            }
-                            __syncwarp();
+                        for (int p = 0; p < JP; ++p) {
+                            const f2 D = mul2(dd, S0[p]);
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
-                    }
-                }
-                if constexpr (FAM == FAM_PV) {
-                    // ---- width and mixing ratio in one pass and one reduction:
-                    // the mixing ratio's change D_eta = A (eta' - eta) (G - L) is
-                    // evaluated with the current width's G - L and with the
-                    // proposed one's (then against the residual after the width
-                    // move, R + 2 h D_w), and the width's outcome picks one
-                    const bool pW = tq[2] != INFINITY, pE = tq[3] != INFINITY;
-                    if (pW || pE) {
-                        n_eval += (unsigned)pW + (unsigned)pE;
-                        const float de = pE ? vq[3] - eta : 0.0f;
-                        const f2 cE = splat2(A * de), Av = splat2(A);
-                        f2 sW = splat2(0.0f), sE0 = sW, sE1 = sW;
-                        float scw = sc;
-                        if (pW) {
-                            ++n_shape;
-                            scw = sc2_of<FAM>(vq[2], wprec);
-                            const f2 scv = splat2(scw), nmsc = splat2(-mu * scw), et = splat2(eta);
-#pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                f2 l = splat2(0.0f);
-                                shape2<FAM>(x[p], scv, nmsc, N0[p], l);
-                                N1[p] = fma2(et, N0[p], l);
-                                const f2 Dw = mul2(Av, sub2(N1[p], S1[p]));
-                                sW = fma2(Dw, fma2(w[p], Dw, r[p]), sW);
-                                const f2 De0 = mul2(cE, S0[p]);
-                                sE0 = fma2(De0, fma2(w[p], De0, r[p]), sE0);
-                                const f2 De1 = mul2(cE, N0[p]);
-                                sE1 = fma2(De1, fma2(w[p], fma2(splat2(2.0f), Dw, De1), r[p]), sE1);
-                            }
-                        } else {
-#pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                const f2 De0 = mul2(cE, S0[p]);
-                                sE0 = fma2(De0, fma2(w[p], De0, r[p]), sE0);
-                            }
-                        }
-                        const float4 t = group_sum4(g, lo2(sW) + hi2(sW), lo2(sE0) + hi2(sE0),
-                                                    lo2(sE1) + hi2(sE1), 0.0f);
-                        const bool accW = pW && tq[2] < -beta * t.x;
-                        const bool accE = pE && tq[3] < -beta * (accW ? t.z : t.y);
-                        if (accW || accE) {
-                            const f2 A2 = splat2(A + A), cE2 = splat2(2.0f * A * de), dev = splat2(de);
-#pragma unroll
-                            for (int p = 0; p < JP; ++p) {
-                                if (accW) {
-                                    r[p] = fma2(w[p], mul2(A2, sub2(N1[p], S1[p])), r[p]);
-                                    S0[p] = N0[p];
-                                    S1[p] = N1[p];
-                                }
-                                if (accE) {
-                                    r[p] = fma2(w[p], mul2(cE2, S0[p]), r[p]);
-                                    S1[p] = fma2(dev, S0[p], S1[p]);
-                                }
-                            }
-                            if (accW) {
-                                wd = vq[2];
-                                sc = scw;
-                            }
-                            if (accE) eta = vq[3];
-                            if (lane == 0) {
-                                if (accW) {
-                                    cs.th[j0 + 2] = tb.un[j0 + 2];
-                                    cs.nat[j0 + 2] = vq[2];
-                                    cs.acc[j0 + 2] += 1u;
-                                }
-                                if (accE) {
-                                    cs.th[j0 + 3] = tb.un[j0 + 3];
-                                    cs.nat[j0 + 3] = vq[3];
-                                    cs.acc[j0 + 3] += 1u;
-                                }
-                            }
-                            __syncwarp();
-                        }
-                    }
-                } else {
-                    // ---- width (Gaussian, Lorentzian): its own pass and reduction
-                    const float tj = tq[2];
-                    if (tj != INFINITY) {
-                        ++n_eval;
+                    } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
-                        const float v = vq[2];
-                        const float scn = sc2_of<FAM>(v, wprec);
-                        const f2 scv = splat2(scn), nmsc = splat2(-mu * scn), Av = splat2(A);
-                        f2 acc2 = splat2(0.0f);
+                        const float mu2 = (c == 1) ? v : mu;
+                        const float scn = (c == 2) ? sc2_of<FAM>(v, wprec) : sc;
+                        const f2 scv = splat2(scn), nmsc = splat2(-mu2 * scn), et = splat2(eta),
+                                 Av = splat2(A);
 #pragma unroll
                         for (int p = 0; p < JP; ++p) {
                             f2 l = splat2(0.0f);
                             shape2<FAM>(x[p], scv, nmsc, N0[p], l);
-                            const f2 D = mul2(Av, sub2(N0[p], S0[p]));
+                            if (FAM == FAM_PV) N1[p] = fma2(et, N0[p], l);
+                            const f2 D = mul2(Av, FAM == FAM_PV ? sub2(N1[p], S1[p]) : sub2(N0[p], S0[p]));
                             acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
-                        const float dE = group_sum(g, lo2(acc2) + hi2(acc2));
-                        if (tj < -beta * dE) {
+                    }
+                    const float dE = group_sum(g, lo2(acc2) + hi2(acc2));
+                    if (tj < -beta * dE) {
+                        if (c == 0) {
+                            const float dA = v - A;
+                            const f2 d2 = splat2(dA + dA);
+#pragma unroll
+                            for (int p = 0; p < JP; ++p)
+                                r[p] = fma2(w[p], mul2(d2, FAM == FAM_PV ? S1[p] : S0[p]), r[p]);
+                            A = v;
+                        } else if (c == 3) {
+                            const float de = v - eta;
+                            const float dd = A * de;
+                            const f2 dd2 = splat2(dd + dd), de2 = splat2(de);
+#pragma unroll
+                            for (int p = 0; p < JP; ++p) {
+                                r[p] = fma2(w[p], mul2(dd2, S0[p]), r[p]);
+                                S1[p] = fma2(de2, S0[p], S1[p]);
+                            }
+                            eta = v;
+                        } else {
                             const f2 AA = splat2(A + A);
 #pragma unroll
                             for (int p = 0; p < JP; ++p) {
-                                r[p] = fma2(w[p], mul2(AA, sub2(N0[p], S0[p])), r[p]);
+                                if (FAM == FAM_PV) {
+                                    r[p] = fma2(w[p], mul2(AA, sub2(N1[p], S1[p])), r[p]);
+                                    S1[p] = N1[p];
+                                } else {
+                                    r[p] = fma2(w[p], mul2(AA, sub2(N0[p], S0[p])), r[p]);
+                                }
                                 S0[p] = N0[p];
                             }
-                            wd = v;
-                            sc = scn;
-                            if (lane == 0) {
-                                cs.th[j0 + 2] = tb.un[j0 + 2];
-                                cs.nat[j0 + 2] = v;
-                                cs.acc[j0 + 2] += 1u;
+                            if (c == 1) {
+                                mu = v;
+                            } else {
+                                wd = v;
+                                sc = sc2_of<FAM>(v, wprec);
                             }
-                            __syncwarp();
                         }
+                        if (lane == 0) {
+                            cs.th[j] = tb.un[j];
+                            cs.nat[j] = v;
+                            cs.acc[j] += 1u;
+                        }
+                        __syncwarp();
                     }
                 }
             }
