@@ -424,8 +424,23 @@ def main():
     # launch's average event-timed duration
     mh_ms = prof_ev["ms"]["metropolis"]
     mh_n = max(1, prof_ev["launches"]["metropolis"])
-    sfu_per_launch = (prof_ev["sfu_ops"] + 2.0 * prof_ev["lg2_ops"]) / mh_n
-    achieved = sfu_per_launch / (mh_ms / mh_n / 1000.0) / 1e9 if mh_ms > 0 else 0.0
+    launch_s = mh_ms / mh_n / 1000.0
+    # the kernel's own count: SFU operations of the centre / width proposals
+    # (the current shape's re-evaluation per block not counted)
+    sfu_kernel = (prof_ev["sfu_ops"] + 2.0 * prof_ev["lg2_ops"]) / mh_n
+    achieved_kernel = sfu_kernel / launch_s / 1e9 if mh_ms > 0 else 0.0
+    # the method's count per unit (one new peak evaluation per peak-component
+    # point evaluation: EX2 for a Gaussian, RCP for a Lorentzian, both for a
+    # pseudo-Voigt; none for background components) x the units of a launch
+    if prof_ev.get("peak_point_evals", 0.0) > 0:
+        units_launch = prof_ev["peak_point_evals"] / mh_n
+        sfu_per_launch = units_launch * prof_ev["peak_sfu_per_eval"]
+        count = "method count: %.0f SFU op per peak-component point evaluation" % prof_ev["peak_sfu_per_eval"]
+    else:
+        units_launch = None
+        sfu_per_launch = sfu_kernel
+        count = "kernel count: SFU ops of evaluated shape proposals"
+    achieved = sfu_per_launch / launch_s / 1e9 if mh_ms > 0 else 0.0
     # denominator: the SFU rate measured on this device for the workload's mix
     # of EX2, RCP and LG2 (time-weighted harmonic combination of the rates);
     # algorithmic units: the shape operations plus the model variance's LG2/RCP
@@ -442,7 +457,9 @@ def main():
     # advances every spectrum of the step by one stage)
     traffic = tr["bytes_per_spectrum"] * B if same_kernel else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU)",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": traffic, "count": count,
+                "units_per_launch": units_launch, "sfu_ops_per_launch": sfu_per_launch,
+                "achieved_kernel_count": achieved_kernel, "frac_kernel_count": achieved_kernel / peak,
                 "kernel": "k_mh (fused Metropolis)", "avg_launch_ms": mh_ms / mh_n,
                 "peak_note": ("measured EX2 %.1f / RCP %.1f / LG2 %.1f results per clock per SM at %.0f MHz "
                               "(smc_k_mufu_rate), mix %.0f%% EX2 %.0f%% RCP %.0f%% LG2; a 16/clk/SM SFU x "

@@ -114,7 +114,13 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
  *   h2d_bytes / d2h_bytes  host<->device bytes the calls copied;
  *   max_batch_requests  the most requests (spectra) whose jobs advanced in
  *                the same launches: > 1 shows that batched or served
- *                requests shared kernels on the device. */
+ *                requests shared kernels on the device;
+ *   peak_point_evals  grid-point evaluations of evaluated peak-component
+ *                proposals in the fused peak kernel (Gaussian, Lorentzian,
+ *                pseudo-Voigt peaks with a Chebyshev background), each costing
+ *                peak_sfu_per_eval SFU operations in the method's own count
+ *                (one new peak evaluation per unit: EX2 for a Gaussian, RCP for
+ *                a Lorentzian, both for a pseudo-Voigt; of the last job read). */
 typedef struct {
     int64_t launches[5];
     double ms[5];
@@ -123,6 +129,7 @@ typedef struct {
     int64_t stages, jobs;
     double ex2_ops, rcp_ops, lg2_ops;
     int64_t max_batch_requests;
+    double peak_point_evals, peak_sfu_per_eval;
 } smc_profile;
 
 int smc_profile_reset(smc_ctx *ctx, int32_t enable_events);

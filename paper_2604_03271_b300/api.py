@@ -68,7 +68,8 @@ class Profile(C.Structure):
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double),
                 ("stages", C.c_int64), ("jobs", C.c_int64),
                 ("ex2_ops", C.c_double), ("rcp_ops", C.c_double), ("lg2_ops", C.c_double),
-                ("max_batch_requests", C.c_int64)]
+                ("max_batch_requests", C.c_int64), ("peak_point_evals", C.c_double),
+                ("peak_sfu_per_eval", C.c_double)]
 
 
 KERNEL_CLASSES = ("reweight", "resample", "gather", "metropolis", "stage_end")
@@ -341,7 +342,8 @@ class Context:
                 "gather_bytes": p.gather_bytes, "resample_bytes": p.resample_bytes,
                 "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes,
                 "stages": p.stages, "jobs": p.jobs, "ex2_ops": p.ex2_ops, "rcp_ops": p.rcp_ops,
-                "lg2_ops": p.lg2_ops, "max_batch_requests": p.max_batch_requests}
+                "lg2_ops": p.lg2_ops, "max_batch_requests": p.max_batch_requests,
+                "peak_point_evals": p.peak_point_evals, "peak_sfu_per_eval": p.peak_sfu_per_eval}
 
     def mufu_rate(self, op: int, stream=None) -> dict:
         """Measured SFU throughput of EX2 (op 0), RCP (op 1) or LG2 (op 2) on this

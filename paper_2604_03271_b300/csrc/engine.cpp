@@ -895,6 +895,8 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             const double esz = jd.fp64 ? 8.0 : 4.0;
             c.prof.point_evals += (double)jd.point_evals + (double)jd.T * jd.n;
             c.prof.sfu_ops += (double)jd.sfu_ops;
+            c.prof.peak_point_evals += (double)jd.peak_evals;
+            if (jd.peak_evals) c.prof.peak_sfu_per_eval = jd.family == SMC_PSEUDO_VOIGT ? 2.0 : 1.0;
             c.prof.lg2_ops += 0.5 * (double)jd.var_ops;  // one LG2 and one RCP per point
             c.prof.rcp_ops += 0.5 * (double)jd.var_ops;
             if (jd.family == SMC_GAUSS) c.prof.ex2_ops += (double)jd.sfu_ops;

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
             r[p] = mul2(neg2(w[p]), r[p]);
             w[p] = mul2(splat2(0.5f), w[p]);
         }
-        unsigned n_eval = 0, n_shape = 0;  // evaluated proposals (group-uniform)
+        unsigned n_eval = 0, n_shape = 0, n_peak = 0;  // evaluated proposals (group-uniform)
         for (int sw = 0; sw < n; ++sw) {
             // ---- this sweep's proposals: lane j of the first warp draws component j
             PropTable &tb = prop_sh[g.grp][sw & 1];
@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     if (tj == INFINITY) continue;  // fixed or outside the prior's support
                     const float v = vq[c];
                     ++n_eval;
+                    ++n_peak;
                     // lanes of the packed accumulator: even and odd points
                     f2 acc2 = splat2(0.0f);
                     if (c == 0) {  // amplitude: D = (A' - A) U
@@ -614,6 +615,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                 atomicAdd(&jobs[slot].point_evals, (unsigned long long)n_eval * npts);
                 atomicAdd(&jobs[slot].sfu_ops,
                           (unsigned long long)n_shape * npts * (FAM == FAM_PV ? 2ull : 1ull));
+                atomicAdd(&jobs[slot].peak_evals, (unsigned long long)n_peak * npts);
             }
         }
         __syncwarp();

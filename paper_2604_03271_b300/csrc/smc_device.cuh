@@ -86,6 +86,10 @@ struct JobDev {
     // shape-changing (centre, width) proposals among them
     unsigned long long point_evals, sfu_ops, var_ops;  // var_ops: LG2 + RCP of the model variance
     unsigned long long ex2_part;  // the EX2 share of sfu_ops (App. D phase kernel)
+    // grid-point evaluations of evaluated peak-component proposals (fused
+    // peak kernel only): the units whose per-unit SFU cost is one EX2
+    // (Gaussian), one RCP (Lorentzian) or one of each (pseudo-Voigt)
+    unsigned long long peak_evals;
 };
 
 // ---------------------------------------------------------------------------

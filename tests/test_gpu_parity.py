@@ -551,3 +551,22 @@ def test_mh_fp32_tracks_oracle_every_tuned_tile(row):
     assert np.abs(acc_g - acc_or).sum() <= 0.02 * prop_or.sum() + 3
     E_true = oracle.energies(spec, K, opts, _to_sampling(spec, K, nat_g))
     assert np.all(np.abs(E_g - E_true) <= 2e-5 * (E_true + spec.n))
+
+
+def test_profile_counts_peak_component_units(ctx):
+    # the roofline's unit count: grid-point evaluations of evaluated peak
+    # proposals, a subset of all evaluated proposals' (background proposals
+    # and the prior draws' energies make up the rest); pseudo-Voigt units
+    # cost two SFU operations each in the method's count
+    spec = W.xps_like(2, n=500, k_true=2, k_max=3)
+    ctx.profile_reset()
+    r = ctx.run(spec, W.Options(particles=1024, sweeps=3, seed=4), keep_samples=False)
+    p = ctx.profile()
+    assert r["status"] == 0
+    assert p["peak_sfu_per_eval"] == 2.0
+    n_prior = 1024 * spec.n * 3  # one energy per particle and K at beta = 0
+    assert 0 < p["peak_point_evals"] < p["point_evals"] - n_prior
+    # every evaluated proposal is a whole number of grid passes
+    assert p["peak_point_evals"] % spec.n == 0
+    # peak components are 4 K of the 4 K + 2 components: most of the work
+    assert p["peak_point_evals"] > 0.7 * (p["point_evals"] - n_prior)
