@@ -28,6 +28,17 @@ namespace smc {
 // request's jobs in shared launches, retirement as soon as a request's jobs
 // are all done.
 // ---------------------------------------------------------------------------
+// the serving thread, started by the first submission (caller holds c.qmu)
+static void start_worker(Ctx &c)
+{
+    if (c.worker_started) return;
+    c.worker_started = true;
+    c.worker = std::thread([&c] {
+        cudaSetDevice(c.device);
+        serve_loop(&c);
+    });
+}
+
 static void finish_failed(Ctx &c, Request *r, int st)
 {
     r->status = st;
@@ -238,16 +249,18 @@ int smc_destroy(smc_ctx *ctx)
 {
     if (!ctx) return SMC_EINVAL;
     Ctx &c = ctx->c;
-    if (c.worker_started) {
-        {
-            std::lock_guard<std::mutex> lk(c.qmu);
-            c.stop = true;
-            for (Request *r : c.queue) {
-                r->status = SMC_ECANCELLED;
-                r->state = 2;
-            }
-            c.queue.clear();
+    bool started = false;
+    {
+        std::lock_guard<std::mutex> lk(c.qmu);
+        started = c.worker_started;
+        c.stop = true;
+        for (Request *r : c.queue) {
+            r->status = SMC_ECANCELLED;
+            r->state = 2;
         }
+        c.queue.clear();
+    }
+    if (started) {
         c.qcv.notify_all();
         c.worker.join();
     }
@@ -320,24 +333,14 @@ int smc_submit(smc_ctx *ctx, const smc_request *req, smc_job *out)
     int st = make_request(c, *req, false, r);
     if (st != SMC_OK) return st;
     r->t_submit = std::chrono::steady_clock::now();
-    {
-        std::lock_guard<std::recursive_mutex> g(c.mu);
-        {
-            std::lock_guard<std::mutex> lk(c.qmu);
-            r->id = c.next_id++;
-            c.reqs[r->id] = r;
-        }
-        if (!c.worker_started) {
-            c.worker_started = true;
-            c.worker = std::thread([&c] {
-                cudaSetDevice(c.device);
-                serve_loop(&c);
-            });
-        }
-    }
+    // the queue lock only: the serving thread holds the engine lock (c.mu)
+    // while it runs stages, and a submission must not wait for that
     {
         std::lock_guard<std::mutex> lk(c.qmu);
+        r->id = c.next_id++;
+        c.reqs[r->id] = r;
         c.queue.push_back(r);
+        start_worker(c);
     }
     c.qcv.notify_all();
     *out = r->id;
@@ -360,26 +363,14 @@ int smc_submit_batch(smc_ctx *ctx, const smc_request *reqs, int32_t count, smc_j
     }
     const auto t0 = std::chrono::steady_clock::now();
     {
-        std::lock_guard<std::recursive_mutex> g(c.mu);
-        {
-            std::lock_guard<std::mutex> lk(c.qmu);
-            for (Request *r : rs) {
-                r->t_submit = t0;
-                r->id = c.next_id++;
-                c.reqs[r->id] = r;
-            }
-        }
-        if (!c.worker_started) {
-            c.worker_started = true;
-            c.worker = std::thread([&c] {
-                cudaSetDevice(c.device);
-                serve_loop(&c);
-            });
-        }
-    }
-    {
         std::lock_guard<std::mutex> lk(c.qmu);
-        for (Request *r : rs) c.queue.push_back(r);
+        for (Request *r : rs) {
+            r->t_submit = t0;
+            r->id = c.next_id++;
+            c.reqs[r->id] = r;
+            c.queue.push_back(r);
+        }
+        start_worker(c);
     }
     c.qcv.notify_all();
     for (int i = 0; i < count; ++i) out[i] = rs[i]->id;
@@ -847,6 +838,7 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
     if (!ctx) return SMC_EINVAL;
     std::lock_guard<std::recursive_mutex> g(ctx->c.mu);
     if (J == 0) {
+        std::lock_guard<std::mutex> tl(ctx->c.tmu);
         ctx->c.tiles.clear();
         return SMC_OK;
     }
@@ -855,6 +847,7 @@ int smc_set_tile(smc_ctx *ctx, int32_t family, int64_t n_max, int32_t J, int32_t
     if (family < 0 || family > 4 || (family == SMC_XRD_PHASE && !coupled)) return SMC_EINVAL;
     family = kernel_family(family) | coupled;
     if (n_max < 1 || !mh_tile_supported(family, J, G, regs) || 32L * J * G < 1) return SMC_EINVAL;
+    std::lock_guard<std::mutex> tl(ctx->c.tmu);
     ctx->c.tiles.push_back({family, n_max, J, G, regs});
     return SMC_OK;
 }

@@ -208,6 +208,7 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
     if (!r->fp64) {
         const int kf = kernel_family(r->family) | (full ? MH_COUPLED : 0);
         r->tile = choose_tile(kf, r->n);
+        std::lock_guard<std::mutex> tl(c.tmu);
         for (const auto &t : c.tiles)
             if (t[0] == kf && t[1] >= r->n && 32L * t[2] * t[3] >= r->n &&
                 mh_tile_supported(kf, (int)t[2], (int)t[3], (int)t[4])) {

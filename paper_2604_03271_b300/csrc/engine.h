@@ -88,8 +88,10 @@ struct Ctx {
     int *d_nactive = nullptr;
     int *h_nactive = nullptr;      // pinned, device-mapped, one entry per stage of a chunk
     int *h_nactive_dev = nullptr;  // its device alias
-    // autotuned tiles: (family, n_max, J, G, R)
+    // autotuned tiles: (family, n_max, J, G, R), under tmu (read when a
+    // request is made, which submissions do without the engine lock)
     std::vector<std::array<int64_t, 5>> tiles;
+    std::mutex tmu;
     // profiling (per-kernel events need the chunked graph: conditional bodies
     // take no event nodes)
     bool prof_events = false;

@@ -77,6 +77,32 @@ __device__ __forceinline__ void group_sync(const GroupCtx<G> &g)
         named_barrier(1 + g.grp, 32 * G);
 }
 
+// The cross-warp part of group_sum, for a value already summed over the warp.
+template <int G>
+__device__ __forceinline__ float group_cross(GroupCtx<G> &g, float v)
+{
+    if (G == 1) return v;
+    float *slot = g.red + g.par * MH_MAX_GROUPS;
+    if (g.lane == 0) slot[g.gw] = v;
+    named_barrier(1 + g.grp, 32 * G);
+    float s = 0.0f;
+    if constexpr (G % 4 == 0) {
+#pragma unroll
+        for (int w = 0; w < G; w += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(slot + w);
+            s += q.x;
+            s += q.y;
+            s += q.z;
+            s += q.w;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < G; ++w) s += slot[w];
+    }
+    g.par ^= 1;
+    return s;
+}
+
 template <int G>
 __device__ __forceinline__ float group_sum(GroupCtx<G> &g, float v)
 {
@@ -450,6 +476,7 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     tq[c] = q2.x;
                     vq[c] = q2.y;
                 }
+                bool mu_ready = false;  // the centre proposal's profile already in N0 / N1
 #pragma unroll
                 for (int c = 0; c < P; ++c) {
                     const int j = j0 + c;
@@ -474,6 +501,14 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                             const f2 D = mul2(dd, S0[p]);
                             acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
+                    } else if (c == 1 && mu_ready) {  // centre, profile computed already
+                        ++n_shape;
+                        const f2 Av = splat2(A);
+#pragma unroll
+                        for (int p = 0; p < JP; ++p) {
+                            const f2 D = mul2(Av, FAM == FAM_PV ? sub2(N1[p], S1[p]) : sub2(N0[p], S0[p]));
+                            acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
+                        }
                     } else {  // centre or width: new shape, D = A (U' - U)
                         ++n_shape;
                         const float mu2 = (c == 1) ? v : mu;
@@ -489,7 +524,30 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                             acc2 = fma2(D, fma2(w[p], D, r[p]), acc2);
                         }
                     }
-                    const float dE = group_sum(g, lo2(acc2) + hi2(acc2));
+                    float dE;
+                    if (c == 0 && tq[1] != INFINITY) {
+                        // The centre proposal's new unit-amplitude profile does
+                        // not depend on the amplitude's outcome: it is computed
+                        // between the shuffles of the amplitude's reduction, so
+                        // that its SFU and FMA work fills the reduction's latency.
+                        float s0 = lo2(acc2) + hi2(acc2);
+                        s0 += __shfl_xor_sync(FULL_MASK, s0, 16);
+                        const f2 scv = splat2(sc), nmsc = splat2(-vq[1] * sc), et = splat2(eta);
+#pragma unroll
+                        for (int p = 0; p < JP; ++p) {
+                            f2 l = splat2(0.0f);
+                            shape2<FAM>(X(p), scv, nmsc, N0[p], l);
+                            if (FAM == FAM_PV) N1[p] = fma2(et, N0[p], l);
+                        }
+                        s0 += __shfl_xor_sync(FULL_MASK, s0, 8);
+                        s0 += __shfl_xor_sync(FULL_MASK, s0, 4);
+                        s0 += __shfl_xor_sync(FULL_MASK, s0, 2);
+                        s0 += __shfl_xor_sync(FULL_MASK, s0, 1);
+                        dE = group_cross(g, s0);
+                        mu_ready = true;
+                    } else {
+                        dE = group_sum(g, lo2(acc2) + hi2(acc2));
+                    }
                     if (tj < -beta * dE) {
                         if (c == 0) {
                             const float dA = v - A;

@@ -123,3 +123,36 @@ def test_oversized_request_fails_cleanly():
         r = ctx.result(j, s)
         assert r["status"] == api.SMC_ENOMEM and r["log_z"] is None
         ctx.release(j)
+
+
+def test_request_arriving_mid_run_joins_the_running_launches():
+    # continuous batching under arrivals: a small request submitted while a
+    # large one is on the GPU is admitted at the next stage boundary, shares
+    # its launches, and finishes first; submitting does not wait for the
+    # serving thread's launches
+    import time
+
+    from paper_2604_03271_b300 import api
+    big = (W.xrd_like(2, n=2048, k_true=6, k_max=8), W.Options(particles=16384, sweeps=20, seed=5))
+    small = (W.gaussian_small(3), W.Options(particles=1024, sweeps=4, seed=6))
+    with api.Context(0) as ctx:
+        ref_small = ctx.run(*small, keep_samples=False)
+        ctx.profile_reset()
+        ja = ctx.submit(*big)
+        time.sleep(0.3)
+        assert not ctx.poll(ja)  # the large request is still running
+        t0 = time.perf_counter()
+        jb = ctx.submit(*small)
+        submit_ms = 1000.0 * (time.perf_counter() - t0)
+        ctx.wait(jb, 120.0)
+        b_done_first = not ctx.poll(ja)
+        ctx.wait(ja, 600.0)
+        rb = ctx.result(jb, small[0])
+        ra = ctx.result(ja, big[0])
+        for j in (ja, jb):
+            ctx.release(j)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert submit_ms < 100.0, submit_ms
+        assert b_done_first
+        assert ctx.profile()["max_batch_requests"] >= 2
+    np.testing.assert_array_equal(ref_small["log_z"], rb["log_z"])
