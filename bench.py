@@ -263,9 +263,9 @@ def reference_arm(args, world: int, rank: int):
 
 # particle-point evaluations per spectrum (prior energies + every evaluated
 # proposal x N), from the GPU arm's own counters on the same seeds
-UNITS_PER_SPECTRUM = {"xps": 7.7e11, "xps_wf": 7.7e11, "xrd": 5.7e13, "gauss": 8.0e8, "mixed": 1.0e12, "xrd_phase": 1.0e12,
-                      "xrd_phase_5000": 2.2e12, "xrd_phase_10000": 1.7e12,
-                      "deconv3": 3.6e10, "deconv10": 8.2e11, "deconv30": 4.8e13}
+UNITS_PER_SPECTRUM = {"xps": 7.70e11, "xps_wf": 7.73e11, "xrd": 5.73e13, "gauss": 8.0e8, "mixed": 8.64e11,
+                      "xps_shirley": 1.10e12, "xrd_phase": 9.63e11, "xrd_phase_5000": 2.2e12,
+                      "xrd_phase_10000": 1.7e12, "deconv3": 3.6e10, "deconv10": 8.24e11, "deconv30": 4.8e13}
 
 
 # ---------------------------------------------------------------------------
@@ -294,6 +294,8 @@ def main():
                     help="steps of the untimed per-kernel event pass (kernel shares, roofline)")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end pass (default 3, 1 for xrd)")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="particles per K instead of the workload's (smaller cases for profilers)")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the serving sweep (Poisson mix of XPS- and XRD-shaped requests)")
     ap.add_argument("--serve-rates", default="0.5,1.0,3.0")
@@ -345,7 +347,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def batch_for(step: int):
-        return [workload(args.workload, seed) for seed in shard_seeds(step, world, rank, B)]
+        items = [workload(args.workload, seed) for seed in shard_seeds(step, world, rank, B)]
+        if args.particles:
+            import dataclasses
+            items = [(s, dataclasses.replace(o, particles=args.particles)) for s, o in items]
+        return items
 
     def to_dev(items):
         out = []
@@ -485,7 +491,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 energies, Metropolis and ESS-search weights (Kahan); f64 evidence, beta and moment totals",
-            "data": "synthetic", "config": config_of(args.workload, B), "impl": "ours",
+            "data": "synthetic", "config": dict(config_of(args.workload, B),
+                                                **({"particles_per_k": args.particles} if args.particles else {})),
+            "impl": "ours",
             "e2e": e2e,
             # kernels of the timed runs: every stage's kernels (counted in the
             # event pass) times the stages run, plus six set-up and result
