@@ -47,7 +47,8 @@ SM_COUNT = 148
 # of one spectrum per step, per workload; valid only for the kernel source
 # (k_mh_impl.cuh, by sha1) they were taken on; scaled by the spectra a launch
 # processes (the particle state of each spectrum's jobs is its own)
-MH_TRAFFIC = {"xps": {"sha1": "0dc5128c1393", "bytes_per_spectrum": 6.380e6 + 0.481e6}}
+MH_TRAFFIC = {"xps": {"sha1": "a220e210ad2e", "bytes_per_spectrum": 6.411e6 + 0.547e6},
+              "xrd": {"sha1": "a220e210ad2e", "bytes_per_spectrum": 105.58e6 + 58.82e6}}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
