@@ -61,6 +61,33 @@ __device__ __forceinline__ float unit_of(float S0, float S1, float eta)
     return FAM == FAM_PV ? fmaf(eta, S0, S1) : S0;
 }
 
+// Sum of the G warp totals of a group in a fixed tree order (pairs within
+// each float4, then across the float4s): identical in every lane, depth log2 G.
+template <int G>
+__device__ __forceinline__ float warp_totals_sum(const float *slot)
+{
+    if constexpr (G % 4 == 0) {
+        float t[G / 4];
+#pragma unroll
+        for (int i = 0; i < G / 4; ++i) {
+            const float4 q = *reinterpret_cast<const float4 *>(slot + 4 * i);
+            t[i] = (q.x + q.y) + (q.z + q.w);
+        }
+#pragma unroll
+        for (int w = 1; w < G / 4; w *= 2)
+#pragma unroll
+            for (int i = 0; i + w < G / 4; i += 2 * w) t[i] += t[i + w];
+        return t[0];
+    } else if constexpr (G == 2) {
+        return slot[0] + slot[1];
+    } else {
+        float s = slot[0];
+#pragma unroll
+        for (int w = 1; w < G; ++w) s += slot[w];
+        return s;
+    }
+}
+
 template <int G>
 struct GroupCtx {
     int lane, gw, grp;
@@ -85,20 +112,7 @@ __device__ __forceinline__ float group_cross(GroupCtx<G> &g, float v)
     float *slot = g.red + g.par * MH_MAX_GROUPS;
     if (g.lane == 0) slot[g.gw] = v;
     named_barrier(1 + g.grp, 32 * G);
-    float s = 0.0f;
-    if constexpr (G % 4 == 0) {
-#pragma unroll
-        for (int w = 0; w < G; w += 4) {
-            const float4 q = *reinterpret_cast<const float4 *>(slot + w);
-            s += q.x;
-            s += q.y;
-            s += q.z;
-            s += q.w;
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < G; ++w) s += slot[w];
-    }
+    const float s = warp_totals_sum<G>(slot);
     g.par ^= 1;
     return s;
 }
@@ -111,20 +125,7 @@ __device__ __forceinline__ float group_sum(GroupCtx<G> &g, float v)
     float *slot = g.red + g.par * MH_MAX_GROUPS;
     if (g.lane == 0) slot[g.gw] = v;
     named_barrier(1 + g.grp, 32 * G);
-    float s = 0.0f;
-    if constexpr (G % 4 == 0) {
-#pragma unroll
-        for (int w = 0; w < G; w += 4) {
-            const float4 q = *reinterpret_cast<const float4 *>(slot + w);
-            s += q.x;
-            s += q.y;
-            s += q.z;
-            s += q.w;
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < G; ++w) s += slot[w];
-    }
+    const float s = warp_totals_sum<G>(slot);
     g.par ^= 1;
     return s;
 }
@@ -585,11 +586,10 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                                 sc = sc2_of<FAM>(v, wprec);
                             }
                         }
-                        if (lane == 0) {
-                            cs.th[j] = tb.un[j];
-                            cs.nat[j] = v;
-                            cs.acc[j] += 1u;
-                        }
+                        // every lane writes the same values (no divergent branch)
+                        cs.th[j] = tb.un[j];
+                        cs.nat[j] = v;
+                        cs.acc[j] += 1u;
                         __syncwarp();
                     }
                 }
@@ -638,11 +638,9 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     const f2 d2 = splat2(dc + dc);
 #pragma unroll
                     for (int p = 0; p < JP; ++p) r[p] = fma2(w[p], mul2(d2, N0[p]), r[p]);
-                    if (lane == 0) {
-                        cs.th[j] = tb.un[j];
-                        cs.nat[j] = v;
-                        cs.acc[j] += 1u;
-                    }
+                    cs.th[j] = tb.un[j];
+                    cs.nat[j] = v;
+                    cs.acc[j] += 1u;
                     __syncwarp();
                 }
             }
