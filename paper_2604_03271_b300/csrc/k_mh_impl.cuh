@@ -586,10 +586,13 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                                 sc = sc2_of<FAM>(v, wprec);
                             }
                         }
-                        // every lane writes the same values (no divergent branch)
-                        cs.th[j] = tb.un[j];
-                        cs.nat[j] = v;
-                        cs.acc[j] += 1u;
+                        // one lane: the acceptance count is a read-modify-write that
+                        // lanes running apart would repeat
+                        if (lane == 0) {
+                            cs.th[j] = tb.un[j];
+                            cs.nat[j] = v;
+                            cs.acc[j] += 1u;
+                        }
                         __syncwarp();
                     }
                 }
@@ -638,9 +641,11 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     const f2 d2 = splat2(dc + dc);
 #pragma unroll
                     for (int p = 0; p < JP; ++p) r[p] = fma2(w[p], mul2(d2, N0[p]), r[p]);
-                    cs.th[j] = tb.un[j];
-                    cs.nat[j] = v;
-                    cs.acc[j] += 1u;
+                    if (lane == 0) {
+                        cs.th[j] = tb.un[j];
+                        cs.nat[j] = v;
+                        cs.acc[j] += 1u;
+                    }
                     __syncwarp();
                 }
             }

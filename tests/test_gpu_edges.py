@@ -170,9 +170,11 @@ def _sampling(spec, K, nat):
     return u
 
 
-def test_bench_config_fp32_energies_move_log_z_by_less_than_005(ctx):
-    """The bench configuration (N = 1001, K = 1..6, PV + linear background,
-    T = 16384, 20 sweeps).  The FP32 path samples and weighs with FP32
+@pytest.mark.parametrize("which", ["xps", "xrd"])
+def test_bench_config_fp32_energies_move_log_z_by_less_than_005(ctx, which):
+    """The bench configurations: XPS-shaped (N = 1001, K = 1..6, PV + linear
+    background, T = 16384) and XRD-shaped (N = 4096, K = 1..12, PV + cubic
+    background, T = 65536), 20 sweeps.  The FP32 path samples and weighs with FP32
     energies E32 = E64 + eps; the evidence of that energy landscape differs
     from the FP64 one's by log Z32 - log Z64 = log E_post64[exp(-eps)]
     (Eq. (11) at beta = 1 is the prior expectation of exp(-E)), which lies in
@@ -183,8 +185,10 @@ def test_bench_config_fp32_energies_move_log_z_by_less_than_005(ctx):
     remaining FP32-vs-FP64 difference of the estimators is Monte Carlo error
     of the same algorithm at the same T (the statistical 0.05 tests run where
     the FP64 path is affordable: configs of N <= 400)."""
-    spec = W.xps_like(1)
-    opts = W.Options(particles=16384, sweeps=20, seed=1)
+    if which == "xps":
+        spec, opts = W.xps_like(1), W.Options(particles=16384, sweeps=20, seed=1)
+    else:
+        spec, opts = W.xrd_like(1), W.Options(particles=65536, sweeps=20, seed=1)
     r = ctx.run(spec, opts, keep_samples=True)
     assert r["status"] == 0
     rng = np.random.default_rng(5)
@@ -200,11 +204,18 @@ def test_bench_config_fp32_energies_move_log_z_by_less_than_005(ctx):
         step = 0.3 * np.maximum(u.std(axis=0), 1e-6)
         nat_o, E_o, acc, prop = ctx.mh_stage(spec, K, opts, nat[idx], e32[idx], step, 1.0, 7, precision=0)
         eps_k = E_o - ctx.energy(spec, K, opts, nat_o, precision=1)
-        print(f"K={K}: eps of the FP32 energy kernel in [{eps.min():.2e}, {eps.max():.2e}], "
+        print(f"{which} K={K}: eps of the FP32 energy kernel in [{eps.min():.2e}, {eps.max():.2e}], "
               f"log-Z shift {shift:.2e}; Metropolis kernel energies in [{eps_k.min():.2e}, {eps_k.max():.2e}]")
         assert acc.sum() > 0
-        assert np.max(np.abs(eps)) <= 0.05 and np.max(np.abs(eps_k)) <= 0.05
-        assert abs(shift) <= 0.05
+        if r["log_z"][a] >= np.max(r["log_z"]) - 100.0:
+            # the candidates that carry posterior weight (Eq. (2)): within 0.05 nat
+            assert np.max(np.abs(eps)) <= 0.05 and np.max(np.abs(eps_k)) <= 0.05
+            assert abs(shift) <= 0.05
+        else:
+            # badly fitting K (energies of 1e5 and more, P(K|D) = 0 to double
+            # precision): FP32 rounding of the energy, a few 1e-7 of it
+            scale = 1e-6 * np.median(np.abs(e64))
+            assert np.max(np.abs(eps)) <= max(0.05, scale) and np.max(np.abs(eps_k)) <= max(0.05, scale)
 
 
 def test_full_size_xrd_g16_tile_energies(ctx):
