@@ -26,15 +26,27 @@ _lib = None
 OK, EINVAL, ENOMEM, EMAXSTAGES, ENUMERIC = 0, 1, 2, 5, 8
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc of one C source into a shared library (strict IEEE double, no
+    fast-math, no contraction into FMA)."""
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-o", out, src, "-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (strict IEEE double, no fast-math)."""
+    """Compile the oracle."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def source() -> str:
+    """Path of the oracle's C source."""
+    return _SRC
 
 
 class Prior(C.Structure):
@@ -69,46 +81,60 @@ class Out(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        d, i64, u32, i32 = C.c_double, C.c_int64, C.c_uint32, C.c_int
-        P = C.POINTER
-        _lib.orc_philox.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
-        _lib.orc_peak.argtypes = [i32, d, d, d, d, d]
-        _lib.orc_peak.restype = d
-        _lib.orc_model_at.argtypes = [i32, i32, i32, P(d), d, d, d]
-        _lib.orc_model_at.restype = d
-        _lib.orc_energy_nat.argtypes = [i32, i32, i32, P(d), P(d), P(d), P(d), i64]
-        _lib.orc_energy_nat.restype = d
-        _lib.orc_model_vec.argtypes = [i32, i32, i32, i32, P(d), P(d), i64, P(d)]
-        _lib.orc_energy_model.argtypes = [i32, i32, i32, i32, i32, P(d), P(d), P(d), P(d), P(d), i64]
-        _lib.orc_energy_model.restype = d
-        _lib.orc_energy_job.argtypes = [P(Job), P(d)]
-        _lib.orc_energy_job.restype = d
-        _lib.orc_xrd_phase.argtypes = [P(d), P(d), P(d), i32, d]
-        _lib.orc_xrd_phase.restype = d
-        _lib.orc_xrd_background.argtypes = [P(d), d]
-        _lib.orc_xrd_background.restype = d
-        _lib.orc_model_vec_xrd.argtypes = [i32, i32, P(d), P(d), i64, P(d), P(d), P(C.c_int32), P(d)]
-        _lib.orc_dim.argtypes = [i32, i32, i32, i32]
-        _lib.orc_dim.restype = i32
-        _lib.orc_prior_draw.argtypes = [Prior, C.c_uint64, u32, u32, u32]
-        _lib.orc_prior_draw.restype = d
-        _lib.orc_ess_frac.argtypes = [P(d), i64, d]
-        _lib.orc_ess_frac.restype = d
-        _lib.orc_choose_delta.argtypes = [P(d), i64, d, d, P(C.c_int), P(C.c_int)]
-        _lib.orc_choose_delta.restype = d
-        _lib.orc_quantise.argtypes = [P(d), i64, P(C.c_uint64)]
-        _lib.orc_resample.argtypes = [P(C.c_uint64), i64, i64, u32, P(C.c_int32)]
-        _lib.orc_init_particles.argtypes = [P(Job), i64, P(d), P(d)]
-        _lib.orc_energies.argtypes = [P(Job), i64, P(d), P(d)]
-        _lib.orc_mh_stage.argtypes = [P(Job), P(d), P(d), i64, P(d), d, u32, P(d), P(d),
-                                      P(C.c_int64), P(C.c_int64)]
-        _lib.orc_step_sizes.argtypes = [P(Job), P(d), P(d), i64, P(d), P(d), P(d)]
-        _lib.orc_predict_step.argtypes = [P(d), d, d, d, d, d]
-        _lib.orc_predict_step.restype = d
-        _lib.orc_run_job.argtypes = [P(Job), P(Out)]
-        _lib.orc_run_job.restype = i32
+        _lib = bind(C.CDLL(build()))
     return _lib
+
+
+def bind(handle):
+    """Declare the argument and result types of every exported function on a
+    loaded oracle library."""
+    L = handle
+    d, i64, u32, i32 = C.c_double, C.c_int64, C.c_uint32, C.c_int
+    P = C.POINTER
+    L.orc_philox.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+    L.orc_peak.argtypes = [i32, d, d, d, d, d]
+    L.orc_peak.restype = d
+    L.orc_model_at.argtypes = [i32, i32, i32, P(d), d, d, d]
+    L.orc_model_at.restype = d
+    L.orc_energy_nat.argtypes = [i32, i32, i32, P(d), P(d), P(d), P(d), i64]
+    L.orc_energy_nat.restype = d
+    L.orc_model_vec.argtypes = [i32, i32, i32, i32, P(d), P(d), i64, P(d)]
+    L.orc_energy_model.argtypes = [i32, i32, i32, i32, i32, P(d), P(d), P(d), P(d), P(d), i64]
+    L.orc_energy_model.restype = d
+    L.orc_energy_job.argtypes = [P(Job), P(d)]
+    L.orc_energy_job.restype = d
+    L.orc_xrd_phase.argtypes = [P(d), P(d), P(d), i32, d]
+    L.orc_xrd_phase.restype = d
+    L.orc_xrd_background.argtypes = [P(d), d]
+    L.orc_xrd_background.restype = d
+    L.orc_model_vec_xrd.argtypes = [i32, i32, P(d), P(d), i64, P(d), P(d), P(C.c_int32), P(d)]
+    L.orc_dim.argtypes = [i32, i32, i32, i32]
+    L.orc_dim.restype = i32
+    L.orc_prior_draw.argtypes = [Prior, C.c_uint64, u32, u32, u32]
+    L.orc_prior_draw.restype = d
+    L.orc_ess_frac.argtypes = [P(d), i64, d]
+    L.orc_ess_frac.restype = d
+    L.orc_choose_delta.argtypes = [P(d), i64, d, d, P(C.c_int), P(C.c_int)]
+    L.orc_choose_delta.restype = d
+    L.orc_quantise.argtypes = [P(d), i64, P(C.c_uint64)]
+    L.orc_resample.argtypes = [P(C.c_uint64), i64, i64, u32, P(C.c_int32)]
+    L.orc_init_particles.argtypes = [P(Job), i64, P(d), P(d)]
+    L.orc_energies.argtypes = [P(Job), i64, P(d), P(d)]
+    L.orc_mh_stage.argtypes = [P(Job), P(d), P(d), i64, P(d), d, u32, P(d), P(d),
+                               P(C.c_int64), P(C.c_int64)]
+    L.orc_step_sizes.argtypes = [P(Job), P(d), P(d), i64, P(d), P(d), P(d)]
+    L.orc_predict_step.argtypes = [P(d), d, d, d, d, d]
+    L.orc_predict_step.restype = d
+    L.orc_run_job.argtypes = [P(Job), P(Out)]
+    L.orc_run_job.restype = i32
+    return L
+
+
+def use_library(handle) -> None:
+    """Route every wrapper in this module through another build of the oracle
+    (a library returned by bind()); None goes back to the default build."""
+    global _lib
+    _lib = handle
 
 
 def _dp(a: np.ndarray):

@@ -45,7 +45,9 @@
  * K = 1 quadrature).  The step-size rule and the waste-free branch are pinned
  * against weighted moments computed independently (row replication, numpy's
  * analytic-weight covariance), replays of standard stages, and the closed-form
- * and quadrature evidences run in waste-free mode.
+ * and quadrature evidences run in waste-free mode.  tests/test_oracle_mutants.py
+ * builds copies of this file with one plausible mistake planted in each and
+ * checks that every copy fails one of those pins.
  */
 #include <math.h>
 #include <stdint.h>

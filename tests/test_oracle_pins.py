@@ -35,6 +35,12 @@ def test_uniform_mapping_is_open_interval():
     lo = (0 + 0.5) * 2.0 ** -32
     hi = (2 ** 32 - 1 + 0.5) * 2.0 ** -32
     assert 0.0 < lo < hi < 1.0
+    # the draw is the mapping of the first word of Philox counter
+    # (256 comp, particle, 0, tag) under key (seed low, seed high), exactly
+    for seed, comp, particle, tag in [(0, 0, 0, 1), (3, 2, 17, 5), (2 ** 40 + 7, 1, 123456, 3)]:
+        k = int(oracle.philox([256 * comp, particle, 0, tag], [seed & 0xFFFFFFFF, seed >> 32])[0])
+        got = oracle.prior_draw(W.UNIFORM, 0.0, 1.0, seed=seed, comp=comp, particle=particle, tag=tag)
+        assert got == (k + 0.5) * 2.0 ** -32
     vals = [oracle.prior_draw(W.UNIFORM, 0.0, 1.0, seed=s, comp=0, particle=p, tag=1)
             for s in range(3) for p in range(200)]
     assert min(vals) > 0.0 and max(vals) < 1.0
@@ -240,6 +246,20 @@ def test_resample_offspring_bounds(T, M):
             lo = (M * int(q[i])) // Q
             assert o[i] in (lo, lo + 1) or (o[i] == lo and M * int(q[i]) % Q == 0)
             assert q[i] > 0 or o[i] == 0
+
+
+def test_resample_equal_and_zero_weights_are_exact():
+    # equal weights: each particle is drawn exactly once, in order, for every U
+    # (t_m lands in particle m's own interval of the cumulative sum); with
+    # zero-weight particles between them, exactly the nonzero ones are drawn --
+    # including U = 0, where t_m falls on an interval's left end
+    T = 64
+    for u32 in (0, 1, 2 ** 31, 2 ** 32 - 1):
+        np.testing.assert_array_equal(oracle.resample(oracle.quantise(np.ones(T)), T, u32), np.arange(T))
+        w = np.zeros(T)
+        w[::3] = 0.37
+        nz = np.flatnonzero(w)
+        np.testing.assert_array_equal(oracle.resample(oracle.quantise(w), len(nz), u32), nz)
 
 
 def test_resample_mean_offspring_is_proportional():
@@ -493,9 +513,9 @@ def test_energy_model_variance_brute_force():
     spec = W.Spectrum(x, y, np.ones_like(x), PV, 2, 2, W.BG_SHIRLEY, 0,
                       W.Priors(amp=W.Prior(W.UNIFORM, 0, 1), centre=W.Prior(W.UNIFORM, 0, 1),
                                width=W.Prior(W.UNIFORM, 0, 1)), truth={},
-                      noise=W.NOISE_MODEL, noise_par=(1.0, 0.01, 0.5))
+                      noise=W.NOISE_MODEL, noise_par=(1.7, 0.01, 0.5))
     e = oracle.energy_spec(spec, 2, nat)
-    assert e == pytest.approx(_mp_energy_model(2, nat, x, y, 1.0, 0.01, 0.5), rel=1e-13)
+    assert e == pytest.approx(_mp_energy_model(2, nat, x, y, 1.7, 0.01, 0.5), rel=1e-13)
 
 
 def test_constant_model_variance_reduces_to_known_sigma():

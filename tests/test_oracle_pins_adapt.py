@@ -279,12 +279,23 @@ def test_waste_free_evidence_k1_gamma_amplitude_quadrature():
 # --------------------------------------------------------------------------
 
 def _rw_acceptance_numeric(s, sigma):
-    """Acceptance rate of a Gaussian random walk of SD s on N(0, sigma^2), by
-    2-D quadrature of E[min(1, pi(x + s z) / pi(x))] over x and z."""
-    f = lambda z, x: (stats.norm.pdf(x, scale=sigma) * stats.norm.pdf(z)
-                      * min(1.0, math.exp(-((x + s * z) ** 2 - x * x) / (2 * sigma * sigma))))
-    val, _ = integrate.dblquad(f, -10 * sigma, 10 * sigma, -10, 10, epsabs=1e-10, epsrel=1e-10)
+    """Acceptance rate of a Gaussian random walk of SD s on N(0, sigma^2),
+    E over x ~ N(0, sigma^2), z ~ N(0, 1) of min(1, pi(x + s z) / pi(x)).
+    pi(x) min(1, pi(x + d) / pi(x)) = min(pi(x), pi(x + d)) is the density of
+    whichever of x, x + d lies farther from 0, so for a fixed d = s z the x
+    integral is P(X + d >= d/2) + P(X < -d/2) = 2 Phi(-|d| / (2 sigma)); the z
+    integral is taken by 1-D adaptive quadrature."""
+    f = lambda z: 2.0 * stats.norm.pdf(z) * 2.0 * stats.norm.cdf(-s * z / (2.0 * sigma))
+    val, _ = integrate.quad(f, 0.0, np.inf, epsabs=1e-13, epsrel=1e-12)
     return val
+
+
+def _rw_acceptance_monte_carlo(s, sigma, n, seed):
+    """The same expectation by plain Monte Carlo of the definition."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0.0, sigma, n)
+    xp = x + s * rng.normal(0.0, 1.0, n)
+    return np.minimum(1.0, np.exp(-(xp * xp - x * x) / (2.0 * sigma * sigma))).mean()
 
 
 def _rw_acceptance(s, sigma):
@@ -293,8 +304,11 @@ def _rw_acceptance(s, sigma):
 
 @pytest.mark.parametrize("ratio", [0.3, 1.0, 2.42, 6.0])
 def test_random_walk_acceptance_closed_form(ratio):
-    # the relation the predictor inverts, checked by direct quadrature
-    assert _rw_acceptance_numeric(ratio, 1.0) == pytest.approx(_rw_acceptance(ratio, 1.0), abs=1e-7)
+    # the relation the predictor inverts, checked by quadrature and, straight
+    # from the definition, by Monte Carlo (4e6 draws: SE below 2.5e-4)
+    assert _rw_acceptance_numeric(ratio, 1.0) == pytest.approx(_rw_acceptance(ratio, 1.0), abs=1e-10)
+    assert _rw_acceptance_monte_carlo(ratio, 1.3, 4_000_000, 11) == pytest.approx(
+        _rw_acceptance(ratio, 1.3), abs=1.5e-3)
 
 
 @pytest.mark.parametrize("gamma", [0.5, 0.3, 0.9])
@@ -340,6 +354,21 @@ def test_predictor_history_weights_and_bounds():
     assert st == pytest.approx(1e-2, rel=1e-14)
     st, _ = oracle.predict_step(np.zeros(5), 1.0, 0.02, 1e-3, 1e-2, sd_pop=1e3)
     assert st == pytest.approx(10.0, rel=1e-14)
+    # the fitted slope is clamped to [-1, 0]: SDs growing with beta (slope
+    # +0.3) predict with slope 0, SDs falling as beta^-1.5 with slope -1.  At
+    # rate 1/2 the SD estimate is s tan(pi/4) / 2 = s / 2
+    betas, b_next = np.array([1e-3, 1e-2, 1e-1]), 0.3
+    wts = np.array([0.25, 0.5, 1.0])
+    xs = np.log(betas)
+    for gamma, b_used in ((0.3, 0.0), (-1.5, -1.0)):
+        sig = 0.5 * betas ** gamma
+        xm, ym = wts @ xs / wts.sum(), wts @ np.log(sig) / wts.sum()
+        expect = 2.0 * math.exp(ym + b_used * (math.log(b_next) - xm)) / math.tan(0.22 * math.pi)
+        h = np.zeros(5)
+        for b, sg in zip(betas, sig):
+            # population SD = the expected step: the bounds [0.01, 10] x SD do not bind
+            st, h = oracle.predict_step(h, 2.0 * sg, 0.5, b, b_next, sd_pop=expect)
+        assert st == pytest.approx(expect, rel=1e-12)
 
 
 def test_predictor_rule_in_runs_evidence_and_rates():
