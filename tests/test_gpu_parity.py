@@ -570,3 +570,28 @@ def test_profile_counts_peak_component_units(ctx):
     assert p["peak_point_evals"] % spec.n == 0
     # peak components are 4 K of the 4 K + 2 components: most of the work
     assert p["peak_point_evals"] > 0.7 * (p["point_evals"] - n_prior)
+
+
+def test_autotune_short_run_writes_a_loadable_table(tmp_path):
+    # the tuner on one family and one bucket: it times every admissible tile
+    # (register budgets included where the kernel has them), keeps the fastest,
+    # and the table it writes loads back into a context whose runs use it
+    import json
+    from paper_2604_03271_b300 import api, autotune
+    with api.Context(0) as c:
+        rows = autotune.tune(c, families=(W.PSEUDO_VOIGT,), buckets=(1024,), particles=1024,
+                             sweeps=1, stages=2, verbose=False)
+        assert len(rows) == 1
+        row = rows[0]
+        tried = [(t["J"], t["G"], t["R"]) for t in row["tried"]]
+        expect = [(J, G, R) for J, G in autotune.candidates(W.PSEUDO_VOIGT, 1024)
+                  for R in autotune.variants(W.PSEUDO_VOIGT, J, G)]
+        assert tried == expect
+        assert all(t["mh_ms"] > 0 for t in row["tried"])
+        assert row["mh_ms"] == min(t["mh_ms"] for t in row["tried"])
+        path = tmp_path / "tiles.json"
+        path.write_text(json.dumps({"device": "B300", "tiles": rows}))
+        assert autotune.load(c, str(path)) == 1
+        spec = W.xps_like(5, n=1001, k_true=2, k_max=3)
+        r = c.run(spec, W.Options(particles=2048, sweeps=2, seed=3), keep_samples=False)
+        assert r["status"] == 0 and np.all(np.isfinite(r["log_z"]))
