@@ -29,6 +29,43 @@ def test_philox_known_answers():
         assert list(got) == v[6:10]
 
 
+def _curand_host():
+    import ctypes
+    import glob
+    paths = sorted(glob.glob("/usr/local/cuda/lib64/libcurand.so*")) + ["libcurand.so.10", "libcurand.so"]
+    for p in paths:
+        try:
+            return ctypes.CDLL(p)
+        except OSError:
+            continue
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    # the same generator through cuRAND's host (CPU) Philox4x32-10 generator:
+    # with the default ordering, a request of 4 B words returns as words
+    # 4b .. 4b+3 the block of counter (0, 0, b, 0) -- subsequence b, offset 0
+    # of its device API's curand_init -- under key (seed low, seed high)
+    import ctypes
+    L = _curand_host()
+    if L is None:
+        pytest.skip("cuRAND not available")
+    B = 4096
+    for seed in (0, 12345, 0x123456789ABCDEF0):
+        gen = ctypes.c_void_p()
+        assert L.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+        try:
+            assert L.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+            buf = (ctypes.c_uint * (4 * B))()
+            assert L.curandGenerate(gen, buf, ctypes.c_size_t(4 * B)) == 0
+        finally:
+            L.curandDestroyGenerator(gen)
+        lib = np.frombuffer(buf, dtype=np.uint32).reshape(B, 4)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        ours = np.array([oracle.philox([0, 0, b, 0], key) for b in range(B)], dtype=np.uint32)
+        np.testing.assert_array_equal(ours, lib)
+
+
 def test_uniform_mapping_is_open_interval():
     # u = (k + 1/2) 2^-32 never reaches 0 or 1; checked at the two extreme words
     # through the Uniform(0, 1) prior draw, whose value is exactly the mapping.
