@@ -442,6 +442,59 @@ def test_evidence_k1_quadrature_free_centre():
     assert abs(np.mean(vals) - exact) < max(0.05, 4 * se)
 
 
+def _gauss_legendre(lo, hi, panels, order=20):
+    z, wq = np.polynomial.legendre.leggauss(order)
+    edges = np.linspace(lo, hi, panels + 1)
+    a, b = edges[:-1, None], edges[1:, None]
+    return (0.5 * (b - a) * z + 0.5 * (a + b)).ravel(), (0.5 * (b - a) * wq).ravel()
+
+
+def _gamma21_amplitude_integral(a, bp):
+    """int_0^inf A exp(-A) exp(-a A^2 / 2 + b A) dA with bp = b - 1: from
+    I0 = int_0^inf exp(-a A^2/2 + bp A) dA = sqrt(pi / 2a) erfcx(-bp / sqrt(2a))
+    and, integrating d/dA exp(...) over [0, inf), -a I1 + bp I0 = -1."""
+    I0 = np.sqrt(np.pi / (2 * a)) * special.erfcx(-bp / np.sqrt(2 * a))
+    return (1.0 + bp * I0) / a
+
+
+def test_evidence_k1_tensor_quadrature_all_three_free():
+    # the 21-point case with all three parameters free under its own priors:
+    # A ~ Gamma(2, 1), mu ~ U(0, 2), w ~ log-uniform(0.1, 1).  The amplitude
+    # integral is closed-form (the likelihood is Gaussian in A), the (mu, log w)
+    # integral a composite Gauss-Legendre tensor rule, refined until it is
+    # converged to 1e-9
+    spec = W.tiny_single_peak(5)
+    x, y, s = spec.x, spec.y, spec.sigma
+    C0 = -np.sum(np.log(np.sqrt(2 * np.pi) * s))
+
+    def log_z(panels):
+        mu, wmu = _gauss_legendre(0.0, 2.0, panels)
+        lw, wlw = _gauss_legendre(math.log(0.1), 0.0, panels // 2)
+        M, LW = np.meshgrid(mu, lw, indexing="ij")
+        phi = np.exp(-(x - M[..., None]) ** 2 / (2 * np.exp(LW)[..., None] ** 2))
+        a = np.sum(phi ** 2 / s ** 2, axis=-1)
+        b = np.sum(phi * y / s ** 2, axis=-1)
+        li = C0 - 0.5 * np.sum((y / s) ** 2) + np.log(_gamma21_amplitude_integral(a, b - 1.0))
+        m = li.max()
+        # prior densities: 1/2 on mu, 1/ln(10) on log w
+        return math.log(np.sum(wmu[:, None] * wlw[None, :] * np.exp(li - m)) / (2.0 * math.log(10.0))) + m
+
+    # the amplitude integral against adaptive quadrature at one node
+    phi = np.exp(-(x - 0.9) ** 2 / (2 * 0.25 ** 2))
+    a, b = np.sum(phi ** 2 / s ** 2), np.sum(phi * y / s ** 2)
+    ref, _ = integrate.quad(lambda A: A * math.exp(-A - 0.5 * a * A * A + b * A - (b - 1) ** 2 / (2 * a)),
+                            0, np.inf, epsabs=0, epsrel=1e-12)
+    assert _gamma21_amplitude_integral(a, b - 1.0) * math.exp(-(b - 1) ** 2 / (2 * a)) == pytest.approx(ref, rel=1e-10)
+    exact = log_z(40)
+    assert abs(exact - log_z(20)) < 1e-9
+    vals = [oracle.run_job(spec, 1, W.Options(particles=3000, sweeps=8, seed=sd))["log_z"]
+            for sd in range(1, 9)]
+    se = np.std(vals, ddof=1) / math.sqrt(len(vals))
+    print("all-free K = 1 log Z: mean", np.mean(vals), "exact", exact, "SE", se)
+    assert 3 * se <= 0.05
+    assert abs(np.mean(vals) - exact) <= 0.05
+
+
 def test_evidence_k1_quadrature_gamma_precision():
     # the App. C parameterisation: A and mu fixed, precision b ~ Gamma(4, 0.25)
     # (shape, rate; mean 16): Z = int Ga(b) L(b) db by adaptive quadrature
