@@ -42,9 +42,9 @@ static void start_worker(Ctx &c)
 static void finish_failed(Ctx &c, Request *r, int st)
 {
     r->status = st;
-    r->state = 2;
     r->t_done = std::chrono::steady_clock::now();
     r->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    r->state.store(2, std::memory_order_release);
     (void)c;
 }
 

@@ -930,10 +930,10 @@ int finalize_requests(Ctx &c, std::vector<Request *> &reqs)
             }
         }
         free_request_device(c, *r);
-        r->state = 2;
         r->t_done = std::chrono::steady_clock::now();
         r->latency_ms =
             std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+        r->state.store(2, std::memory_order_release);
     }
     return SMC_OK;
 }

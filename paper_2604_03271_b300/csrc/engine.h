@@ -6,6 +6,7 @@
 // not active, so one launch sequence advances every job of a batch by one
 // tempering stage regardless of where each job is in its schedule.
 #pragma once
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -63,7 +64,11 @@ struct Request {
     std::vector<void *> job_arena;
     std::vector<size_t> job_bytes;
     // results
-    int state = 0;  // 0 queued, 1 running, 2 done
+    // 0 queued, 1 running, 2 done.  Written by the serving thread or the
+    // blocking entry points and read by smc_poll / smc_wait / smc_result under
+    // another lock: atomic, and set to 2 only after every result field is
+    // written (release), so that a reader that sees 2 sees the results
+    std::atomic<int> state{0};
     int status = SMC_OK;
     int dim_max = 0;
     int64_t n_samples = 0;
