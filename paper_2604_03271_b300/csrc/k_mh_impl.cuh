@@ -183,10 +183,15 @@ struct WarpComp {
 
 // One sweep's proposals of a chain, drawn once by the group's first warp and
 // read by all of its warps (double-buffered by sweep parity: the group
-// barrier after each table write keeps every warp within one sweep).
+// barrier after each table write keeps every warp within one sweep).  An
+// accepted proposal sets its flag (every lane of every warp of the group
+// stores the same 1, so no lane waits on another); the first warp adds the
+// flags of sweep s to its acceptance counts when it draws sweep s + 2 into the
+// same buffer, and those of the last two sweeps when the chain ends.
 struct PropTable {
     float2 tv[SMC_DMAX];  // (thr, vn): accept iff thr < -beta dE (INFINITY: not proposed), natural value
     float un[SMC_DMAX];   // proposal, sampling coordinate
+    unsigned acc[SMC_DMAX];  // 1: accepted in this table's sweep
 };
 
 // Chebyshev T_q(t) by the three-term recurrence
@@ -356,6 +361,10 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
             cs.th[j] = u;
             cs.nat[j] = natural_f(jb.pri[j], u);
             cs.acc[j] = 0u;
+            if (g.gw == 0) {
+                prop_sh[g.grp][0].acc[j] = 0u;
+                prop_sh[g.grp][1].acc[j] = 0u;
+            }
         }
         __syncwarp();
 
@@ -452,6 +461,8 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                 }
                 tb.tv[j] = make_float2(thr, v);
                 tb.un[j] = u;
+                cs.acc[j] += tb.acc[j];  // acceptances of sweep sw - 2
+                tb.acc[j] = 0u;
             }
             group_sync(g);
 
@@ -586,14 +597,11 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                                 sc = sc2_of<FAM>(v, wprec);
                             }
                         }
-                        // one lane: the acceptance count is a read-modify-write that
-                        // lanes running apart would repeat
-                        if (lane == 0) {
-                            cs.th[j] = tb.un[j];
-                            cs.nat[j] = v;
-                            cs.acc[j] += 1u;
-                        }
-                        __syncwarp();
+                        // every lane stores the same values (no lane waits on
+                        // another); the count is the table's flag
+                        cs.th[j] = tb.un[j];
+                        cs.nat[j] = v;
+                        tb.acc[j] = 1u;
                     }
                 }
             }
@@ -641,12 +649,9 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
                     const f2 d2 = splat2(dc + dc);
 #pragma unroll
                     for (int p = 0; p < JP; ++p) r[p] = fma2(w[p], mul2(d2, N0[p]), r[p]);
-                    if (lane == 0) {
-                        cs.th[j] = tb.un[j];
-                        cs.nat[j] = v;
-                        cs.acc[j] += 1u;
-                    }
-                    __syncwarp();
+                    cs.th[j] = tb.un[j];
+                    cs.nat[j] = v;
+                    tb.acc[j] = 1u;
                 }
             }
             if (wf) {
@@ -668,7 +673,9 @@ __global__ void __launch_bounds__(MhThreads<G>::NT, (MhMinBlocks<FAM, J, G, R>::
         if (g.gw == 0) {
             for (int j = lane; j < d; j += 32)
                 if (jb.pri[j].kind != PR_FIXED) {
-                    atomicAdd(&jobs[slot].acc[j], (unsigned long long)cs.acc[j]);
+                    atomicAdd(&jobs[slot].acc[j],
+                              (unsigned long long)(cs.acc[j] + prop_sh[g.grp][0].acc[j] +
+                                                   prop_sh[g.grp][1].acc[j]));
                     atomicAdd(&jobs[slot].prop[j], (unsigned long long)n);
                 }
             if (lane == 0) {
