@@ -47,8 +47,8 @@ SM_COUNT = 148
 # of one spectrum per step, per workload; valid only for the kernel source
 # (k_mh_impl.cuh, by sha1) they were taken on; scaled by the spectra a launch
 # processes (the particle state of each spectrum's jobs is its own)
-MH_TRAFFIC = {"xps": {"sha1": "5e06a8045b8e", "bytes_per_spectrum": 6.769e6 + 0.484e6},
-              "xrd": {"sha1": "5e06a8045b8e", "bytes_per_spectrum": 105.80e6 + 59.20e6}}
+MH_TRAFFIC = {"xps": {"sha1": "6bb139c702a2", "bytes_per_spectrum": 6.608e6 + 0.529e6},
+              "xrd": {"sha1": "6bb139c702a2", "bytes_per_spectrum": 105.22e6 + 58.61e6}}
 SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (EX2, RCP)
 
 
