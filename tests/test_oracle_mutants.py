@@ -17,6 +17,7 @@ import inspect
 import itertools
 import os
 import tempfile
+import textwrap
 from concurrent.futures import ThreadPoolExecutor
 
 import pytest
@@ -222,6 +223,22 @@ MUTANTS = [
 ]
 
 
+# Mistakes in the Python half of the oracle (the cross-K post-processing):
+# (name, function, edits, pins).
+PY_MUTANTS = [
+    ("posterior_not_normalised", "posterior_over_k", [("return p / p.sum()", "return p")],
+     [P.test_posterior_over_k_is_softmax_of_evidence]),
+    ("posterior_without_max_shift", "posterior_over_k", [("p = np.exp(lz - m)", "p = np.exp(lz)")],
+     [P.test_posterior_over_k_survives_large_evidences]),
+    ("summary_sorted_by_amplitude", "sorted_summary", [("peaks[:, :, 1]", "peaks[:, :, 0]")],
+     [P.test_sorted_summary_orders_peaks_by_centre]),
+    ("summary_pv_read_as_three_components", "sorted_summary",
+     [("p = 4 if family == 2 else 3", "p = 3")], [P.test_sorted_summary_orders_peaks_by_centre]),
+    ("summary_sorts_phases", "sorted_summary", [("if family == 4:", "if family == -1:")],
+     [P.test_sorted_summary_orders_peaks_by_centre]),
+]
+
+
 def _mutated_source(src: str, edits) -> str:
     for e in edits:
         old, new = e[0], e[1]
@@ -284,7 +301,8 @@ def _detects(fn) -> bool:
 def test_pins_pass_on_the_oracle_itself():
     """The harness calls the pins the way pytest does: on the unmutated
     oracle none of them fails."""
-    for fn in {id(f): f for _, _, pins in MUTANTS for f in pins}.values():
+    pins = [f for m in MUTANTS + PY_MUTANTS for f in m[-1]]
+    for fn in {id(f): f for f in pins}.values():
         assert not _detects(fn), fn.__name__
 
 
@@ -296,4 +314,20 @@ def test_planted_mistake_fails_a_pin(mutant, mutant_libs):
         caught = next((fn.__name__ for fn in pins if _detects(fn)), None)
     finally:
         oracle.use_library(None)
+    assert caught, f"mistake '{name}' passed {[f.__name__ for f in pins]}"
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # a mutant's overflow / 0/0 is its failure
+@pytest.mark.parametrize("mutant", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_python_mistake_fails_a_pin(mutant):
+    name, func, edits, pins = mutant
+    original = getattr(oracle, func)
+    src = _mutated_source(textwrap.dedent(inspect.getsource(original)), edits)
+    ns = dict(vars(oracle))
+    exec(compile(src, f"<oracle mutant {name}>", "exec"), ns)
+    setattr(oracle, func, ns[func])
+    try:
+        caught = next((fn.__name__ for fn in pins if _detects(fn)), None)
+    finally:
+        setattr(oracle, func, original)
     assert caught, f"mistake '{name}' passed {[f.__name__ for f in pins]}"

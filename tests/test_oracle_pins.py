@@ -531,6 +531,34 @@ def test_posterior_over_k_is_softmax_of_evidence():
     np.testing.assert_allclose(p, ref / ref.sum(), rtol=1e-14)
 
 
+def test_posterior_over_k_survives_large_evidences():
+    # log Z of order 1e5 (large N): the softmax must not overflow
+    p = oracle.posterior_over_k([-1.0e5, -1.0e5 + 2.0, -1.0e5 + 1.0])
+    ref = np.array([math.exp(-2.0), 1.0, math.exp(-1.0)])
+    np.testing.assert_allclose(p, ref / ref.sum(), rtol=1e-13)
+
+
+def test_sorted_summary_orders_peaks_by_centre():
+    # two samples of a K = 2 Gaussian model plus a linear background, written
+    # out by hand: sorting each sample's peaks by centre (R10) gives peak 1 =
+    # (2, 3, 2) and (3, 1, 3), peak 2 = (1, 5, 1) and (4, 7, 4); the background
+    # components are not reordered
+    s = np.array([[1.0, 5.0, 1.0, 2.0, 3.0, 2.0, 10.0, 20.0],
+                  [3.0, 1.0, 3.0, 4.0, 7.0, 4.0, 30.0, 40.0]])
+    mean, sd = oracle.sorted_summary(s, W.GAUSS, 2)
+    np.testing.assert_allclose(mean, [2.5, 2.0, 2.5, 2.5, 6.0, 2.5, 20.0, 30.0], rtol=1e-15)
+    np.testing.assert_allclose(sd, [0.5, 1.0, 0.5, 1.5, 1.0, 1.5, 10.0, 10.0], rtol=1e-15)
+    # pseudo-Voigt: four components a peak, the mixing ratio moves with its peak
+    pv = np.array([[1.0, 5.0, 1.0, 0.1, 2.0, 3.0, 2.0, 0.2],
+                   [3.0, 1.0, 3.0, 0.3, 4.0, 7.0, 4.0, 0.4]])
+    mean, _ = oracle.sorted_summary(pv, W.PSEUDO_VOIGT, 2)
+    np.testing.assert_allclose(mean, [2.5, 2.0, 2.5, 0.25, 2.5, 6.0, 2.5, 0.25], rtol=1e-15)
+    # App. D phases are not exchangeable: no reordering
+    ph = np.arange(2 * 18, dtype=np.float64).reshape(2, 18)[:, ::-1].copy()
+    mean, _ = oracle.sorted_summary(ph, W.XRD_PHASE, 2)
+    np.testing.assert_allclose(mean, ph.mean(axis=0), rtol=1e-15)
+
+
 def test_invalid_inputs_rejected():
     spec = W.gaussian_small(1)
     spec.sigma = spec.sigma.copy()
