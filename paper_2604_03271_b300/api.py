@@ -406,3 +406,42 @@ class Context:
                                       _ptr(step), beta, stage, precision, _ptr(nat_out), _ptr(E_out),
                                       _ptr(acc), _ptr(prop)), "smc_k_mh_stage")
         return nat_out, E_out, acc, prop
+
+
+# ---------------------------------------------------------------------------
+# one-call form: one known-sigma spectrum, every candidate K (smc_run)
+# ---------------------------------------------------------------------------
+def make_spectrum(x, y, sigma, k_range, family: int, priors: W.Priors, bg: int = W.BG_NONE,
+                  bg_degree: int = 0) -> W.Spectrum:
+    """The spectrum record smc_run takes: grid x, data y, per-point sigma (a
+    scalar is broadcast to every point), candidate peak counts k_range (a range
+    or a (k_min, k_max) pair: every K from its smallest to its largest value),
+    peak family, priors of the peak components and the background kind.  An
+    empty list of background priors is filled with uniform priors derived from
+    the data range (workloads.data_bg_priors)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    s = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, dtype=np.float64), x.shape))
+    ks = [int(k) for k in k_range]
+    nbg = W.bg_count(int(bg), int(bg_degree))
+    if nbg and not priors.bg:
+        priors = W.Priors(amp=priors.amp, centre=priors.centre, width=priors.width, eta=priors.eta,
+                          bg=W.data_bg_priors(y, nbg))
+    return W.Spectrum(x, y, s, int(family), min(ks), max(ks), int(bg), int(bg_degree), priors, truth={})
+
+
+def run(x, y, sigma, k_range, family: int, priors: W.Priors, bg: int = W.BG_NONE, bg_degree: int = 0,
+        particles: int = 1024, ess: float = 0.5, sweeps: int = 10, waste_free: int = 0,
+        energy_fp64: int = 0, seed: int = 1, max_stages: int = 10000, step_rule: int = 0,
+        device: int = 0, keep_samples: bool = True) -> dict:
+    """Run the sampler on one spectrum for every candidate K and return log Z
+    per K, P(K|D), the selected K, posterior summaries and (optionally) the
+    samples: smc_create, smc_run, smc_result, smc_release, smc_destroy.  The
+    arguments are those of make_spectrum and of smc_options (ess: the ESS
+    target of the tempering bisection)."""
+    spec = make_spectrum(x, y, sigma, k_range, family, priors, bg, bg_degree)
+    opts = W.Options(particles=int(particles), ess_target=float(ess), sweeps=int(sweeps),
+                     waste_free=int(waste_free), energy_fp64=int(energy_fp64), seed=int(seed),
+                     max_stages=int(max_stages), step_rule=int(step_rule))
+    with Context(device) as ctx:
+        return ctx.run(spec, opts, keep_samples=keep_samples)

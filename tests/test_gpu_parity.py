@@ -595,3 +595,18 @@ def test_autotune_short_run_writes_a_loadable_table(tmp_path):
         spec = W.xps_like(5, n=1001, k_true=2, k_max=3)
         r = c.run(spec, W.Options(particles=2048, sweeps=2, seed=3), keep_samples=False)
         assert r["status"] == 0 and np.all(np.isfinite(r["log_z"]))
+
+
+def test_one_call_run_equals_context_run():
+    # api.run (make_spectrum + smc_run in a context of its own) is marshalling
+    # only: the same arrays and options give bit-identical results
+    from paper_2604_03271_b300 import api
+    spec = W.xps_like(4, n=400, k_true=2, k_max=3)
+    with api.Context(0) as c:
+        ref = c.run(spec, W.Options(particles=1024, sweeps=3, seed=9), keep_samples=False)
+    got = api.run(spec.x, spec.y, spec.sigma, range(spec.k_min, spec.k_max + 1), spec.family,
+                  spec.priors, bg=spec.bg, bg_degree=spec.bg_degree, particles=1024, sweeps=3,
+                  seed=9, keep_samples=False)
+    assert ref["status"] == 0 and got["status"] == 0
+    np.testing.assert_array_equal(ref["log_z"], got["log_z"])
+    assert got["argmax_k"] == ref["argmax_k"]
