@@ -49,7 +49,11 @@
  * sigma_i^2 <= 0), sigma unused; or SMC_NOISE_POISSON (App. D), counts y_i >= 0,
  * E = sum_i [(f_i - y_i) - y_i ln(f_i / y_i)] (f_i for y_i = 0, +inf where
  * f_i <= 0) with the normaliser sum_i [y_i ln y_i - y_i - ln Gamma(y_i + 1)] in
- * log Z.  Either way log Z is the log marginal likelihood of Eq. (5) and
+ * log Z.  Poisson requests with FP32 energies (energy_fp64 = 0), a Gaussian
+ * peak family (SMC_GAUSS, SMC_GAUSS_PRECISION) and no background are rejected
+ * with SMC_EINVAL: far from every peak the model falls below FP32's range, and
+ * a positive count there has an infinite FP32 energy where the FP64 one is
+ * finite; such requests take energy_fp64 = 1 or 2, or a background.  Either way log Z is the log marginal likelihood of Eq. (5) and
  * F = -log Z.  The Shirley background and the model variance run
  * in the coupled-grid Metropolis kernel and are combined with no Chebyshev
  * background.

@@ -376,8 +376,10 @@ def run_job(spec, K: int, opts, comp_priors=None, traces: bool = True) -> dict:
         o.beta_trace, o.logz_trace, o.acc_trace, o.step_trace = _dp(bt), _dp(lt), _dp(at), _dp(st)
     lib().orc_run_job(C.byref(h.job), C.byref(o))
     L = o.n_stages
-    return {"status": o.status, "log_z": o.log_z, "n_stages": L, "d": h.d,
-            "samples": samples[:, :h.d], "energies": en,
+    # the final set as the oracle reports it (n_out particles)
+    m = min(int(o.n_out), n_out) if o.status in (OK, EMAXSTAGES) else n_out
+    return {"status": o.status, "log_z": o.log_z, "n_stages": L, "d": h.d, "n_out": int(o.n_out),
+            "samples": samples[:m, :h.d], "energies": en[:m],
             "beta": bt[:L + 1], "logz": lt[:L + 1], "acc": at[:L + 1, :h.d],
             "step": st[:L + 1, :h.d]}
 

@@ -138,6 +138,13 @@ int make_request(Ctx &c, const smc_request &rq, bool on_device, Request *&out)
         for (int q = 0; q < 3; ++q)
             if (!std::isfinite(rq.noise_par[q])) return SMC_EINVAL;
     const smc_options &o = *rq.opts;
+    // FP32 Poisson energies need the model inside FP32's range wherever a count
+    // is positive: Gaussian-tailed peaks with no background underflow there
+    // (an infinite FP32 energy where the FP64 one is finite), so those
+    // requests must take the FP64 energies
+    if (rq.noise == SMC_NOISE_POISSON && o.energy_fp64 == 0 && rq.bg == SMC_BG_NONE &&
+        (rq.family == SMC_GAUSS || rq.family == SMC_GAUSS_PRECISION))
+        return SMC_EINVAL;
     if (rq.n < 2 || rq.n > (1 << 24)) return SMC_EINVAL;
     if (rq.family < 0 || rq.family > 4 || rq.bg < 0 || rq.bg > 5) return SMC_EINVAL;
     const bool xrd = rq.family == SMC_XRD_PHASE;

@@ -206,7 +206,25 @@ MUTANTS = [
         ("orc_quantise(w, Tc, q);", "orc_quantise(w, S, q);"),
         ("orc_resample(q, Tc, S,", "orc_resample(q, S, S,")],
      [A.test_waste_free_second_stage_runs_over_all_states]),
+    ("lambda_initial_value", [("for (int j = 0; j < d; ++j) lam[j] = 2.38;", "for (int j = 0; j < d; ++j) lam[j] = 1.0;")],
+     [A.test_first_stage_step_uses_pre_resample_weights]),
+    ("waste_free_chain_count_floored", [("(T + n - 1) / n : T; /* chains per stage */", "T / n : T; /* chains per stage */")],
+     [P.test_waste_free_particle_count]),
+    ("run_energy_model_variance_ignored", [("if (job->bg_kind == BG_SHIRLEY || job->noise == NOISE_MODEL)",
+                                            "if (job->bg_kind == BG_SHIRLEY)")],
+     [P.test_constant_model_variance_reduces_to_known_sigma]),
+    ("run_energy_poisson_ignored", [("if (job->family == FAM_XRD_PHASE || job->noise == NOISE_POISSON)",
+                                     "if (job->family == FAM_XRD_PHASE)")],
+     [P.test_poisson_counts_with_a_peak_family_fixed_parameters_exact]),
+    ("poisson_normaliser_y_sign", [("lognorm += (y > 0.0 ? y * log(y) : 0.0) - y - lgamma(y + 1.0);",
+                                    "lognorm += (y > 0.0 ? y * log(y) : 0.0) + y - lgamma(y + 1.0);")],
+     [P.test_xrd_poisson_log_z_of_fixed_background_is_exact]),
+    ("xrd_background_lorentz_width_doubled", [("xrd_pv(x, bg[1], bg[1], bg[2])", "xrd_pv(x, bg[1], 2.0 * bg[1], bg[2])")],
+     [P.test_xrd_background_closed_form]),
     # the history step-size predictor (step_rule 1)
+    ("predictor_history_at_next_beta", [("double x = log(beta_prev), y = log(sig);",
+                                         "double x = log(beta_next), y = log(sig);")],
+     [A.test_predictor_hits_target_rate_on_a_power_law, A.test_predictor_history_weights_and_bounds]),
     ("predictor_target_rate", [("/ tan(M_PI * 0.44 / 2.0);", "/ tan(M_PI * 0.234 / 2.0);")],
      [A.test_predictor_hits_target_rate_on_a_power_law]),
     ("predictor_inversion_factor", [("double sig = s_prev * tan(M_PI * a / 2.0) / 2.0;",

@@ -568,10 +568,14 @@ def test_invalid_inputs_rejected():
 
 
 def test_waste_free_particle_count():
+    # S = ceil(T / n) = ceil(100 / 7) = 15 chains, n = 7 states kept per chain
     spec = W.gaussian_small(1)
     r = oracle.run_job(spec, 1, W.Options(particles=100, sweeps=7, waste_free=1, seed=2))
     assert r["status"] == 0
-    assert r["samples"].shape[0] == 15 * 7
+    assert r["n_out"] == 15 * 7 and r["samples"].shape[0] == 15 * 7
+    # every kept state is a real one: its energy is the energy of its sample
+    e = np.array([oracle.energy_spec(spec, 1, nat) for nat in r["samples"]])
+    np.testing.assert_allclose(r["energies"], e, rtol=1e-12)
 
 
 # --------------------------------------------------------------------------
@@ -757,6 +761,26 @@ def test_xrd_poisson_log_z_of_fixed_background_is_exact():
     f = np.array([oracle.xrd_background(bg, xi) for xi in spec.x])
     exact = float(np.sum(stats.poisson.logpmf(spec.y, f)))
     r = oracle.run_job(spec, 0, W.Options(particles=64, sweeps=2, seed=1))
+    assert r["n_stages"] == 1
+    assert r["log_z"] == pytest.approx(exact, rel=1e-12)
+
+
+def test_poisson_counts_with_a_peak_family_fixed_parameters_exact():
+    # Poisson likelihood on the ordinary peak families (not only the phase
+    # model): one Gaussian peak on a constant, every parameter fixed, so one
+    # stage and log Z = sum_i log Poisson(y_i; f_i) exactly
+    rng = np.random.default_rng(8)
+    x = np.linspace(0.0, 10.0, 80)
+    A, mu, w, c0 = 40.0, 4.2, 0.7, 5.0
+    f = A * np.exp(-(x - mu) ** 2 / (2 * w * w)) + c0
+    y = rng.poisson(f).astype(np.float64)
+    pri = W.Priors(amp=W.Prior(W.UNIFORM, 0, 100), centre=W.Prior(W.UNIFORM, 0, 10),
+                   width=W.Prior(W.UNIFORM, 0.1, 2), bg=[W.Prior(W.UNIFORM, 0, 20)])
+    spec = W.Spectrum(x, y, np.ones_like(x), W.GAUSS, 1, 1, W.BG_CONST, 0, pri, truth={},
+                      noise=W.NOISE_POISSON,
+                      comp_priors=[W.Prior(W.FIXED, v) for v in (A, mu, w, c0)])
+    exact = float(np.sum(stats.poisson.logpmf(y, f)))
+    r = oracle.run_job(spec, 1, W.Options(particles=64, sweeps=2, seed=1))
     assert r["n_stages"] == 1
     assert r["log_z"] == pytest.approx(exact, rel=1e-12)
 
