@@ -213,6 +213,9 @@ MUTANTS = [
     ("run_energy_model_variance_ignored", [("if (job->bg_kind == BG_SHIRLEY || job->noise == NOISE_MODEL)",
                                             "if (job->bg_kind == BG_SHIRLEY)")],
      [P.test_constant_model_variance_reduces_to_known_sigma]),
+    ("run_energy_shirley_ignored", [("if (job->bg_kind == BG_SHIRLEY || job->noise == NOISE_MODEL)",
+                                     "if (job->noise == NOISE_MODEL)")],
+     [P.test_shirley_known_sigma_run_is_exact_at_fixed_parameters]),
     ("run_energy_poisson_ignored", [("if (job->family == FAM_XRD_PHASE || job->noise == NOISE_POISSON)",
                                      "if (job->family == FAM_XRD_PHASE)")],
      [P.test_poisson_counts_with_a_peak_family_fixed_parameters_exact]),

@@ -601,6 +601,30 @@ def test_shirley_background_endpoints_and_gaussian_closed_form():
     np.testing.assert_array_equal(f0, np.full_like(x, a))
 
 
+def test_shirley_known_sigma_run_is_exact_at_fixed_parameters():
+    # Shirley background with known per-point sigma in a run: every parameter
+    # fixed, so one stage and log Z = sum log N(y_i; f_i, sigma_i^2) with f the
+    # peak plus its Shirley background (B = a + (b - a) C_i / C_N, C_i the
+    # right-end rectangle sum of the peak from the first point), computed here
+    rng = np.random.default_rng(12)
+    x = np.linspace(845.0, 860.0, 61)
+    A, mu, w, eta, a, b = 900.0, 851.0, 1.1, 0.4, 120.0, 260.0
+    d2 = (x - mu) ** 2
+    peak = A * (eta * np.exp(-math.log(2.0) * d2 / (w * w)) + (1 - eta) * w * w / (w * w + d2))
+    inc = np.concatenate([[0.0], peak[1:] * np.abs(np.diff(x))])
+    f = peak + a + (b - a) * np.cumsum(inc) / inc.sum()
+    sig = np.full_like(x, 25.0)
+    y = f + rng.normal(0.0, 25.0, x.shape)
+    pri = W.Priors(amp=W.Prior(W.UNIFORM, 0, 2000), centre=W.Prior(W.UNIFORM, 845, 860),
+                   width=W.Prior(W.UNIFORM, 0.2, 3), bg=[W.Prior(W.UNIFORM, 0, 500)] * 2)
+    spec = W.Spectrum(x, y, sig, W.PSEUDO_VOIGT, 1, 1, W.BG_SHIRLEY, 0, pri, truth={},
+                      comp_priors=[W.Prior(W.FIXED, v) for v in (A, mu, w, eta, a, b)])
+    exact = float(np.sum(stats.norm.logpdf(y, loc=f, scale=sig)))
+    r = oracle.run_job(spec, 1, W.Options(particles=64, sweeps=2, seed=1))
+    assert r["n_stages"] == 1
+    assert r["log_z"] == pytest.approx(exact, rel=1e-12)
+
+
 def _mp_energy_model(K, nat, x, y, s0, s1, s2):
     """1/2 ln(2 pi v) + 1/2 (y - f)^2 / v summed, v = s0^2 f + s1^2 f^2 + s2^2,
     f = PV peaks (Eq. (E1)) + Shirley background, in 50-digit arithmetic."""
