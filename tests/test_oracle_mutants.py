@@ -110,6 +110,14 @@ MUTANTS = [
                                         "return bg[0] * xrd_pv(x, bg[1], bg[1], bg[2]); }")],
      [P.test_xrd_background_closed_form]),
     # prior draws and prior densities (Sec. II B 2)
+    ("gamma_small_shape_not_boosted", [("double a = pr.p1 < 1.0 ? pr.p1 + 1.0 : pr.p1;", "double a = pr.p1;")],
+     [P.test_prior_draw_distributions]),
+    ("chebyshev_second_kind", [("double a = 1.0, b = t;", "double a = 1.0, b = 2.0 * t;")],
+     [P.test_background_is_chebyshev_series]),
+    ("mh_normal_from_one_word", [("box_muller(ww[0], ww[1])", "box_muller(ww[0], ww[0])")],
+     [P.test_mh_keeps_prior_at_beta_zero, P.test_mh_keeps_gaussian_posterior_invariant]),
+    ("mh_accept_uniform_from_a_normal_word", [("log(u01(ww[2]))", "log(u01(ww[0]))")],
+     [P.test_mh_keeps_gaussian_posterior_invariant, P.test_mh_keeps_prior_at_beta_zero]),
     ("gamma_rate_read_as_scale", [("return g / pr.p2;", "return g * pr.p2;")],
      [P.test_prior_draw_distributions]),
     ("gamma_small_shape_boost_exponent", [("if (pr.p1 < 1.0) g *= pow(u01(w[3]), 1.0 / pr.p1);",
@@ -130,6 +138,10 @@ MUTANTS = [
      [P.test_bisection_bracket_property]),
     ("bisection_branches_swapped", [("            lo = mid;\n        else\n            hi = mid;",
                                      "            hi = mid;\n        else\n            lo = mid;")],
+     [P.test_bisection_bracket_property, P.test_bisection_exponential_closed_form]),
+    ("final_step_never_taken", [("if (orc_ess_frac(e, T, room) >= rho) {", "if (0) {")],
+     [P.test_bisection_final_step_when_flat, P.test_flat_likelihood_single_stage]),
+    ("bisection_stop_absolute", [("hi - lo > 1e-7 * hi", "hi - lo > 1e-7")],
      [P.test_bisection_bracket_property, P.test_bisection_exponential_closed_form]),
     ("evidence_mean_not_taken", [("logz += -delta * emin + log(sw / (double)Tc);",
                                   "logz += -delta * emin + log(sw);")],
