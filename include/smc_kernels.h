@@ -7,6 +7,9 @@
  * Particles are passed as natural parameter values, row-major [count][d],
  * components in the order documented in smc.h.  `precision` selects the
  * kernel family: 0 = the FP32-energy batched kernels, 1 = the plain FP64 ones.
+ * A request is validated as smc_run validates it, with energy_fp64 taken from
+ * `precision` (so a request that smc_run rejects in FP32 -- Poisson counts on
+ * Gaussian peaks without a background -- is rejected here at precision 0).
  * Every call returns an SMC_* status and leaves outputs untouched on error.
  */
 #ifndef SMC_KERNELS_H
