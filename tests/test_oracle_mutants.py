@@ -162,6 +162,21 @@ MUTANTS = [
      [P.test_resample_equal_and_zero_weights_are_exact, P.test_resample_matches_textbook_float_version,
       P.test_resample_offspring_bounds]),
     # Metropolis (Sec. II B 4)
+    ("log_uniform_support_in_natural_units", [("case PR_LOG_UNIFORM: return u >= log(pr.p1) && u <= log(pr.p2);",
+                                               "case PR_LOG_UNIFORM: return u >= pr.p1 && u <= pr.p2;")],
+     [P.test_mh_keeps_prior_at_beta_zero]),
+    ("log_uniform_value_not_exponentiated", [("return pr.kind == PR_LOG_UNIFORM ? exp(u) : u; }", "return u; }")],
+     [P.test_evidence_k1_tensor_quadrature_all_three_free, P.test_evidence_linear_gaussian_closed_form]),
+    ("normal_log_prior_sd_dropped", [("double z = (u - pr.p1) / pr.p2;", "double z = (u - pr.p1);")],
+     [P.test_mh_keeps_gaussian_posterior_invariant, P.test_evidence_linear_gaussian_closed_form]),
+    ("standard_mode_energy_not_updated", [("            memcpy(u_out + (size_t)m * d, cur, sizeof(double) * d);\n            E_out[m] = Ec;",
+                                           "            memcpy(u_out + (size_t)m * d, cur, sizeof(double) * d);\n            E_out[m] = E_start[m];")],
+     [P.test_evidence_linear_gaussian_closed_form, P.test_evidence_k1_quadrature_free_centre,
+      P.test_evidence_k1_tensor_quadrature_all_three_free]),
+    ("standard_mode_keeps_start_state", [("            memcpy(u_out + (size_t)m * d, cur, sizeof(double) * d);\n            E_out[m] = Ec;",
+                                          "            memcpy(u_out + (size_t)m * d, u_start + (size_t)m * d, sizeof(double) * d);\n            E_out[m] = E_start[m];")],
+     [P.test_evidence_linear_gaussian_closed_form, P.test_evidence_k1_quadrature_free_centre,
+      P.test_evidence_k1_tensor_quadrature_all_three_free]),
     ("mh_energy_difference_reversed", [("if (log(u01(ww[2])) < -beta * (Ep - Ec) + dlp) {",
                                         "if (log(u01(ww[2])) < -beta * (Ec - Ep) + dlp) {")],
      [P.test_mh_keeps_gaussian_posterior_invariant]),
